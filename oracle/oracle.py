@@ -1,0 +1,454 @@
+"""FP64 CPU oracle for the dual price-discovery method (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It imports nothing from the product
+package: problems arrive as plain numpy arrays.
+
+The per-job arithmetic lives in ``ra_oracle.c`` (FP64, OpenMP over jobs);
+this module adds the price-discovery loop of Section 5 (Algorithm 2):
+
+* dual value and subgradient  g(lam), q = R - r          (Section 3)
+* feasible lower bound by column scaling  U(X~)            (Section 5)
+* initial prices                                             (Eq. e-initialization)
+* L-BFGS price updates with bounds lam >= 0 -- scipy's L-BFGS-B
+  (memory 10) serves as the quasi-Newton step (Section 5, "More efficient
+  price updates"; Section 6.1 uses L-BFGS with memory 10)
+* the projected subgradient update  lam+ = max(lam - a_k q, 0)  (Section 5)
+* stopping on the duality gap  g(lam) - U(X~) <= eps  (Algorithm 2, step 2),
+  made relative:  (g_best - U_best) / max(|U_best|, |g_best|, 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import time
+
+import numpy as np
+
+from . import build as _build
+
+NOUT = 10
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+        P = ctypes.c_void_p
+        L.ora_version.restype = i32
+        L.ora_max_threads.restype = i32
+        L.ora_job.argtypes = [i32, P, P, i32, d, d, i32, i32, P]
+        L.ora_job.restype = None
+        L.ora_dual.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32, P, P, P, i32]
+        L.ora_dual.restype = i32
+        L.ora_scaled_utility.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32, P, i32]
+        L.ora_scaled_utility.restype = i32
+        L.ora_init.argtypes = [i64, i32, P, P, P, P, P, i32, P, i32]
+        L.ora_init.restype = i32
+        L.ora_jobs.argtypes = [i64, i32, P, P, P, P, P, i32, i32, i64, P, P, i32]
+        L.ora_jobs.restype = i32
+        L.ora_cost.argtypes = [i32, P, P, d, P]
+        L.ora_cost.restype = d
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _arrays(prob):
+    A = np.ascontiguousarray(prob.A, dtype=np.float32)
+    kind = np.ascontiguousarray(prob.kind, dtype=np.uint8)
+    w = np.ascontiguousarray(prob.w, dtype=np.float32)
+    par = np.ascontiguousarray(prob.param, dtype=np.float32)
+    R = np.ascontiguousarray(prob.R, dtype=np.float64)
+    return A, kind, w, par, R
+
+
+def max_threads() -> int:
+    return int(lib().ora_max_threads())
+
+
+# --------------------------------------------------------------------------- per job
+
+def job(a, lam, kind, w, par, cap=True, method="hull"):
+    """One subproblem (Eq. e-subproblem) from FP64 data.  Returns a dict with
+    t, h, jstar, j1, j2, x1, x2 and the tie margins."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    out = np.zeros(NOUT)
+    lib().ora_job(len(a), _p(a), _p(lam), int(kind), float(w), float(par), int(bool(cap)),
+                  0 if method == "hull" else 1, _p(out))
+    return _record(out)
+
+
+def cost(a, lam, t):
+    """(c(t), x): the parametric LP of Section 4.1 solved on the lower hull."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    x = np.zeros(len(a))
+    c = lib().ora_cost(len(a), _p(a), _p(lam), float(t), _p(x))
+    return float(c), x
+
+
+def _record(o):
+    return dict(t=o[0], h=o[1], jstar=int(o[2]), j1=int(o[3]), j2=int(o[4]), x1=o[5], x2=o[6],
+                tie_ratio=o[7], tie_seg=o[8], tie_t=o[9])
+
+
+def jobs(prob, lam, idx=None, cap=True, method="hull", nthreads=0):
+    """Per-job records (array (k, 10)) for rows ``idx`` (all rows if None)."""
+    A, kind, w, par, _ = _arrays(prob)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    if idx is None:
+        cnt, ip = prob.n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        cnt, ip = len(idx), _p(idx)
+    out = np.zeros((cnt, NOUT))
+    rc = lib().ora_jobs(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(lam), int(bool(cap)),
+                        0 if method == "hull" else 1, cnt, ip, _p(out), nthreads)
+    assert rc == 0
+    return out
+
+
+# --------------------------------------------------------------------------- dual
+
+def dual(prob, lam, cap=True, method="hull", nthreads=0):
+    """(g, r, U): dual value g(lam) = lam^T R + sum_i h_i, usage r = sum_i x_i
+    and the utility U(X) of the unscaled subproblem solutions (Section 3)."""
+    A, kind, w, par, R = _arrays(prob)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    g = np.zeros(1)
+    r = np.zeros(prob.m)
+    U = np.zeros(1)
+    rc = lib().ora_dual(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(R), _p(lam),
+                        int(bool(cap)), 0 if method == "hull" else 1, _p(g), _p(r), _p(U),
+                        nthreads)
+    assert rc == 0
+    return float(g[0]), r, float(U[0])
+
+
+def column_scale(R, r):
+    """s_j = min(1, R_j / r_j): scaling that makes X diag(s) meet r <= R (Section 5)."""
+    R = np.asarray(R, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    s = np.ones_like(R)
+    over = r > R
+    s[over] = R[over] / r[over]
+    return s
+
+
+def scaled_utility(prob, lam, s, cap=True, method="hull", nthreads=0):
+    """U(X diag(s)) with X the subproblem solutions at lam (Section 5)."""
+    A, kind, w, par, _ = _arrays(prob)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    U = np.zeros(1)
+    rc = lib().ora_scaled_utility(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(lam),
+                                  _p(s), int(bool(cap)), 0 if method == "hull" else 1, _p(U),
+                                  nthreads)
+    assert rc == 0
+    return float(U[0])
+
+
+def lower_bound(prob, lam, cap=True, method="hull", nthreads=0, r=None):
+    """Feasible utility U(X~) at lam by column scaling, with the scaling used."""
+    if r is None:
+        _, r, _ = dual(prob, lam, cap, method, nthreads)
+    s = column_scale(prob.R, r)
+    return scaled_utility(prob, lam, s, cap, method, nthreads), s
+
+
+def init_prices(prob, cap=True, nthreads=0):
+    """lam^1 of Eq. e-initialization."""
+    A, kind, w, par, R = _arrays(prob)
+    lam = np.zeros(prob.m)
+    rc = lib().ora_init(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(R), int(bool(cap)),
+                        _p(lam), nthreads)
+    assert rc == 0
+    return lam
+
+
+def rel_gap(g, lb):
+    return (g - lb) / max(abs(lb), abs(g), 1.0)
+
+
+# --------------------------------------------------------------------------- solve
+
+@dataclasses.dataclass
+class Solution:
+    lam: np.ndarray          # prices at the best dual value
+    g: float                 # best (smallest) dual value = upper bound on U*
+    U_lb: float              # best feasible utility = lower bound on U*
+    lam_lb: np.ndarray       # prices whose scaled allocation gave U_lb
+    s_lb: np.ndarray         # column scaling used for U_lb
+    gap: float               # relative duality gap
+    evals: int
+    converged: bool
+    seconds: float
+    history: list
+
+
+class _Converged(Exception):
+    pass
+
+
+def solve(prob, cap=True, tol=1e-6, max_evals=400, method="hull", nthreads=0, lam0=None,
+          update="lbfgs", lam_floor=None, history=False, repair=True):
+    """Algorithm 2: evaluate g, q and U(X~) at each price vector, stop when the
+    relative duality gap is <= tol, update the prices with L-BFGS (default) or
+    the projected subgradient method.  When the loop ends above ``tol`` and
+    ``repair`` is set, the tie-aware repair of ``repair_lower_bound`` is
+    tried at the best prices."""
+    m = prob.m
+    lam = init_prices(prob, cap, nthreads) if lam0 is None else np.asarray(lam0, np.float64).copy()
+    if lam_floor is None:
+        # Without the per-job cap a zero price makes strictly increasing
+        # utilities demand unbounded throughput, so prices stay positive.
+        lam_floor = 0.0 if cap else 1e-9 * max(float(np.max(lam)), 1e-300)
+    lam = np.maximum(lam, lam_floor)
+    st = dict(g=np.inf, lam=lam.copy(), lb=-np.inf, lam_lb=lam.copy(), s_lb=np.ones(m), evals=0,
+              hist=[])
+    t0 = time.perf_counter()
+
+    def evaluate(x):
+        x = np.maximum(np.asarray(x, np.float64), lam_floor)
+        g, r, _ = dual(prob, x, cap, method, nthreads)
+        lb, s = lower_bound(prob, x, cap, method, nthreads, r=r)
+        st["evals"] += 1
+        if g < st["g"]:
+            st["g"], st["lam"] = g, x.copy()
+        if lb > st["lb"]:
+            st["lb"], st["lam_lb"], st["s_lb"] = lb, x.copy(), s
+        if history:
+            st["hist"].append((st["evals"], g, lb, rel_gap(st["g"], st["lb"])))
+        if rel_gap(st["g"], st["lb"]) <= tol:
+            raise _Converged
+        if st["evals"] >= max_evals:
+            raise _Converged
+        return g, np.asarray(prob.R, np.float64) - r
+
+    try:
+        if update == "lbfgs":
+            from scipy.optimize import minimize
+            minimize(evaluate, lam, jac=True, method="L-BFGS-B",
+                     bounds=[(lam_floor, None)] * m,
+                     options=dict(maxcor=10, maxfun=max_evals, maxiter=max_evals, ftol=0.0,
+                                  gtol=0.0, maxls=40))
+        elif update == "subgradient":
+            # lam^{k+1} = max(lam^k - a_k q^k, 0), a_k = a_0 / sqrt(k): a_k -> 0, sum a_k = inf
+            g0, q = evaluate(lam)
+            a0 = 0.1 * max(float(np.max(lam)), 1e-12) / max(float(np.max(np.abs(q))), 1e-300)
+            k = 1
+            while True:
+                lam = np.maximum(lam - (a0 / np.sqrt(k)) * q, lam_floor)
+                _, q = evaluate(lam)
+                k += 1
+        else:
+            raise ValueError(update)
+    except _Converged:
+        pass
+    if repair and rel_gap(st["g"], st["lb"]) > tol:
+        # the column-scaled bound stalls when the optimum sits on ties
+        for rel in (1e-10, 1e-8, 1e-6, 1e-4):
+            lb, info = repair_lower_bound(prob, st["lam"], cap, rel, nthreads)
+            if lb > st["lb"]:
+                st["lb"], st["lam_lb"], st["s_lb"] = lb, st["lam"].copy(), info.get("s", st["s_lb"])
+            if rel_gap(st["g"], st["lb"]) <= tol:
+                break
+    gap = rel_gap(st["g"], st["lb"])
+    return Solution(st["lam"], st["g"], st["lb"], st["lam_lb"], st["s_lb"], gap, st["evals"],
+                    gap <= tol, time.perf_counter() - t0, st["hist"])
+
+
+# --------------------------------------------------------------------------- primal
+
+def allocation(prob, lam, cap=True, method="hull", nthreads=0):
+    """Dense X (n x m, FP64) of the subproblem solutions at lam (Section 3,
+    "Recovering an optimal allocation from optimal prices")."""
+    rec = jobs(prob, lam, cap=cap, method=method, nthreads=nthreads)
+    X = np.zeros((prob.n, prob.m))
+    rows = np.arange(prob.n)
+    for jc, xc in ((3, 5), (4, 6)):
+        sel = rec[:, jc] >= 0
+        X[rows[sel], rec[sel, jc].astype(np.int64)] += rec[sel, xc]
+    return X, rec
+
+
+def utility_of(prob, t):
+    """U(t) = sum_i u_i(t_i) in FP64 (Section 2.2)."""
+    w = prob.w.astype(np.float64)
+    par = prob.param.astype(np.float64)
+    t = np.asarray(t, np.float64)
+    u = np.empty_like(t)
+    k = prob.kind
+    with np.errstate(divide="ignore"):
+        m0 = k == 0
+        u[m0] = w[m0] * np.log(t[m0])
+        m1 = k == 1
+        u[m1] = w[m1] * np.power(t[m1], par[m1])
+        m2 = k == 2
+        u[m2] = w[m2] * np.minimum(t[m2], par[m2])
+        m3 = k == 3
+        u[m3] = w[m3] * np.minimum(t[m3] - par[m3], 0.0)
+    return float(np.sum(u))
+
+
+# --------------------------------------------------------------------------- repair
+
+def _u_vec(kind, w, par, t):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if kind == 0:
+            return w * np.log(t)
+        if kind == 1:
+            return w * np.power(t, par)
+        if kind == 2:
+            return w * np.minimum(t, par)
+        return w * np.minimum(t - par, 0.0)
+
+
+def job_alternatives(a, lam, kind, w, par, cap=True, rel=1e-9):
+    """All extreme optimal allocations of one subproblem, within a relative
+    value tolerance: every pair (P, Q) of the points (0,0), (a_j, lam_j)
+    (Section 4.1) with both ends of its maximising t-interval.  Returns a
+    list of (t, x) with x a dense m-vector."""
+    a = np.asarray(a, np.float64)
+    lam = np.asarray(lam, np.float64)
+    m = len(a)
+    cand = []
+    pts = [(-1, 0.0, 0.0)] + [(j, a[j], lam[j]) for j in range(m) if a[j] > 0]
+    for (Q, aQ, lQ) in pts[1:]:
+        starts = pts if cap else pts[:1]
+        for (P, aP, lP) in starts:
+            if not aP < aQ:
+                continue
+            alpha = (lQ - lP) / (aQ - aP)
+            beta = lP - alpha * aP
+            hi = aQ if cap else np.inf
+            ts = []
+            if kind in (0, 1):
+                if alpha <= 0:
+                    ts = [hi]
+                else:
+                    t = w / alpha if kind == 0 else (w * par / alpha) ** (1.0 / (1.0 - par))
+                    ts = [min(max(t, aP), hi)]
+            else:
+                if w < alpha * (1 - rel):
+                    ts = [aP]
+                elif w <= alpha * (1 + rel):
+                    ts = [aP, min(max(par, aP), hi)]
+                elif alpha < 0:
+                    ts = [hi]
+                elif alpha <= rel * w:
+                    ts = [min(max(par, aP), hi), hi]
+                else:
+                    ts = [min(max(par, aP), hi)]
+            for t in ts:
+                if not np.isfinite(t):
+                    continue
+                v = float(_u_vec(kind, w, par, t)) - (alpha * t + beta)
+                x = np.zeros(m)
+                if cap:
+                    xQ = (t - aP) / (aQ - aP)
+                    x[Q] = xQ
+                    if P >= 0:
+                        x[P] = (aQ - t) / (aQ - aP)
+                else:
+                    x[Q] = t / aQ
+                cand.append((v, t, x))
+    if not cand:
+        return [(0.0, np.zeros(m))]
+    best = max(c[0] for c in cand)
+    scale = max(abs(best), 1e-12)
+    keep = []
+    for v, t, x in cand:
+        if v >= best - rel * scale and not any(np.allclose(x, y, rtol=0, atol=1e-13) for _, y in keep):
+            keep.append((t, x))
+    return keep
+
+
+def repair_lower_bound(prob, lam, cap=True, rel=1e-9, nthreads=0, max_flex=20000):
+    """Feasible utility at prices lam when subproblems have several optimal
+    solutions (the paper is silent here; Section 3 only says any optimal
+    allocation solves every job's subproblem at lam*).
+
+    Jobs whose solution is unique within ``rel`` keep it.  For the others the
+    optimal extreme allocations are enumerated and an LP (scipy HiGHS) picks
+    convex weights that (A) minimise the total relative overuse
+    sum_j max(r_j - R_j, 0)/R_j and then (B) maximise the linearised utility
+    sum_k theta_k u(t_k).  Remaining overuse is removed by column scaling.
+    Returns (U_lb, info) with U_lb the exact utility of the repaired X~."""
+    from scipy.optimize import linprog
+    rec = jobs(prob, lam, cap=cap, nthreads=nthreads)
+    flex = np.flatnonzero((rec[:, 8] <= rel * 10) | (rec[:, 9] <= rel * 10))
+    if len(flex) > max_flex:
+        return -np.inf, dict(n_flex=len(flex), status="too many flexible jobs")
+    n, m = prob.n, prob.m
+    R = np.asarray(prob.R, np.float64)
+    X, _ = allocation(prob, lam, cap=cap, nthreads=nthreads)
+    t_all = rec[:, 0].copy()
+    alts = []
+    for i in flex:
+        alts.append(job_alternatives(prob.A[i].astype(np.float64), lam, int(prob.kind[i]),
+                                     float(prob.w[i]), float(prob.param[i]), cap, rel))
+    fixed = np.ones(n, bool)
+    fixed[flex] = False
+    r_fixed = X[fixed].sum(axis=0)
+    nv = sum(len(a_) for a_ in alts)
+    if nv == 0:
+        s = column_scale(R, r_fixed)
+        return (utility_of(prob, (prob.A.astype(np.float64) * X * s).sum(1)),
+                dict(n_flex=0, n_alt=0, s=s, X=X))
+    # variables: theta (nv), v (m)
+    Mx = np.zeros((m, nv))
+    uvec = np.zeros(nv)
+    Aeq = np.zeros((len(alts), nv + m))
+    col = 0
+    for k, (i, al) in enumerate(zip(flex, alts)):
+        for (t, x) in al:
+            Mx[:, col] = x
+            uvec[col] = float(_u_vec(int(prob.kind[i]), float(prob.w[i]), float(prob.param[i]),
+                                     max(t, 1e-300)))
+            Aeq[k, col] = 1.0
+            col += 1
+    Aub = np.hstack([Mx, -np.eye(m)])
+    bub = R - r_fixed
+    beq = np.ones(len(alts))
+    bounds = [(0, None)] * (nv + m)
+    resA = linprog(np.concatenate([np.zeros(nv), 1.0 / R]), A_ub=Aub, b_ub=bub, A_eq=Aeq, b_eq=beq,
+                   bounds=bounds, method="highs")
+    if resA.status != 0:
+        return -np.inf, dict(n_flex=len(flex), status=resA.message)
+    vstar = resA.x[nv:]
+    bounds_b = [(0, None)] * nv + [(0, vj * (1 + 1e-9) + 1e-12) for vj in vstar]
+    resB = linprog(np.concatenate([-uvec, np.zeros(m)]), A_ub=Aub, b_ub=bub, A_eq=Aeq, b_eq=beq,
+                   bounds=bounds_b, method="highs")
+    theta = (resB.x if resB.status == 0 else resA.x)[:nv]
+    Xr = X.copy()
+    col = 0
+    for i, al in zip(flex, alts):
+        xi = np.zeros(m)
+        for (t, x) in al:
+            xi += theta[col] * x
+            col += 1
+        Xr[i] = xi
+    r = Xr.sum(axis=0)
+    s = column_scale(R, r)
+    Af = prob.A.astype(np.float64)
+    t_rep = (Af * Xr * s[None, :]).sum(axis=1)
+    return utility_of(prob, t_rep), dict(n_flex=len(flex), n_alt=nv, s=s, X=Xr)
+
+
+def allocation_stats(X, tol=1e-9):
+    """Fractions of jobs using two resources and of jobs with positive slack
+    1 - 1^T x_i (the statistics quoted in Section 6.2)."""
+    nz = (X > tol).sum(axis=1)
+    slack = 1.0 - X.sum(axis=1)
+    return dict(two_resources=float(np.mean(nz == 2)), one_resource=float(np.mean(nz == 1)),
+                positive_slack=float(np.mean(slack > 1e-6)))

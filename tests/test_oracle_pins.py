@@ -1,0 +1,432 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the
+mathematics, independent of the oracle's own code:
+
+* the worked example of Section 4.1 (golden fixture),
+* the parametric LP c(t) against scipy's LP solver,
+* Algorithm 1 read literally (all pairs) against the hull walk,
+* the subproblem against a generic NLP solver / exact candidate sets,
+* closed forms (m = 1 log utility, water-filling, Fisher-market spending),
+* weak duality, the subgradient against finite differences of g,
+* KKT conditions and zero duality gap at the solution,
+* a brute-force primal solve on tiny problems,
+* price sensitivity lam* = grad_R U*(R) (Eq. e-pstar-grad),
+* the allocation statistics quoted for the medium problem (Section 6.2).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import linprog, minimize
+
+from paper_2104_00282_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_example.json")
+
+
+def _u(kind, w, p, t):
+    if kind == 0:
+        return w * math.log(t) if t > 0 else -math.inf
+    if kind == 1:
+        return w * t ** p
+    if kind == 2:
+        return w * min(t, p)
+    return w * min(t - p, 0.0)
+
+
+def _lp_cost(a, lam, t):
+    """min lam^T x s.t. x >= 0, 1^T x <= 1, a^T x = t (scipy HiGHS)."""
+    m = len(a)
+    res = linprog(c=lam, A_ub=np.ones((1, m)), b_ub=[1.0], A_eq=np.asarray(a, float)[None, :],
+                  b_eq=[t], bounds=[(0, None)] * m, method="highs")
+    assert res.status == 0, res.message
+    return res.fun, res.x
+
+
+# --------------------------------------------------------------------------- Section 4.1
+
+def test_worked_example_cost_curve(oracle):
+    ex = json.load(open(GOLDEN))
+    a, lam = ex["a"], ex["prices"]
+    for tk, ck in zip(ex["kink_points"], ex["kink_values"]):
+        c, _ = oracle.cost(a, lam, tk)
+        assert c == pytest.approx(ck, abs=1e-12)
+    # affine between successive kinks, convex, increasing, c(0) = 0, domain [0, a_max]
+    ks, vs = ex["kink_points"], ex["kink_values"]
+    for (t0, c0), (t1, c1) in zip(zip(ks, vs), zip(ks[1:], vs[1:])):
+        for f in (0.25, 0.5, 0.9):
+            t = t0 + f * (t1 - t0)
+            assert oracle.cost(a, lam, t)[0] == pytest.approx(c0 + f * (c1 - c0), abs=1e-12)
+    assert math.isinf(oracle.cost(a, lam, 5.0001)[0])
+    # which resources a basic solution uses as t sweeps [0, 5]
+    used = set()
+    for t in np.linspace(0.01, 5.0, 500):
+        _, x = oracle.cost(a, lam, t)
+        sup = [j + 1 for j in range(4) if x[j] > 1e-12]
+        used.update(sup)
+        for band in ex["support_by_t"]:
+            lo_ok = t > band["t_lo"] or (band["closed_lo"] and t == band["t_lo"])
+            hi_ok = t < band["t_hi"] or (band["closed_hi"] and t == band["t_hi"])
+            if lo_ok and hi_ok:
+                assert sup == band["resources_1based"], (t, sup)
+        assert len(sup) <= 2                       # basic feasible solution
+        assert x.sum() <= 1 + 1e-12 and np.dot(a, x) == pytest.approx(t, abs=1e-12)
+    assert not used & set(ex["never_used_1based"])
+    # the same curve from an independent LP solver
+    for t in (0.3, 1.0, 2.0, 2.7, 4.2, 5.0):
+        assert oracle.cost(a, lam, t)[0] == pytest.approx(_lp_cost(a, lam, t)[0], abs=1e-9)
+
+
+def test_worked_example_optimal_throughput(oracle):
+    ex = json.load(open(GOLDEN))
+    a, lam = ex["a"], ex["prices"]
+    for method in ("hull", "pairs"):
+        r = oracle.job(a, lam, 0, 1.0, 0.0, True, method)       # u = log t
+        assert r["t"] == pytest.approx(2.0, abs=1e-12)
+        assert (r["j1"], r["j2"], r["x1"]) == (1, -1, pytest.approx(1.0))
+        assert r["h"] == pytest.approx(math.log(2.0) - 1.0, abs=1e-12)
+        r = oracle.job(a, lam, 0, 4.0, 0.0, True, method)       # u = 4 log t
+        assert r["t"] == pytest.approx(ex["paper_t_opt_log_utility"], abs=1e-12)
+        assert (r["j1"], r["j2"]) == (1, 3)
+        assert r["x1"] == pytest.approx(13 / 15, abs=1e-12) and r["x2"] == pytest.approx(2 / 15, abs=1e-12)
+
+
+def test_cost_curve_matches_linprog(oracle):
+    rng = np.random.default_rng(11)
+    for _ in range(150):
+        m = int(rng.integers(1, 7))
+        a = rng.uniform(0.05, 2.0, m)
+        lam = rng.uniform(0.0, 3.0, m)
+        t = rng.uniform(0, a.max())
+        c, x = oracle.cost(a, lam, t)
+        c_lp, _ = _lp_cost(a, lam, t)
+        assert c == pytest.approx(c_lp, rel=1e-8, abs=1e-10)
+        assert np.all(x >= -1e-15) and x.sum() <= 1 + 1e-12
+        assert np.dot(a, x) == pytest.approx(t, rel=1e-12, abs=1e-12)
+        assert np.dot(lam, x) == pytest.approx(c, rel=1e-12, abs=1e-12)
+        assert (x > 1e-14).sum() <= 2
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+
+@pytest.mark.parametrize("cap", [True, False])
+def test_hull_walk_equals_all_pairs(oracle, cap):
+    rng = np.random.default_rng(5 + cap)
+    for _ in range(4000):
+        m = int(rng.integers(1, 8))
+        a = rng.uniform(0.05, 1.5, m)
+        lam = rng.uniform(0.01, 2.0, m)
+        kind = int(rng.integers(0, 4))
+        w = rng.uniform(0.2, 3.0)
+        p = rng.uniform(0.2, 0.8) if kind == 1 else rng.uniform(0.1, 2.0)
+        h = oracle.job(a, lam, kind, w, p, cap, "hull")
+        q = oracle.job(a, lam, kind, w, p, cap, "pairs")
+        assert h["t"] == pytest.approx(q["t"], rel=1e-10, abs=1e-12)
+        assert h["h"] == pytest.approx(q["h"], rel=1e-10, abs=1e-12)
+        assert h["jstar"] == q["jstar"]
+        if min(h["tie_seg"], q["tie_seg"]) > 1e-9 and h["tie_t"] > 1e-9:
+            assert (h["j1"], h["j2"]) == (q["j1"], q["j2"])
+            assert h["x1"] == pytest.approx(q["x1"], rel=1e-9, abs=1e-12)
+            assert h["x2"] == pytest.approx(q["x2"], rel=1e-9, abs=1e-12)
+
+
+def test_subproblem_against_generic_solvers(oracle):
+    """Strictly concave kinds: SLSQP over x from several starts never beats
+    the oracle and comes within its tolerance.  Piecewise-linear kinds: the
+    optimum of the concave piecewise-linear u - c sits at 0, a kink a_j or the
+    target T, so enumerating those with c from scipy's LP is exact."""
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        m = int(rng.integers(1, 5))
+        a = rng.uniform(0.1, 1.5, m)
+        lam = rng.uniform(0.05, 2.0, m)
+        kind = trial % 4
+        w = rng.uniform(0.3, 3.0)
+        p = rng.uniform(0.2, 0.8) if kind == 1 else rng.uniform(0.1, 1.6)
+        ref = oracle.job(a, lam, kind, w, p, True, "hull")
+        if kind in (0, 1):
+            best = -np.inf
+            f = lambda x: -(_u(kind, w, p, max(float(a @ x), 1e-300)) - float(lam @ x))
+            cons = [{"type": "ineq", "fun": lambda x: 1.0 - x.sum()}]
+            for _ in range(6):
+                x0 = rng.dirichlet(np.ones(m + 1))[:m]
+                res = minimize(f, x0, method="SLSQP", bounds=[(1e-12, 1)] * m, constraints=cons,
+                               options=dict(ftol=1e-14, maxiter=500))
+                best = max(best, -res.fun)
+            assert best <= ref["h"] + 1e-8
+            assert best >= ref["h"] - 1e-5 * max(1.0, abs(ref["h"]))
+        else:
+            cands = {0.0, float(p), *map(float, a)}
+            best = max(_u(kind, w, p, t) - _lp_cost(a, lam, t)[0]
+                       for t in cands if 0 <= t <= a.max())
+            assert ref["h"] == pytest.approx(best, abs=1e-9)
+
+
+def test_interior_optimum_meets_marginal_utility(oracle):
+    """Where t* lies strictly inside a cost segment of slope alpha,
+    u'(t*) = alpha (Eq. e-opt-t-log); u' by central differences."""
+    rng = np.random.default_rng(17)
+    checked = 0
+    for _ in range(600):
+        m = int(rng.integers(1, 6))
+        a = rng.uniform(0.1, 1.5, m)
+        lam = rng.uniform(0.05, 2.0, m)
+        kind = int(rng.integers(0, 2))
+        w = rng.uniform(0.3, 3.0)
+        p = rng.uniform(0.2, 0.8)
+        r = oracle.job(a, lam, kind, w, p, True, "hull")
+        if r["j1"] < 0:
+            continue
+        if r["j2"] >= 0:
+            P, Q = r["j1"], r["j2"]
+            alpha = (lam[Q] - lam[P]) / (a[Q] - a[P])
+        elif r["x1"] < 1 - 1e-9:
+            alpha = lam[r["j1"]] / a[r["j1"]]
+        else:
+            continue                                   # at a kink: u' lies between two slopes
+        t, e = r["t"], 1e-6 * r["t"]
+        du = (_u(kind, w, p, t + e) - _u(kind, w, p, t - e)) / (2 * e)
+        assert du == pytest.approx(alpha, rel=1e-6)
+        checked += 1
+    assert checked > 200
+
+
+# --------------------------------------------------------------------------- closed forms
+
+def _single_resource(n, seed, R):
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(0.5, 1.0, (n, 1)).astype(np.float32)
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    return W.Problem(A, np.zeros(n, np.uint8), w, np.zeros(n, np.float32), np.array([R], float))
+
+
+def test_single_resource_log_closed_form(oracle):
+    """m = 1, log utility, cap slack: x_i = w_i / lam, lam = sum w / R; the
+    initialisation of Eq. e-initialization equals lam* exactly."""
+    n = 3000
+    p0 = _single_resource(n, 1, 1.0)
+    wsum = float(p0.w.astype(np.float64).sum())
+    R = 0.3 * wsum / 2.0                                   # lam* = sum w / R >= max w
+    p = _single_resource(n, 1, R)
+    lam_star = wsum / R
+    assert oracle.init_prices(p)[0] == pytest.approx(lam_star, rel=1e-12)
+    sol = oracle.solve(p, tol=1e-11)
+    assert sol.lam[0] == pytest.approx(lam_star, rel=1e-8)
+    U = float(np.sum(p.w.astype(float) * np.log(p.A[:, 0].astype(float) * p.w / lam_star)))
+    assert sol.g == pytest.approx(U, rel=1e-10) and sol.U_lb == pytest.approx(U, rel=1e-9)
+
+
+def test_single_resource_log_water_filling(oracle):
+    """m = 1 with the cap binding: x_i = min(w_i / lam, 1) and
+    sum_i min(w_i / lam, 1) = R, solved exactly by sorting the w_i."""
+    n = 2500
+    p = _single_resource(n, 2, 0.0)
+    w = np.sort(p.w.astype(np.float64))[::-1]
+    R = 0.7 * n                                            # many jobs capped at 1
+    p = _single_resource(n, 2, R)
+    lam = None
+    for k in range(n + 1):                                 # k largest w are capped
+        cand = w[k:].sum() / (R - k) if R > k else np.inf
+        if (k == 0 or w[k - 1] >= cand) and (k == n or w[k] <= cand):
+            lam = cand
+            break
+    assert lam is not None
+    sol = oracle.solve(p, tol=1e-11)
+    assert sol.lam[0] == pytest.approx(lam, rel=1e-7)
+
+
+def test_uncapped_log_fisher_market_spending(oracle):
+    """Without the per-job cap, log utilities form a linear Fisher market
+    (Eisenberg-Gale): every job spends exactly w_i, so lam*^T R = sum_i w_i."""
+    p = W.random_small(4000, 3, seed=4, kinds=(0,))
+    sol = oracle.solve(p, cap=False, tol=1e-10)
+    assert float(sol.lam @ p.R) == pytest.approx(float(p.w.astype(float).sum()), rel=1e-7)
+
+
+# --------------------------------------------------------------------------- duality
+
+def test_weak_duality_and_feasible_lower_bound(oracle):
+    p = W.random_small(3000, 4, seed=7)
+    rng = np.random.default_rng(0)
+    lams = [rng.uniform(0.05, 3.0, p.m) for _ in range(8)]
+    gs, lbs = [], []
+    for lam in lams:
+        g, r, U = oracle.dual(p, lam)
+        lb, s = oracle.lower_bound(p, lam, r=r)
+        X, _ = oracle.allocation(p, lam)
+        rt = (X * s[None, :]).sum(axis=0)
+        assert np.all(rt <= p.R * (1 + 1e-12))                    # X~ is feasible
+        assert np.all(X.sum(axis=1) <= 1 + 1e-12) and np.all(X >= 0)
+        gs.append(g)
+        lbs.append(lb)
+        # g - U(X) = lam^T (R - r): the definition of the Lagrangian at X
+        assert g - U == pytest.approx(float(lam @ (p.R - r)), rel=1e-9, abs=1e-7)
+    assert min(gs) >= max(lbs)
+
+
+def test_subgradient_matches_finite_differences(oracle):
+    p = W.random_small(4000, 4, seed=9, kinds=(0, 1))
+    lam = np.array([0.7, 1.1, 0.9, 1.6])
+    g, r, _ = oracle.dual(p, lam)
+    q = p.R - r
+    for j in range(p.m):
+        h = 1e-7 * lam[j]
+        e = np.zeros(p.m)
+        e[j] = h
+        fd = (oracle.dual(p, lam + e)[0] - oracle.dual(p, lam - e)[0]) / (2 * h)
+        assert fd == pytest.approx(q[j], abs=2e-6 * p.R[j] + 5.0)
+
+
+def test_kkt_and_zero_gap_at_solution(oracle):
+    p = W.config_plain_small()
+    sol = oracle.solve(p, tol=1e-9)
+    assert sol.converged and sol.gap <= 1e-9
+    X, _ = oracle.allocation(p, sol.lam_lb)
+    rt = (X * sol.s_lb[None, :]).sum(axis=0)
+    assert np.all(rt <= p.R * (1 + 1e-12))
+    slack = sol.lam_lb * (p.R - rt)
+    assert np.all(np.abs(slack) <= 1e-7 * abs(sol.U_lb))
+    assert sol.g >= sol.U_lb
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bruteforce_primal_tiny(oracle, seed):
+    """Strong duality on tiny problems (Section 3): problem (e-res-alloc)
+    solved directly over X by SLSQP equals min_{lam >= 0} g(lam), the latter
+    found by a derivative-free search (g is not differentiable at ties, which
+    at n = 4 sit at the optimum); every oracle dual value is an upper bound."""
+    rng = np.random.default_rng(100 + seed)
+    n, m = 4, 3
+    A = rng.uniform(0.2, 1.0, (n, m)).astype(np.float32)
+    kind = np.array([0, 1, 0, 1], np.uint8)
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    par = np.where(kind == 1, rng.uniform(0.3, 0.7, n), 0).astype(np.float32)
+    R = rng.uniform(0.4, 1.2, m)
+    p = W.Problem(A, kind, w, par, R)
+    Af = A.astype(float)
+
+    def negU(x):
+        X = x.reshape(n, m)
+        t = np.maximum((Af * X).sum(1), 1e-300)
+        return -sum(_u(int(kind[i]), float(w[i]), float(par[i]), t[i]) for i in range(n))
+
+    cons = [{"type": "ineq", "fun": lambda x, i=i: 1 - x.reshape(n, m)[i].sum()} for i in range(n)]
+    cons += [{"type": "ineq", "fun": lambda x, j=j: R[j] - x.reshape(n, m)[:, j].sum()}
+             for j in range(m)]
+    best = np.inf
+    for _ in range(8):
+        x0 = rng.uniform(0.01, 0.2, n * m)
+        res = minimize(negU, x0, method="SLSQP", bounds=[(1e-12, 1)] * (n * m), constraints=cons,
+                       options=dict(ftol=1e-15, maxiter=2000))
+        if res.success:
+            best = min(best, res.fun)
+    U_star = -best
+    sol = oracle.solve(p, tol=1e-12, max_evals=300)
+    assert sol.g >= U_star - 1e-9 and sol.U_lb <= U_star + 1e-9
+    gfun = lambda lam: oracle.dual(p, np.abs(lam))[0]
+    g_min = np.inf
+    x = sol.lam
+    for _ in range(4):
+        res = minimize(gfun, x, method="Nelder-Mead",
+                       options=dict(xatol=1e-13, fatol=1e-15, maxiter=20000, maxfev=20000))
+        x = np.abs(res.x)
+        g_min = min(g_min, res.fun)
+    assert g_min == pytest.approx(U_star, rel=1e-7, abs=1e-8)
+
+
+def test_price_is_gradient_of_optimal_utility(oracle):
+    """Eq. e-pstar-grad: (U*(R + h e_j) - U*(R - h e_j)) / 2h -> lam*_j; a
+    resource left unused has price exactly 0.  U*(R) is only piecewise
+    smooth (jobs switch resources), so the difference quotient converges
+    to first order in h."""
+    p = W.random_small(6000, 3, seed=21, kinds=(0, 1))
+    sol = oracle.solve(p, tol=1e-12, max_evals=1000)
+    assert sol.converged
+    for j in range(p.m):
+        h = 3e-4 * p.R[j]
+        vals = []
+        for sgn in (1, -1):
+            q = W.Problem(p.A, p.kind, p.w, p.param, p.R.copy())
+            q.R[j] += sgn * h
+            s2 = oracle.solve(q, tol=1e-12, lam0=sol.lam, max_evals=1000)
+            vals.append(0.5 * (s2.g + s2.U_lb))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert fd == pytest.approx(sol.lam[j], rel=5e-3, abs=1e-9)
+    assert sol.lam.min() == 0.0 and sol.lam.max() > 0.01
+
+
+# --------------------------------------------------------------------------- Section 6.2
+
+def test_paper_medium_problem_statistics(oracle):
+    """Log utility on the Section 6.2 generator: about 17 % of jobs use two
+    resources and about 18 % have positive slack; without the per-job cap no
+    job uses two resources."""
+    p = W.paper_medium(n=200_000, utility="log", seed=1)
+    sol = oracle.solve(p, tol=1e-7)
+    assert sol.converged
+    X, _ = oracle.allocation(p, sol.lam)
+    st = oracle.allocation_stats(X)
+    assert st["two_resources"] == pytest.approx(0.17, abs=0.03)
+    assert st["positive_slack"] == pytest.approx(0.18, abs=0.03)
+    sol_u = oracle.solve(p, cap=False, tol=1e-7)
+    Xu, _ = oracle.allocation(p, sol_u.lam, cap=False)
+    assert oracle.allocation_stats(Xu)["two_resources"] == 0.0
+
+
+def test_projected_subgradient_reaches_same_optimum(oracle):
+    """The basic update of Section 5 converges (slowly) to the L-BFGS optimum."""
+    p = W.config_plain_small(n=400)
+    ref = oracle.solve(p, tol=1e-10)
+    sg = oracle.solve(p, tol=2e-3, update="subgradient", max_evals=20000)
+    assert sg.converged
+    assert sg.g >= ref.U_lb - 1e-9 and sg.U_lb <= ref.g + 1e-9
+    assert sg.g == pytest.approx(ref.g, rel=2e-3)
+
+
+# --------------------------------------------------------------------------- Eq. e-initialization
+
+def test_initialization_is_gradient_of_uniform_allocation_utility(oracle):
+    """With kappa = 1^T R / n <= 1, lam^1 = grad_R sum_i u_i(a_i^T R / n), checked
+    by central differences of the utility of the uniform allocation (all kinds)."""
+    p = W.random_small(5000, 3, seed=31, r_scale=0.2)
+    assert p.R.sum() / p.n <= 1
+    lam1 = oracle.init_prices(p)
+    Af = p.A.astype(np.float64)
+
+    def U_uniform(R):
+        return oracle.utility_of(p, Af @ (np.asarray(R) / p.n))
+
+    for j in range(p.m):
+        h = 1e-6 * p.R[j]
+        e = np.zeros(p.m)
+        e[j] = h
+        fd = (U_uniform(p.R + e) - U_uniform(p.R - e)) / (2 * h)
+        assert fd == pytest.approx(lam1[j], rel=1e-5)
+
+
+def test_initialization_rescales_when_budget_exceeds_one_unit_per_job(oracle):
+    """kappa > 1: x_i = R / (kappa n) has 1^T x_i = 1; with m = 1 and log
+    utility, t_i = a_i and lam^1 = mean(w)."""
+    p = _single_resource(2000, 3, 0.0)
+    p.R = np.array([3.5 * p.n])
+    assert oracle.init_prices(p, cap=True)[0] == pytest.approx(float(p.w.astype(float).mean()), rel=1e-12)
+    # without the per-job cap no rescaling: t_i = 3.5 a_i, lam^1 = mean(w) / 3.5
+    assert oracle.init_prices(p, cap=False)[0] == pytest.approx(float(p.w.astype(float).mean()) / 3.5,
+                                                               rel=1e-12)
+
+
+def test_repaired_allocation_is_feasible_and_below_dual(oracle):
+    """The tie-aware repair yields a feasible X~ whose utility lies between
+    the plain column-scaled bound at the same prices and g (weak duality)."""
+    p = W.paper_medium(n=20_000, utility="log", seed=2)
+    sol = oracle.solve(p, tol=1e-9, repair=False)
+    plain, _ = oracle.lower_bound(p, sol.lam)
+    lb, info = oracle.repair_lower_bound(p, sol.lam, rel=1e-4)
+    assert info["n_flex"] > 0
+    X = info["X"] * info["s"][None, :]
+    assert np.all(X >= -1e-15) and np.all(X.sum(axis=1) <= 1 + 1e-12)
+    assert np.all(X.sum(axis=0) <= p.R * (1 + 1e-12))
+    assert lb <= sol.g + 1e-12 * abs(sol.g)
+    assert lb >= plain
+    assert oracle.rel_gap(sol.g, lb) < 0.1 * oracle.rel_gap(sol.g, plain)
