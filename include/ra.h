@@ -1,0 +1,203 @@
+/*
+ * ra.h -- C ABI of the GB300 price-discovery library (libra.so).
+ *
+ * The library solves the fungible resource-allocation problem of
+ * "Allocation of Fungible Resources via a Fast, Scalable Price Discovery
+ * Method" (arXiv 2104.00282), Section 2.4, problem (e-res-alloc):
+ *
+ *     maximize    sum_i u_i(a_i^T x_i)
+ *     subject to  x_i >= 0,  1^T x_i <= 1   (per-job cap; optional),
+ *                 sum_i x_i <= R,
+ *
+ * by minimising the dual function over resource prices lambda >= 0
+ * (Section 3, problem (e-dual); the paper writes the prices as p).
+ *
+ * Conventions for every entry point:
+ *  - All array arguments are DEVICE pointers unless the comment says
+ *    "host".  They are borrowed: the caller keeps them alive and unchanged
+ *    until the work has completed on the problem's stream.
+ *  - Work is enqueued on the CUDA stream given to ra_problem_create and is
+ *    asynchronous unless the comment says the call synchronises.
+ *  - Matrices are row-major; the efficiency matrix A is n x m FP32 with row i
+ *    equal to a_i^T.  A, kind, w and param must be 16-byte aligned.
+ *  - No exception crosses the ABI.  A non-RA_OK status leaves outputs
+ *    unspecified; ra_last_error() returns a thread-local message.
+ *  - Utility kinds (per job, uint8):
+ *      RA_U_LOG     u(t) = w log t                 (Eq. e-log-util, weighted)
+ *      RA_U_POWER   u(t) = w t^p, 0 < p < 1        (Section 2.2, power utility)
+ *      RA_U_LINCAP  u(t) = w min(t, T)             (target-priority + w T)
+ *      RA_U_TARGET  u(t) = w min(t - T, 0)         (Eq. e-target-priority-util)
+ *    param[i] holds p (power) or T (lincap, target) and is ignored for log.
+ */
+#ifndef RA_H
+#define RA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RA_OK = 0,
+    RA_EINVAL = 1,      /* invalid argument or problem data                  */
+    RA_ENOMEM = 2,      /* device allocation failed                          */
+    RA_ECUDA = 3,       /* a CUDA runtime call failed                        */
+    RA_ENOTCONV = 4,    /* solve stopped at max_evals above the tolerance    */
+    RA_ETIMEOUT = 5,    /* a bounded device wait expired (kernel gave up)    */
+    RA_EUNBOUNDED = 6   /* a zero price with no per-job cap: demand unbounded */
+} ra_status;
+
+enum { RA_U_LOG = 0, RA_U_POWER = 1, RA_U_LINCAP = 2, RA_U_TARGET = 3 };
+
+/* Flags for ra_problem_create. */
+#define RA_JOB_CAP      0x0u /* default: keep the per-job cap 1^T x_i <= 1 (Eq. e-res-alloc) */
+#define RA_NO_JOB_CAP   0x1u /* drop the per-job cap: c_i(t) = t min_j lambda_j / A_ij        */
+#define RA_FP64_JOBMATH 0x2u /* per-job arithmetic in FP64 instead of FP32                     */
+#define RA_VALIDATE     0x4u /* check the data at create time (copies it to the host; syncs)  */
+
+typedef struct ra_problem ra_problem; /* opaque; owns its device workspace */
+
+/* Maximum number of resources m handled by the kernels. */
+#define RA_MAX_M 32
+
+/*
+ * ra_problem_create -- bind problem data (Section 2.4) and allocate the
+ * workspace (per-block partial sums, two n-length compact allocation
+ * buffers of 10 bytes per job, solver state; about 20 n bytes).
+ *   n      number of jobs, n >= 1
+ *   m      number of resources, 1 <= m <= RA_MAX_M
+ *   A      n*m FP32 efficiencies, A_ij >= 0                       (borrowed)
+ *   kind   n uint8 utility kinds                                   (borrowed)
+ *   w      n FP32 weights, w > 0                                   (borrowed)
+ *   param  n FP32 utility parameters (p in (0,1) or T > 0)         (borrowed)
+ *   R      m FP64 resource limits, R_j >= 0                        (borrowed)
+ *   flags  RA_JOB_CAP or RA_NO_JOB_CAP, | RA_FP64_JOBMATH, | RA_VALIDATE
+ *   stream cudaStream_t used by every call on this problem (NULL = legacy)
+ *   out    host: receives the problem handle
+ * Errors: RA_EINVAL on bad sizes, misaligned pointers or (with RA_VALIDATE)
+ * invalid data; RA_ENOMEM / RA_ECUDA on allocation failure.
+ */
+ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t *kind,
+                            const float *w, const float *param, const double *R, uint32_t flags,
+                            void *stream, ra_problem **out);
+
+/* Release the workspace (synchronises the problem's stream first). */
+void ra_problem_destroy(ra_problem *prob);
+
+/*
+ * ra_eval_dual -- dual function and subgradient at prices lambda
+ * (Section 3, "Evaluating the dual function" and eq. e-g-subgrad):
+ *     g(lambda) = lambda^T R + sum_i max_{x_i} [u_i(a_i^T x_i) - lambda^T x_i],
+ *     q         = R - sum_i x_i(lambda).
+ * Each job's subproblem (Algorithm 1) is solved in closed form on the lower
+ * convex hull of (0,0), (A_ij, lambda_j) (Section 4).
+ *   lambda  m FP64 prices >= 0
+ *   g       1 FP64 output (may be NULL)
+ *   q       m FP64 output (may be NULL)
+ *   U_lb    1 FP64 output or NULL: utility of the column-scaled feasible
+ *           allocation X diag(min(1, R/r)) (Section 5); costs a second,
+ *           lighter pass over the jobs.
+ * Deterministic: identical inputs give bitwise identical outputs on the
+ * same GPU (fixed-order two-stage reductions, FP64 across blocks).
+ */
+ra_status ra_eval_dual(ra_problem *prob, const double *lambda, double *g, double *q, double *U_lb);
+
+/*
+ * ra_eval_records -- the per-job allocation chosen inside the last
+ * ra_eval_dual call made with U_lb != NULL (the compact record the lower
+ * bound is formed from): for job i, resources j12[2i], j12[2i+1] (-1 = none,
+ * lower efficiency first) and the throughput A_ij x_ij each delivers,
+ * t12[2i], t12[2i+1] (FP32).  Both outputs are 2n device arrays.
+ */
+ra_status ra_eval_records(ra_problem *prob, int32_t *j12, float *t12);
+
+/*
+ * ra_init_prices -- initial prices of Section 5, Eq. e-initialization:
+ *     x_i = R / (kappa n), kappa = max(1, 1^T R / n) (kappa = 1 without the cap),
+ *     lambda^1 = (1/n) sum_i u_i'(a_i^T x_i) a_i.
+ *   lambda1  m FP64 output.
+ */
+ra_status ra_init_prices(ra_problem *prob, double *lambda1);
+
+typedef struct {
+    double tol_rel;       /* stop when (g_best - U_best)/max(|U_best|,|g_best|,1) <= tol_rel */
+    int32_t max_evals;    /* cap on dual evaluations (line-search trials included)             */
+    int32_t lbfgs_mem;    /* L-BFGS memory, 1..16 (Section 6.1 uses 10)                         */
+    int32_t update;       /* 0 = projected L-BFGS, 1 = projected subgradient (Section 5)        */
+    int32_t use_graph;    /* 1 = run the loop as one CUDA graph with a device-side while node   */
+    double lam_floor;     /* lower bound on prices; <0 selects 0 (cap) / 1e-12 max(lambda^1)    */
+} ra_solve_opts;
+
+typedef struct {
+    int32_t status;       /* ra_status of the solve                                            */
+    int32_t iters;        /* accepted price updates                                            */
+    int32_t evals;        /* dual evaluations                                                  */
+    int32_t ls_fail;      /* line searches that gave up (then a gradient step is used)          */
+    double g;             /* best dual value (upper bound on U*)                                */
+    double U_lb;          /* best feasible utility (lower bound on U*)                          */
+    double rel_gap;       /* relative duality gap at exit                                      */
+    double gap_per_job;   /* (g - U_lb) / n, the paper's absolute measure (Algorithm 2)         */
+} ra_solve_info;
+
+/* Fill *opts with the defaults (tol 1e-6, 500 evals, memory 10, L-BFGS, graph). */
+void ra_solve_opts_default(ra_solve_opts *opts);
+
+/*
+ * ra_solve -- price discovery, Algorithm 2 of Section 5: from lambda0 (or
+ * Eq. e-initialization when lambda0 is NULL) repeat {dual evaluation,
+ * column-scaled lower bound, gap test, price update} on the device until the
+ * relative duality gap is <= tol_rel or max_evals is reached.  The loop runs
+ * without host round trips.  The lower bound of an evaluation is formed in
+ * the following evaluation's pass from a 10-byte-per-job record, so it costs
+ * no second read of A.
+ *   opts        host, may be NULL for defaults
+ *   lambda0     m FP64 start prices or NULL
+ *   lambda_out  m FP64 output: prices with the best dual value
+ *   lambda_lb   m FP64 output or NULL: prices whose (column-scaled) allocation
+ *               gave the best lower bound U_lb
+ *   info        host output (may be NULL)
+ * Synchronises the problem's stream.  Returns RA_ENOTCONV when max_evals
+ * was reached above the tolerance (lambda_out and info are still valid).
+ */
+ra_status ra_solve(ra_problem *prob, const ra_solve_opts *opts, const double *lambda0,
+                   double *lambda_out, double *lambda_lb, ra_solve_info *info);
+
+/*
+ * ra_solve_history -- per-evaluation log of the last ra_solve (the paper's
+ * verbose output, Section 6.1): rows of (evaluation, g, best U_lb, relative
+ * gap).  hist: host buffer of 4*cap doubles.  Returns the number of rows
+ * written (<= cap) or -1 on error.  Synchronises.
+ */
+int32_t ra_solve_history(ra_problem *prob, double *hist, int32_t cap);
+
+/*
+ * ra_recover_primal -- allocation at prices lambda (Section 3, "Recovering an
+ * optimal allocation from optimal prices"): each job's subproblem solution,
+ * which uses at most two resources (Section 4.1).
+ *   jstar     n int32 output or NULL: argmin_j lambda_j / A_ij (-1 if none)
+ *   j12       2n int32 output or NULL: resources used, -1 = none, lower-A first
+ *   x12       2n FP32 output or NULL: their time fractions
+ *   t         n FP32 output or NULL: throughput a_i^T x_i
+ *   X_dense   n*m FP32 output or NULL: dense allocation matrix
+ *   U         1 FP64 output or NULL: sum_i u_i(t_i) of this (unscaled) allocation
+ *   near_tie  n uint8 output or NULL: 1 where the two best effective prices
+ *             lambda_j/A_ij are within 1e-6 relative
+ *   n_near_ties host output or NULL: count of such jobs (synchronises)
+ */
+ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jstar, int32_t *j12,
+                            float *x12, float *t, float *X_dense, double *U, uint8_t *near_tie,
+                            int64_t *n_near_ties);
+
+/* Static strings; ra_last_error() is thread-local and valid until the next call. */
+const char *ra_status_string(ra_status s);
+const char *ra_last_error(void);
+
+/* Library build information, e.g. "libra sm_103a". */
+const char *ra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RA_H */

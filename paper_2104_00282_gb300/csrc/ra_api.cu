@@ -1,0 +1,303 @@
+// C ABI of libra: problem lifetime, argument checks, error strings and the
+// thin host wrappers around the kernels of ra_dual.cu / ra_solve.cu.
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ra_internal.cuh"
+
+namespace ra {
+
+static thread_local char g_err[512] = "";
+
+ra_status fail(ra_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Host-side data checks (RA_VALIDATE): problem (e-res-alloc) needs A >= 0,
+// w > 0, p in (0,1), T > 0, R >= 0, all finite, and a positive efficiency for
+// every log-utility job (Section 2.4: a_i = 0 with log utility is infeasible).
+static ra_status validate(const ra_problem *p)
+{
+    const int64_t n = p->n;
+    const int m = p->m;
+    std::vector<float> A(static_cast<size_t>(n) * m), w(n), par(n);
+    std::vector<uint8_t> kind(n);
+    std::vector<double> R(m);
+    cudaError_t e = cudaMemcpyAsync(A.data(), p->A, A.size() * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.data(), p->w, n * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(par.data(), p->param, n * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kind.data(), p->kind, n, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.data(), p->R, m * 8, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "validate copy: %s", cudaGetErrorString(e));
+    for (int j = 0; j < m; ++j)
+        if (!(std::isfinite(R[j]) && R[j] >= 0.0)) return fail(RA_EINVAL, "R[%d] = %g is not finite and >= 0", j, R[j]);
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i] > RA_U_TARGET) return fail(RA_EINVAL, "kind[%lld] = %d is not a utility kind", (long long)i, kind[i]);
+        if (!(std::isfinite(w[i]) && w[i] > 0.f)) return fail(RA_EINVAL, "w[%lld] = %g must be finite and > 0", (long long)i, w[i]);
+        if (kind[i] == RA_U_POWER && !(par[i] > 0.f && par[i] < 1.f))
+            return fail(RA_EINVAL, "param[%lld] = %g: power exponent must lie in (0, 1)", (long long)i, par[i]);
+        if (kind[i] >= RA_U_LINCAP && !(std::isfinite(par[i]) && par[i] > 0.f))
+            return fail(RA_EINVAL, "param[%lld] = %g: target throughput must be finite and > 0", (long long)i, par[i]);
+        bool any = false;
+        for (int j = 0; j < m; ++j) {
+            const float a = A[static_cast<size_t>(i) * m + j];
+            if (!(std::isfinite(a) && a >= 0.f))
+                return fail(RA_EINVAL, "A[%lld,%d] = %g must be finite and >= 0", (long long)i, j, a);
+            any = any || a > 0.f;
+        }
+        if (!any && kind[i] == RA_U_LOG)
+            return fail(RA_EINVAL, "job %lld has log utility and a zero efficiency row", (long long)i);
+    }
+    return RA_OK;
+}
+
+}  // namespace ra
+
+using ra::fail;
+
+extern "C" {
+
+const char *ra_status_string(ra_status s)
+{
+    switch (s) {
+    case RA_OK: return "ok";
+    case RA_EINVAL: return "invalid argument";
+    case RA_ENOMEM: return "out of device memory";
+    case RA_ECUDA: return "CUDA error";
+    case RA_ENOTCONV: return "not converged";
+    case RA_ETIMEOUT: return "device wait timed out";
+    case RA_EUNBOUNDED: return "unbounded";
+    }
+    return "unknown status";
+}
+
+const char *ra_last_error(void) { return ra::g_err; }
+
+const char *ra_version(void) { return "libra 0.1 sm_103a"; }
+
+void ra_solve_opts_default(ra_solve_opts *o)
+{
+    if (!o) return;
+    o->tol_rel = 1e-6;
+    o->max_evals = 500;
+    o->lbfgs_mem = 10;
+    o->update = 0;
+    o->use_graph = 1;
+    o->lam_floor = -1.0;
+}
+
+ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t *kind,
+                            const float *w, const float *param, const double *R, uint32_t flags,
+                            void *stream, ra_problem **out)
+{
+    ra::g_err[0] = 0;
+    if (!out) return fail(RA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1) return fail(RA_EINVAL, "n = %lld must be >= 1", (long long)n);
+    if (m < 1 || m > RA_MAX_M) return fail(RA_EINVAL, "m = %d must lie in [1, %d]", m, RA_MAX_M);
+    if (n > (int64_t(1) << 40)) return fail(RA_EINVAL, "n = %lld too large", (long long)n);
+    if (!A || !kind || !w || !param || !R) return fail(RA_EINVAL, "a data pointer is NULL");
+    if (!ra::aligned16(A) || !ra::aligned16(kind) || !ra::aligned16(w) || !ra::aligned16(param))
+        return fail(RA_EINVAL, "A, kind, w and param must be 16-byte aligned");
+    if (flags & ~(RA_NO_JOB_CAP | RA_FP64_JOBMATH | RA_VALIDATE)) return fail(RA_EINVAL, "unknown flags 0x%x", flags);
+    ra_problem *p = new (std::nothrow) ra_problem();
+    if (!p) return fail(RA_ENOMEM, "host allocation failed");
+    memset(p, 0, sizeof(*p));
+    p->n = n;
+    p->m = m;
+    p->flags = flags;
+    p->A = A;
+    p->kind = kind;
+    p->w = w;
+    p->param = param;
+    p->R = R;
+    p->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e == cudaSuccess) e = ra::configure_dual(p);
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(RA_ECUDA, "device query: %s", cudaGetErrorString(e));
+    }
+    if (flags & RA_VALIDATE) {
+        ra_status vs = ra::validate(p);
+        if (vs != RA_OK) {
+            delete p;
+            return vs;
+        }
+    }
+    const int gmax = p->grid_dual > p->grid_aux ? p->grid_dual : p->grid_aux;
+    bool ok = true;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
+    };
+    alloc(reinterpret_cast<void **>(&p->partials), sizeof(double) * ra::kPartW * gmax);
+    alloc(reinterpret_cast<void **>(&p->ticket), sizeof(unsigned) * 8);
+    alloc(reinterpret_cast<void **>(&p->status), sizeof(int) * 4);
+    for (int b = 0; b < 2; ++b) {
+        alloc(reinterpret_cast<void **>(&p->lbt[b]), sizeof(float2) * n);
+        alloc(reinterpret_cast<void **>(&p->lbj[b]), sizeof(uchar2) * n);
+    }
+    alloc(reinterpret_cast<void **>(&p->ev), sizeof(ra::EvalOut) * 2);
+    alloc(reinterpret_cast<void **>(&p->s_buf), sizeof(double) * RA_MAX_M);
+    alloc(reinterpret_cast<void **>(&p->st), sizeof(ra::SolverState));
+    alloc(reinterpret_cast<void **>(&p->graph_flag), sizeof(int32_t) * 8);
+    alloc(reinterpret_cast<void **>(&p->tmp), sizeof(double) * (RA_MAX_M + 8));
+    if (!ok) {
+        (void)cudaGetLastError();
+        ra_problem_destroy(p);
+        return fail(RA_ENOMEM, "workspace allocation of about %lld bytes failed", (long long)(20 * n));
+    }
+    e = cudaMemsetAsync(p->ticket, 0, sizeof(unsigned) * 8, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int) * 4, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->graph_flag, 0, sizeof(int32_t) * 8, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ev, 0, sizeof(ra::EvalOut) * 2, p->stream);
+    if (e != cudaSuccess) {
+        ra_problem_destroy(p);
+        return fail(RA_ECUDA, "workspace init: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return RA_OK;
+}
+
+void ra_problem_destroy(ra_problem *p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->partials);
+    cudaFree(p->ticket);
+    cudaFree(p->status);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->lbt[b]);
+        cudaFree(p->lbj[b]);
+    }
+    cudaFree(p->ev);
+    cudaFree(p->s_buf);
+    cudaFree(p->st);
+    cudaFree(p->graph_flag);
+    cudaFree(p->tmp);
+    delete p;
+}
+
+static ra_status check_status_word(ra_problem *p)
+{
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "status read: %s", cudaGetErrorString(e));
+    if (st & ra::kStatusTimeout) return fail(RA_ETIMEOUT, "a device wait gave up (status 0x%x)", st);
+    return RA_OK;
+}
+
+ra_status ra_eval_dual(ra_problem *p, const double *lambda, double *g, double *q, double *U_lb)
+{
+    if (!p || !lambda) return fail(RA_EINVAL, "NULL problem or lambda");
+    ra::DualParams dp{};
+    dp.A = p->A;
+    dp.kind = p->kind;
+    dp.w = p->w;
+    dp.param = p->param;
+    dp.R = p->R;
+    dp.n = p->n;
+    dp.m = p->m;
+    dp.lam = lambda;
+    dp.lbt_out = U_lb ? p->lbt[0] : nullptr;
+    dp.lbj_out = U_lb ? p->lbj[0] : nullptr;
+    dp.partials = p->partials;
+    dp.ticket = p->ticket;
+    dp.status = p->status;
+    dp.out = p->ev;
+    cudaError_t e = ra::launch_dual(p, dp, p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
+    if (U_lb) {
+        e = ra::launch_lower_bound(p, p->lbt[0], p->lbj[0], p->ev, U_lb, p->stream);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "lower-bound launch: %s", cudaGetErrorString(e));
+    }
+    if (g) {
+        e = cudaMemcpyAsync(g, &p->ev->g, sizeof(double), cudaMemcpyDeviceToDevice, p->stream);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "copy g: %s", cudaGetErrorString(e));
+    }
+    if (q) {
+        e = cudaMemcpyAsync(q, p->ev->q, sizeof(double) * p->m, cudaMemcpyDeviceToDevice, p->stream);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "copy q: %s", cudaGetErrorString(e));
+    }
+    return RA_OK;
+}
+
+ra_status ra_eval_records(ra_problem *p, int32_t *j12, float *t12)
+{
+    if (!p || !j12 || !t12) return fail(RA_EINVAL, "NULL argument");
+    cudaError_t e = ra::launch_records(p, j12, t12, p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "records launch: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_init_prices(ra_problem *p, double *lambda1)
+{
+    if (!p || !lambda1) return fail(RA_EINVAL, "NULL problem or output");
+    cudaError_t e = ra::launch_init(p, lambda1, p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "init launch: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_solve(ra_problem *p, const ra_solve_opts *opts, const double *lambda0,
+                   double *lambda_out, double *lambda_lb, ra_solve_info *info)
+{
+    if (!p) return fail(RA_EINVAL, "NULL problem");
+    ra_status s = ra::solve(p, opts, lambda0, lambda_out, lambda_lb, info);
+    if (s == RA_OK || s == RA_ENOTCONV) {
+        ra_status w = check_status_word(p);
+        if (w != RA_OK) return w;
+    }
+    return s;
+}
+
+int32_t ra_solve_history(ra_problem *p, double *hist, int32_t cap)
+{
+    if (!p || !hist || cap < 0) {
+        fail(RA_EINVAL, "bad arguments");
+        return -1;
+    }
+    return ra::solve_history(p, hist, cap);
+}
+
+ra_status ra_recover_primal(ra_problem *p, const double *lambda, int32_t *jstar, int32_t *j12,
+                            float *x12, float *t, float *X_dense, double *U, uint8_t *near_tie,
+                            int64_t *n_near_ties)
+{
+    if (!p || !lambda) return fail(RA_EINVAL, "NULL problem or lambda");
+    unsigned long long *cnt = nullptr;
+    cudaError_t e;
+    if (n_near_ties) {
+        cnt = reinterpret_cast<unsigned long long *>(p->tmp);
+        e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), p->stream);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "memset: %s", cudaGetErrorString(e));
+    }
+    e = ra::launch_recover(p, lambda, jstar, j12, x12, t, X_dense, U, near_tie, cnt, p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "recover launch: %s", cudaGetErrorString(e));
+    if (n_near_ties) {
+        unsigned long long h = 0;
+        e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "tie count: %s", cudaGetErrorString(e));
+        *n_near_ties = static_cast<int64_t>(h);
+    }
+    return RA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1109 @@
+// Fused dual evaluation for the price-discovery method (arXiv 2104.00282).
+//
+// One pass over the jobs computes, at prices lambda (Section 3):
+//   g(lambda) = lambda^T R + sum_i h_i,   r = sum_i x_i,   U(X) = sum_i u_i(t_i),
+// where (t_i, x_i, h_i) solve job i's subproblem (Eq. e-subprob) by the
+// lower-hull walk of Section 4 (Algorithm 1): the first segment leaves the
+// origin towards argmin_j lambda_j/A_ij; while the unconstrained optimum of
+// u - c lies beyond the segment's right end, step to the next hull vertex
+// (the minimum slope among points further right) and solve again with
+// Eq. e-opt-t-log / e-opt-t-target.
+//
+// Layout and data movement (GB300): A is n x m FP32 row-major.  Each CTA owns
+// 256-job tiles (one thread per job); a tile's rows (256*m*4 bytes), weights,
+// parameters and kinds are contiguous, so one elected thread moves each with
+// a 1-D bulk TMA copy (cp.async.bulk) into a multi-stage shared-memory ring
+// completed on mbarriers.  Threads read their row with 128-bit shared loads
+// in a per-thread rotated chunk order (conflict-free); prices live in
+// registers in the same rotated order, so the argmin and hull loops are fully
+// unrolled register code.  The per-resource sums r_j use the tile's own rows
+// as a warp-private dense 32 x m scratch (each job writes its <= 2 nonzeros),
+// reduced column-wise in a fixed order.  Per-thread FP64 accumulators, a
+// fixed-order block stage and a last-block-done grid stage make every output
+// bitwise deterministic for a given GPU.
+
+#include <cstdio>
+
+#include "ra_internal.cuh"
+
+namespace ra {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = kTile / 32;
+
+// ---------------------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for completion of phase `parity`; gives up after about two seconds.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0; it < (1u << 28); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 31 && globaltimer() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------- utilities
+
+template <typename Real> struct Fn;
+template <> struct Fn<float> {
+    static __device__ __forceinline__ float log(float x) { return logf(x); }
+    static __device__ __forceinline__ float log2(float x) { return log2f(x); }
+    static __device__ __forceinline__ float exp2(float x) { return exp2f(x); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <> struct Fn<double> {
+    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double log2(double x) { return ::log2(x); }
+    static __device__ __forceinline__ double exp2(double x) { return ::exp2(x); }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+
+// mu = 1/lambda for the effective-price argmax (argmax_j a_j mu_j).  An exact
+// zero price becomes a huge finite mu instead of +inf, so that zero-price
+// resources still compare by efficiency: the lower hull then leaves the
+// origin along lambda = 0 straight to the most efficient free resource (the
+// farthest collinear point), and no two free resources tie at +inf.
+template <typename Real> __device__ __forceinline__ Real inv_price(Real lam);
+template <> __device__ __forceinline__ float inv_price<float>(float lam)
+{
+    return lam > 0.0f ? 1.0f / lam : (lam == 0.0f ? 5.192296858534828e33f /* 2^112 */ : 0.0f);
+}
+template <> __device__ __forceinline__ double inv_price<double>(double lam)
+{
+    return lam > 0.0 ? 1.0 / lam : (lam == 0.0 ? 0x1p960 : 0.0);
+}
+
+// u(t), Section 2.2.
+template <typename Real>
+__device__ __forceinline__ Real util(int kind, Real w, Real p, Real t)
+{
+    if (kind == RA_U_LOG) return w * Fn<Real>::log(t);
+    if (kind == RA_U_POWER) return t > Real(0) ? w * Fn<Real>::exp2(p * Fn<Real>::log2(t)) : Real(0);
+    if (kind == RA_U_LINCAP) return w * fmin(t, p);
+    return w * fmin(t - p, Real(0));
+}
+
+// Smallest maximiser of u(t) - alpha t on [lo, hi]:
+//   strictly concave kinds: Pi_[lo,hi] (u')^{-1}(alpha)        (Eq. e-opt-t-log)
+//   piecewise-linear kinds: case analysis of Eq. e-opt-t-target.
+template <typename Real>
+__device__ __forceinline__ Real topt(int kind, Real w, Real p, Real alpha, Real lo, Real hi)
+{
+    Real t;
+    if (kind <= RA_U_POWER) {
+        if (!(alpha > Real(0))) return hi;
+        if (kind == RA_U_LOG) t = w / alpha;
+        else t = Fn<Real>::exp2(Fn<Real>::log2(w * p / alpha) / (Real(1) - p));
+    } else {
+        if (w <= alpha) return lo;
+        if (alpha < Real(0)) return hi;
+        t = p;
+    }
+    return fmin(fmax(t, lo), hi);
+}
+
+// Slot k of a per-thread register array holds column colof(k): rows are read
+// in 16-byte chunks rotated by `rot` so that a warp's 128-bit shared loads hit
+// distinct banks.  rot = 0 is the identity mapping.
+template <int MT>
+__device__ __forceinline__ int colof(int k, int rot)
+{
+    constexpr int C = MT / 4;
+    return ((((k >> 2) + rot) & (C - 1)) << 2) | (k & 3);
+}
+
+template <typename Real>
+struct JobSol {
+    Real t, h;
+    Real xP, xQ;      // time fractions on the segment ends (P may be the origin)
+    Real tP, tQ;      // throughput delivered by P and by Q
+    int cP, cQ;       // columns, -1 = none
+    int jstar;        // argmin_j lambda_j / A_ij, -1 = none
+    Real second;      // runner-up of a_j / lambda_j (near-tie detection)
+    Real best;
+};
+
+// Algorithm 1 for one job.  a/lam/mu are register arrays in slot order
+// (mu = 1/lam); fetch(k, &a, &lam) re-reads slot k's pair by column from
+// memory so that no register array is indexed dynamically.
+template <int MT, bool CAP, bool TIES, typename Real, class Fetch>
+__device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)[MT],
+                                          const Real (&mu)[MT], int rot, Fetch fetch, int kind,
+                                          Real w, Real p, JobSol<Real> &s)
+{
+    // A1: cheapest effective price, argmax_j a_j / lambda_j, in four
+    // independent chains (ILP); ties go to the lower column.
+    Real bv[4] = {Real(0), Real(0), Real(0), Real(0)};
+    int bk[4] = {-1, -1, -1, -1};
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        const Real v = a[k] * mu[k];
+        if (v > bv[k & 3]) {
+            bv[k & 3] = v;
+            bk[k & 3] = k;
+        }
+    }
+    Real vb = bv[0];
+    int kb = bk[0];
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+        const bool take = bv[c] > vb || (bv[c] == vb && bk[c] >= 0 &&
+                                         (kb < 0 || colof<MT>(bk[c], rot) < colof<MT>(kb, rot)));
+        if (take) {
+            vb = bv[c];
+            kb = bk[c];
+        }
+    }
+    s.best = vb;
+    s.second = Real(0);
+    if (TIES) {
+        Real sec = Real(0);
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            const Real v = a[k] * mu[k];
+            if (k != kb && v > sec) sec = v;
+        }
+        s.second = sec;
+    }
+    s.cP = -1;
+    s.xP = Real(0);
+    s.tP = Real(0);
+    if (kb < 0) {  // no usable resource
+        s.jstar = -1;
+        s.cQ = -1;
+        s.t = Real(0);
+        s.xQ = Real(0);
+        s.tQ = Real(0);
+        s.h = util<Real>(kind, w, p, Real(0));
+        return;
+    }
+    Real aQ, lQ;
+    fetch(kb, aQ, lQ);
+    s.jstar = colof<MT>(kb, rot);
+    int kQ = kb;
+    Real aP = Real(0), lP = Real(0);
+    int kP = -1;
+    Real alpha = lQ / aQ;
+    Real t;
+    if (!CAP) {
+        t = topt<Real>(kind, w, p, alpha, Real(0), Fn<Real>::inf());
+    } else {
+        // A3: walk the lower hull until the segment holds the optimum.
+        for (int step = 0; step < MT; ++step) {
+            t = topt<Real>(kind, w, p, alpha, aP, aQ);
+            if (t < aQ) break;
+            Real bdl = Real(1), bda = Real(0);
+            int kn = -1;
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                const Real da = a[k] - aQ;
+                const Real dl = lam[k] - lQ;
+                if (da > Real(0) && dl * bda < bdl * da) {
+                    bdl = dl;
+                    bda = da;
+                    kn = k;
+                }
+            }
+            if (kn < 0) {  // aQ = max_j a_j: right end of the domain
+                t = aQ;
+                break;
+            }
+            kP = kQ;
+            aP = aQ;
+            lP = lQ;
+            kQ = kn;
+            fetch(kn, aQ, lQ);
+            alpha = bdl / bda;
+        }
+    }
+    s.t = t;
+    const Real cost = lP + alpha * (t - aP);
+    s.h = util<Real>(kind, w, p, t) - cost;
+    Real xQ, xP;
+    if (CAP) {
+        const Real den = aQ - aP;
+        xQ = (t - aP) / den;
+        xP = (kP >= 0) ? (aQ - t) / den : Real(0);
+    } else {
+        xQ = t / aQ;
+        xP = Real(0);
+    }
+    s.cQ = xQ > Real(0) ? colof<MT>(kQ, rot) : -1;
+    s.xQ = xQ > Real(0) ? xQ : Real(0);
+    s.tQ = s.xQ * aQ;
+    if (kP >= 0 && xP > Real(0)) {
+        s.cP = colof<MT>(kP, rot);
+        s.xP = xP;
+        s.tP = xP * aP;
+    }
+}
+
+// Warp-cooperative r accumulation: each lane's `row` (m entries of shared
+// memory that the lane alone owns) becomes its dense x_i; the 32 x m block is
+// then summed column-wise in a fixed order.  `racc` of lane c (< m) gains the
+// column-c sum.  `grouped` selects the lane-split column sum used when
+// m == MT is a power of two >= 4.
+template <int MT, typename Real>
+__device__ __forceinline__ void warp_rsum(Real *warp_rows, int m, int lane, bool grouped,
+                                          int rot, const JobSol<Real> &s, double &racc)
+{
+    Real *row = warp_rows + lane * m;
+    if (grouped && sizeof(Real) == 4) {
+        constexpr int C = MT / 4;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int q = (c + rot) & (C - 1);
+            reinterpret_cast<float4 *>(row)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        for (int j = 0; j < m; ++j) row[j] = Real(0);
+    }
+    if (s.cP >= 0) row[s.cP] = s.xP;
+    if (s.cQ >= 0) row[s.cQ] = s.xQ;
+    __syncwarp();
+    if (grouped) {
+        constexpr int G = 32 / MT;
+        const int c = lane % MT, g = lane / MT;
+        Real cs = Real(0);
+#pragma unroll
+        for (int k = 0; k < MT; ++k) cs += warp_rows[(g + k * G) * MT + c];
+#pragma unroll
+        for (int off = MT; off < 32; off <<= 1) cs += __shfl_xor_sync(kFull, cs, off);
+        if (g == 0) racc += static_cast<double>(cs);
+    } else if (lane < m) {
+        Real cs = Real(0);
+        for (int r = 0; r < 32; ++r) cs += warp_rows[r * m + lane];
+        racc += static_cast<double>(cs);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+// Block stage + grid stage: per-thread FP64 values -> per-block partials
+// (fixed warp order) -> the last CTA to finish sums the partials in block
+// order and writes the EvalOut slots.  red is kWarps x kPartW shared doubles.
+__device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, double racc,
+                                    int m, bool lane_owns_col, const DualParams &P,
+                                    double (*red)[kPartW])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int is_last;
+    hsum = warp_sum_d(hsum);
+    uxsum = warp_sum_d(uxsum);
+    lbsum = warp_sum_d(lbsum);
+    if (lane == 0) {
+        red[warp][0] = hsum;
+        red[warp][1] = uxsum;
+        red[warp][2] = lbsum;
+        red[warp][3] = 0.0;
+    }
+    if (lane < m) red[warp][4 + lane] = lane_owns_col ? racc : 0.0;
+    __syncthreads();
+    if (tid < m + 4) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += red[w][tid];
+        P.partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(P.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (tid < m + 4) {
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&P.partials[static_cast<size_t>(b) * kPartW + tid]);
+        red[0][tid] = v;
+    }
+    __syncthreads();
+    if (tid < m) {
+        P.out->r[tid] = red[0][4 + tid];
+        P.out->q[tid] = P.R[tid] - red[0][4 + tid];
+    }
+    if (tid == 0) {
+        double lr = 0.0;
+        for (int j = 0; j < m; ++j) lr += P.lam[j] * P.R[j];
+        P.out->sumh = red[0][0];
+        P.out->g = lr + red[0][0];
+        P.out->Ux = red[0][1];
+        P.out->Ulb_prev = red[0][2];
+        *P.ticket = 0u;  // ready for the next launch
+    }
+}
+
+// ---------------------------------------------------------------------------- TMA kernel
+
+template <int MT>
+struct StageLayout {
+    static __host__ __device__ size_t a_bytes(int m) { return static_cast<size_t>(kTile) * m * 4; }
+    static __host__ __device__ size_t bytes(int m) { return a_bytes(m) + kTile * 9; }
+};
+
+// Main streaming kernel, FP32 per-job arithmetic.  Full 256-job tiles come in
+// through the TMA ring; the ragged tail (n mod 256 jobs) is read directly.
+template <int MT, bool CAP, bool LAG, bool REC>
+__global__ void __launch_bounds__(kTile, 2)
+    dual_tma_kernel(DualParams P, int stages, long long num_full)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t bars[kMaxStages];
+    __shared__ float lam_s[RA_MAX_M];
+    __shared__ float s_s[RA_MAX_M];
+    __shared__ double red[kWarps][kPartW];
+
+    if (P.skip != nullptr && *P.skip != 0) return;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = P.m;
+    const bool grouped = (m == MT);
+    const float2 *lbt_prev = P.lbt_prev;
+    const uchar2 *lbj_prev = P.lbj_prev;
+    float2 *lbt_out = P.lbt_out;
+    uchar2 *lbj_out = P.lbj_out;
+    if (P.pingpong != nullptr) {
+        const int q = *P.pingpong & 1;
+        lbt_prev = P.lbt_buf[q];
+        lbj_prev = P.lbj_buf[q];
+        lbt_out = P.lbt_buf[q ^ 1];
+        lbj_out = P.lbj_buf[q ^ 1];
+    }
+    const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
+    constexpr int C = MT / 4;
+    const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~static_cast<uintptr_t>(127));
+    const size_t a_bytes = StageLayout<MT>::a_bytes(m);
+    const size_t st_bytes = StageLayout<MT>::bytes(m);
+
+    if (tid < RA_MAX_M) {
+        lam_s[tid] = tid < m ? static_cast<float>(P.lam[tid]) : Fn<float>::inf();
+        s_s[tid] = (LAG && lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    float lam_r[MT], mu_r[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        const int c = colof<MT>(k, rot);
+        lam_r[k] = lam_s[c];
+        mu_r[k] = inv_price<float>(lam_s[c]);
+    }
+
+    const long long G = gridDim.x;
+    const long long n_my = (num_full > blockIdx.x) ? (num_full - blockIdx.x + G - 1) / G : 0;
+
+    auto issue = [&](long long it) {
+        if (it >= n_my) return;
+        const long long tile = blockIdx.x + it * G;
+        const int st = static_cast<int>(it % stages);
+        unsigned char *base = smem + st * st_bytes;
+        const long long j0 = tile * kTile;
+        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
+        bulk_load(base, P.A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
+        bulk_load(base + a_bytes, P.w + j0, kTile * 4, &bars[st]);
+        bulk_load(base + a_bytes + kTile * 4, P.param + j0, kTile * 4, &bars[st]);
+        bulk_load(base + a_bytes + kTile * 8, P.kind + j0, kTile, &bars[st]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < stages; ++s) issue(s);
+
+    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
+    bool aborted = false;
+
+    auto finish_job = [&](long long i, bool valid, int kind, float w, float p,
+                          const JobSol<float> &s, float *warp_rows) {
+        if (valid) {
+            hsum += static_cast<double>(s.h);
+            uxsum += static_cast<double>(util<float>(kind, w, p, s.t));
+            if (LAG && lag) {
+                const float2 tp = lbt_prev[i];
+                const uchar2 jp = lbj_prev[i];
+                float tt = 0.f;
+                if (jp.x != 255) tt += s_s[jp.x] * tp.x;
+                if (jp.y != 255) tt += s_s[jp.y] * tp.y;
+                lbsum += static_cast<double>(util<float>(kind, w, p, tt));
+            }
+            if (REC) {
+                lbt_out[i] = make_float2(s.tP, s.tQ);
+                lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
+            }
+        }
+        warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, s, racc);
+    };
+
+    long long it_fail = 0;
+    for (long long it = 0; it < n_my; ++it) {
+        const int st = static_cast<int>(it % stages);
+        const uint32_t parity = static_cast<uint32_t>((it / stages) & 1);
+        const bool ok = mbar_wait_bounded(&bars[st], parity);
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            it_fail = it;
+            break;
+        }
+        unsigned char *base = smem + st * st_bytes;
+        float *a_s = reinterpret_cast<float *>(base);
+        const float *w_s = reinterpret_cast<const float *>(base + a_bytes);
+        const float *p_s = reinterpret_cast<const float *>(base + a_bytes + kTile * 4);
+        const uint8_t *k_s = base + a_bytes + kTile * 8;
+        const long long i = (blockIdx.x + it * G) * kTile + tid;
+
+        float a[MT];
+        const float *row = a_s + tid * m;
+        if (grouped) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float4 v = reinterpret_cast<const float4 *>(row)[(c + rot) & (C - 1)];
+                a[4 * c + 0] = v.x;
+                a[4 * c + 1] = v.y;
+                a[4 * c + 2] = v.z;
+                a[4 * c + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < MT; ++k) a[k] = k < m ? row[k] : 0.0f;
+        }
+        const int kind = k_s[tid];
+        const float w = w_s[tid], p = p_s[tid];
+        JobSol<float> s;
+        auto fetch = [&](int k, float &av, float &lv) {
+            const int c = colof<MT>(k, rot);
+            av = row[c];
+            lv = lam_s[c];
+        };
+        solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
+        finish_job(i, true, kind, w, p, s, a_s + warp * 32 * m);
+        __syncthreads();  // stage fully consumed
+        if (tid == 0) {
+            fence_proxy_async();
+            issue(it + stages);
+        }
+    }
+
+    if (aborted) {
+        if (tid == 0) {
+            atomicOr(P.status, kStatusTimeout);
+            // let copies already in flight land before the CTA exits (bounded)
+            for (long long it2 = it_fail; it2 < n_my && it2 < it_fail + stages; ++it2)
+                (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1));
+        }
+        __syncthreads();
+    } else {
+        // ragged tail: jobs [num_full * 256, n), one block, direct loads
+        const long long tail0 = num_full * kTile;
+        if (tail0 < P.n && blockIdx.x == static_cast<unsigned>(num_full % G)) {
+            const long long i = tail0 + tid;
+            const bool valid = i < P.n;
+            float a[MT];
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                const int c = colof<MT>(k, rot);
+                a[k] = (valid && c < m) ? __ldg(&P.A[i * m + c]) : 0.0f;
+            }
+            const int kind = valid ? P.kind[i] : RA_U_LINCAP;
+            const float w = valid ? P.w[i] : 1.0f, p = valid ? P.param[i] : 0.0f;
+            JobSol<float> s;
+            auto fetch = [&](int k, float &av, float &lv) {
+                const int c = colof<MT>(k, rot);
+                av = __ldg(&P.A[i * m + c]);
+                lv = lam_s[c];
+            };
+            if (valid) {
+                solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
+            } else {
+                s.cP = s.cQ = -1;
+                s.xP = s.xQ = 0.f;
+            }
+            float *scratch = reinterpret_cast<float *>(smem);  // stage 0 is idle now
+            finish_job(i, valid, kind, w, p, s, scratch + warp * 32 * m);
+        }
+    }
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, m, grouped ? (lane / MT == 0) : true, P, red);
+}
+
+// ---------------------------------------------------------------------------- simple kernel
+
+// One thread per job with direct global loads; used for FP64 per-job
+// arithmetic (the precision study) and as the generic path.
+template <int MT, bool CAP, typename Real, bool LAG, bool REC>
+__global__ void __launch_bounds__(kTile)
+    dual_simple_kernel(DualParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_simple[];
+    __shared__ Real lam_s[RA_MAX_M];
+    __shared__ float s_s[RA_MAX_M];
+    __shared__ double red[kWarps][kPartW];
+    Real *rows = reinterpret_cast<Real *>(smem_simple);  // kTile x m
+
+    if (P.skip != nullptr && *P.skip != 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = P.m;
+    const float2 *lbt_prev = P.lbt_prev;
+    const uchar2 *lbj_prev = P.lbj_prev;
+    float2 *lbt_out = P.lbt_out;
+    uchar2 *lbj_out = P.lbj_out;
+    if (P.pingpong != nullptr) {
+        const int q = *P.pingpong & 1;
+        lbt_prev = P.lbt_buf[q];
+        lbj_prev = P.lbj_buf[q];
+        lbt_out = P.lbt_buf[q ^ 1];
+        lbj_out = P.lbj_buf[q ^ 1];
+    }
+    const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
+    if (tid < RA_MAX_M) {
+        lam_s[tid] = tid < m ? static_cast<Real>(P.lam[tid]) : Fn<Real>::inf();
+        s_s[tid] = (lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
+    }
+    __syncthreads();
+    Real lam_r[MT], mu_r[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        lam_r[k] = lam_s[k];
+        mu_r[k] = inv_price<Real>(lam_s[k]);
+    }
+    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
+    const long long stride = static_cast<long long>(gridDim.x) * kTile;
+    const long long nround = (P.n + stride - 1) / stride;
+    for (long long rr = 0; rr < nround; ++rr) {
+        const long long i = rr * stride + static_cast<long long>(blockIdx.x) * kTile + tid;
+        const bool valid = i < P.n;
+        Real a[MT];
+#pragma unroll
+        for (int k = 0; k < MT; ++k) a[k] = (valid && k < m) ? static_cast<Real>(__ldg(&P.A[i * m + k])) : Real(0);
+        JobSol<Real> s;
+        s.cP = s.cQ = -1;
+        s.xP = s.xQ = Real(0);
+        int kind = RA_U_LINCAP;
+        Real w = 1, p = 0;
+        if (valid) {
+            kind = P.kind[i];
+            w = P.w[i];
+            p = P.param[i];
+            auto fetch = [&](int k, Real &av, Real &lv) {
+                av = static_cast<Real>(__ldg(&P.A[i * m + k]));
+                lv = lam_s[k];
+            };
+            solve_job<MT, CAP, false, Real>(a, lam_r, mu_r, 0, fetch, kind, w, p, s);
+            hsum += static_cast<double>(s.h);
+            uxsum += static_cast<double>(util<Real>(kind, w, p, s.t));
+            if (lag) {
+                const float2 tp = lbt_prev[i];
+                const uchar2 jp = lbj_prev[i];
+                Real tt = Real(0);
+                if (jp.x != 255) tt += static_cast<Real>(s_s[jp.x]) * static_cast<Real>(tp.x);
+                if (jp.y != 255) tt += static_cast<Real>(s_s[jp.y]) * static_cast<Real>(tp.y);
+                lbsum += static_cast<double>(util<Real>(kind, w, p, tt));
+            }
+            if (REC) {
+                lbt_out[i] = make_float2(static_cast<float>(s.tP), static_cast<float>(s.tQ));
+                lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
+            }
+        }
+        warp_rsum<MT, Real>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
+    }
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, m, true, P, red);
+}
+
+// ---------------------------------------------------------------------------- lower bound
+
+// U(X~) = sum_i u_i(s_P t_P + s_Q t_Q), s = min(1, R / r) from an evaluation's r
+// (Section 5, column scaling), from the compact per-job records.
+__global__ void __launch_bounds__(kTile)
+    lower_bound_kernel(const uint8_t *kind, const float *w, const float *param, const float2 *lbt,
+                       const uchar2 *lbj, long long n, int m, const EvalOut *src, const double *R,
+                       double *partials, unsigned *ticket, double *U_lb)
+{
+    __shared__ float s_s[RA_MAX_M];
+    __shared__ double red[kWarps];
+    __shared__ int is_last;
+    const int tid = threadIdx.x;
+    if (tid < RA_MAX_M) {
+        float s = 1.0f;
+        if (tid < m) {
+            const double r = src->r[tid];
+            s = r > R[tid] ? static_cast<float>(R[tid] / r) : 1.0f;
+        }
+        s_s[tid] = s;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * kTile + tid; i < n;
+         i += static_cast<long long>(gridDim.x) * kTile) {
+        const float2 tp = lbt[i];
+        const uchar2 jp = lbj[i];
+        float tt = 0.f;
+        if (jp.x != 255) tt += s_s[jp.x] * tp.x;
+        if (jp.y != 255) tt += s_s[jp.y] * tp.y;
+        acc += static_cast<double>(util<float>(kind[i], w[i], param[i], tt));
+    }
+    acc = warp_sum_d(acc);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kWarps; ++k) v += red[k];
+        partials[blockIdx.x] = v;
+        __threadfence();
+        is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last && tid == 0) {
+        __threadfence();
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[b]);
+        *U_lb = v;
+        *ticket = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------- initialisation
+
+// Eq. e-initialization: lambda^1 = (1/n) sum_i u_i'(a_i^T x0) a_i,
+// x0 = R / (kappa n).  Per-thread FP32 sums over chunks of 16 jobs are
+// flushed into FP64; warps, blocks and the grid are summed in fixed order.
+template <int MT>
+__global__ void __launch_bounds__(kTile)
+    init_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
+                const double *R, long long n, int m, int cap, double *partials, unsigned *ticket,
+                double *lam1)
+{
+    __shared__ float x0_s[RA_MAX_M];
+    __shared__ double red[kWarps][RA_MAX_M];
+    __shared__ int is_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        double kappa = 0.0;
+        for (int j = 0; j < m; ++j) kappa += R[j] / static_cast<double>(n);
+        const double div = (cap && kappa > 1.0) ? kappa : 1.0;
+        for (int j = 0; j < RA_MAX_M; ++j)
+            x0_s[j] = j < m ? static_cast<float>(R[j] / (static_cast<double>(n) * div)) : 0.0f;
+    }
+    __syncthreads();
+    double acc[MT];
+    float part[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        acc[k] = 0.0;
+        part[k] = 0.0f;
+    }
+    int cnt = 0;
+    for (long long i = static_cast<long long>(blockIdx.x) * kTile + tid; i < n;
+         i += static_cast<long long>(gridDim.x) * kTile) {
+        float a[MT];
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            a[k] = k < m ? __ldg(&A[i * m + k]) : 0.0f;
+            t = fmaf(a[k], x0_s[k], t);
+        }
+        const int kd = kind[i];
+        const float wi = w[i], pi = param[i];
+        float d;
+        if (kd == RA_U_LOG) d = wi / t;
+        else if (kd == RA_U_POWER) d = wi * pi * exp2f((pi - 1.0f) * log2f(t));
+        else d = t < pi ? wi : 0.0f;
+#pragma unroll
+        for (int k = 0; k < MT; ++k) part[k] = fmaf(d, a[k], part[k]);
+        if (++cnt == 16) {
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                acc[k] += static_cast<double>(part[k]);
+                part[k] = 0.0f;
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        acc[k] += static_cast<double>(part[k]);
+        acc[k] = warp_sum_d(acc[k]);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < MT; ++k) red[warp][k] = acc[k];
+    __syncthreads();
+    if (tid < m) {
+        double v = 0.0;
+        for (int k = 0; k < kWarps; ++k) v += red[k][tid];
+        partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (tid < m) {
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[static_cast<size_t>(b) * kPartW + tid]);
+        lam1[tid] = v / static_cast<double>(n);
+    }
+    if (tid == 0) *ticket = 0u;
+}
+
+// ---------------------------------------------------------------------------- recovery
+
+// Per-job allocation at lambda (Section 3, recovering an allocation), with
+// the near-tie flag of the effective-price argmin.
+template <int MT, bool CAP, typename Real>
+__global__ void __launch_bounds__(kTile)
+    recover_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
+                   long long n, int m, const double *lam, int32_t *jstar, int32_t *j12, float *x12,
+                   float *tout, float *X, uint8_t *near_tie, unsigned long long *n_ties,
+                   double *partials, unsigned *ticket, double *U)
+{
+    __shared__ Real lam_s[RA_MAX_M];
+    __shared__ double red[kWarps];
+    __shared__ int is_last;
+    const int tid = threadIdx.x;
+    if (tid < RA_MAX_M) lam_s[tid] = tid < m ? static_cast<Real>(lam[tid]) : Fn<Real>::inf();
+    __syncthreads();
+    Real lam_r[MT], mu_r[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        lam_r[k] = lam_s[k];
+        mu_r[k] = inv_price<Real>(lam_s[k]);
+    }
+    double usum = 0.0;
+    unsigned long long ties = 0;
+    for (long long i = static_cast<long long>(blockIdx.x) * kTile + tid; i < n;
+         i += static_cast<long long>(gridDim.x) * kTile) {
+        Real a[MT];
+#pragma unroll
+        for (int k = 0; k < MT; ++k) a[k] = k < m ? static_cast<Real>(__ldg(&A[i * m + k])) : Real(0);
+        const int kd = kind[i];
+        const Real wi = w[i], pi = param[i];
+        JobSol<Real> s;
+        auto fetch = [&](int k, Real &av, Real &lv) {
+            av = static_cast<Real>(__ldg(&A[i * m + k]));
+            lv = lam_s[k];
+        };
+        solve_job<MT, CAP, true, Real>(a, lam_r, mu_r, 0, fetch, kd, wi, pi, s);
+        usum += static_cast<double>(util<Real>(kd, wi, pi, s.t));
+        const bool tie = s.best > Real(0) && s.second >= s.best * Real(1.0 / (1.0 + 1e-6));
+        ties += tie ? 1ull : 0ull;
+        if (near_tie) near_tie[i] = tie ? 1 : 0;
+        if (jstar) jstar[i] = s.jstar;
+        if (j12) {
+            j12[2 * i] = s.cP >= 0 ? s.cP : s.cQ;
+            j12[2 * i + 1] = s.cP >= 0 ? s.cQ : -1;
+        }
+        if (x12) {
+            x12[2 * i] = static_cast<float>(s.cP >= 0 ? s.xP : s.xQ);
+            x12[2 * i + 1] = static_cast<float>(s.cP >= 0 ? s.xQ : Real(0));
+        }
+        if (tout) tout[i] = static_cast<float>(s.t);
+        if (X) {
+            for (int j = 0; j < m; ++j) {
+                float v = 0.f;
+                if (j == s.cP) v = static_cast<float>(s.xP);
+                if (j == s.cQ) v = static_cast<float>(s.xQ);
+                X[i * m + j] = v;
+            }
+        }
+    }
+    if (n_ties) {
+        for (int off = 16; off > 0; off >>= 1) ties += __shfl_xor_sync(kFull, ties, off);
+        if ((tid & 31) == 0 && ties) atomicAdd(n_ties, ties);
+    }
+    usum = warp_sum_d(usum);
+    if ((tid & 31) == 0) red[tid >> 5] = usum;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kWarps; ++k) v += red[k];
+        partials[blockIdx.x] = v;
+        __threadfence();
+        is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last && tid == 0) {
+        __threadfence();
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[b]);
+        if (U) *U = v;
+        *ticket = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------- records
+
+__global__ void records_kernel(const float2 *lbt, const uchar2 *lbj, long long n, int32_t *j12,
+                               float *t12)
+{
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uchar2 j = lbj[i];
+        const float2 t = lbt[i];
+        j12[2 * i] = j.x == 255 ? -1 : j.x;
+        j12[2 * i + 1] = j.y == 255 ? -1 : j.y;
+        t12[2 * i] = t.x;
+        t12[2 * i + 1] = t.y;
+    }
+}
+
+// ---------------------------------------------------------------------------- dispatch
+
+template <int MT>
+int mt_stages(int m)
+{
+    const size_t sb = StageLayout<MT>::bytes(m);
+    int s = static_cast<int>((106 * 1024) / sb);  // two CTAs per SM fit in 228 KB
+    if (s > kMaxStages) s = kMaxStages;
+    if (s < 2) s = 2;
+    return s;
+}
+
+template <int MT, bool CAP, bool LAG, bool REC>
+cudaError_t launch_tma(const ra_problem *p, const DualParams &dp, cudaStream_t s)
+{
+    const long long num_full = p->n / kTile;
+    int grid = p->grid_dual;
+    if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
+    dual_tma_kernel<MT, CAP, LAG, REC><<<grid, kTile, p->smem_dual, s>>>(dp, p->stages, num_full);
+    return cudaGetLastError();
+}
+
+template <int MT, bool CAP, typename Real, bool LAG, bool REC>
+cudaError_t launch_simple(const ra_problem *p, const DualParams &dp, cudaStream_t s)
+{
+    long long blocks = (p->n + kTile - 1) / kTile;
+    if (blocks > p->grid_aux) blocks = p->grid_aux;
+    const size_t smem = static_cast<size_t>(kTile) * p->m * sizeof(Real);
+    dual_simple_kernel<MT, CAP, Real, LAG, REC><<<static_cast<int>(blocks), kTile, smem, s>>>(dp);
+    return cudaGetLastError();
+}
+
+template <int MT, bool CAP>
+cudaError_t launch_dual_mt(const ra_problem *p, const DualParams &dp, cudaStream_t s)
+{
+    const bool lag = dp.lbt_prev != nullptr;
+    const bool rec = dp.lbt_out != nullptr;
+    if (p->flags & RA_FP64_JOBMATH) {
+        if (lag) return rec ? launch_simple<MT, CAP, double, true, true>(p, dp, s)
+                            : launch_simple<MT, CAP, double, true, false>(p, dp, s);
+        return rec ? launch_simple<MT, CAP, double, false, true>(p, dp, s)
+                   : launch_simple<MT, CAP, double, false, false>(p, dp, s);
+    }
+    if (lag) return rec ? launch_tma<MT, CAP, true, true>(p, dp, s) : launch_tma<MT, CAP, true, false>(p, dp, s);
+    return rec ? launch_tma<MT, CAP, false, true>(p, dp, s) : launch_tma<MT, CAP, false, false>(p, dp, s);
+}
+
+template <int MT, bool CAP>
+cudaError_t set_attrs_mt()
+{
+    cudaError_t e;
+#define RA_ATTR(L, R)                                                                              \
+    e = cudaFuncSetAttribute(dual_tma_kernel<MT, CAP, L, R>,                                      \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);            \
+    if (e != cudaSuccess) return e;
+    RA_ATTR(false, false)
+    RA_ATTR(false, true)
+    RA_ATTR(true, false)
+    RA_ATTR(true, true)
+#undef RA_ATTR
+#define RA_ATTR(L, R)                                                                              \
+    e = cudaFuncSetAttribute(dual_simple_kernel<MT, CAP, double, L, R>,                           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTile * MT * 8);        \
+    if (e != cudaSuccess) return e;                                                                \
+    e = cudaFuncSetAttribute(dual_simple_kernel<MT, CAP, float, L, R>,                            \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTile * MT * 4);        \
+    if (e != cudaSuccess) return e;
+    RA_ATTR(false, false)
+    RA_ATTR(false, true)
+    RA_ATTR(true, false)
+    RA_ATTR(true, true)
+#undef RA_ATTR
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t configure_dual(ra_problem *p)
+{
+    const int m = p->m;
+    p->mt = m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
+    switch (p->mt) {
+    case 4: p->stages = mt_stages<4>(m); break;
+    case 8: p->stages = mt_stages<8>(m); break;
+    case 16: p->stages = mt_stages<16>(m); break;
+    default: p->stages = mt_stages<32>(m); break;
+    }
+    const size_t sb = StageLayout<4>::bytes(m);  // layout does not depend on MT
+    p->smem_dual = p->stages * sb + 128;
+    cudaError_t e;
+    if ((e = set_attrs_mt<4, true>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<8, true>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<16, true>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<32, true>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<4, false>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<8, false>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<16, false>()) != cudaSuccess) return e;
+    if ((e = set_attrs_mt<32, false>()) != cudaSuccess) return e;
+    int per_sm = 1;
+    const void *fn = nullptr;
+    switch (p->mt) {
+    case 4: fn = reinterpret_cast<const void *>(dual_tma_kernel<4, true, true, true>); break;
+    case 8: fn = reinterpret_cast<const void *>(dual_tma_kernel<8, true, true, true>); break;
+    case 16: fn = reinterpret_cast<const void *>(dual_tma_kernel<16, true, true, true>); break;
+    default: fn = reinterpret_cast<const void *>(dual_tma_kernel<32, true, true, true>); break;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, p->smem_dual);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    p->grid_dual = p->num_sms * per_sm;
+    p->grid_aux = p->num_sms * 4;
+    return cudaSuccess;
+}
+
+cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t s)
+{
+    const bool cap = !(p->flags & RA_NO_JOB_CAP);
+    switch (p->mt) {
+    case 4: return cap ? launch_dual_mt<4, true>(p, dp, s) : launch_dual_mt<4, false>(p, dp, s);
+    case 8: return cap ? launch_dual_mt<8, true>(p, dp, s) : launch_dual_mt<8, false>(p, dp, s);
+    case 16: return cap ? launch_dual_mt<16, true>(p, dp, s) : launch_dual_mt<16, false>(p, dp, s);
+    default: return cap ? launch_dual_mt<32, true>(p, dp, s) : launch_dual_mt<32, false>(p, dp, s);
+    }
+}
+
+cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
+                               const EvalOut *src, double *U_lb, cudaStream_t s)
+{
+    long long blocks = (p->n + kTile - 1) / kTile;
+    if (blocks > p->grid_aux) blocks = p->grid_aux;
+    lower_bound_kernel<<<static_cast<int>(blocks), kTile, 0, s>>>(
+        p->kind, p->w, p->param, lbt, lbj, p->n, p->m, src, p->R, p->partials, p->ticket + 1, U_lb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s)
+{
+    long long blocks = (p->n + kTile - 1) / kTile;
+    if (blocks > p->grid_aux) blocks = p->grid_aux;
+    records_kernel<<<static_cast<int>(blocks), kTile, 0, s>>>(p->lbt[0], p->lbj[0], p->n, j12, t12);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s)
+{
+    long long blocks = (p->n + kTile - 1) / kTile;
+    if (blocks > p->grid_aux) blocks = p->grid_aux;
+    const int cap = !(p->flags & RA_NO_JOB_CAP);
+    const int b = static_cast<int>(blocks);
+    switch (p->mt) {
+    case 4: init_kernel<4><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
+    case 8: init_kernel<8><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
+    case 16: init_kernel<16><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
+    default: init_kernel<32><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int MT, bool CAP, typename Real>
+static cudaError_t launch_recover_t(const ra_problem *p, int blocks, const double *lam,
+                                    int32_t *jstar, int32_t *j12, float *x12, float *t, float *X,
+                                    double *U, uint8_t *near_tie, unsigned long long *n_ties,
+                                    cudaStream_t s)
+{
+    recover_kernel<MT, CAP, Real><<<blocks, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->n, p->m,
+                                                            lam, jstar, j12, x12, t, X, near_tie,
+                                                            n_ties, p->partials, p->ticket + 3, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jstar, int32_t *j12,
+                           float *x12, float *t, float *X, double *U, uint8_t *near_tie,
+                           unsigned long long *n_ties, cudaStream_t s)
+{
+    long long blocks = (p->n + kTile - 1) / kTile;
+    if (blocks > p->grid_aux) blocks = p->grid_aux;
+    const int b = static_cast<int>(blocks);
+    const bool cap = !(p->flags & RA_NO_JOB_CAP);
+    const bool f64 = (p->flags & RA_FP64_JOBMATH) != 0;
+#define RA_REC(MT)                                                                                 \
+    if (f64) return cap ? launch_recover_t<MT, true, double>(p, b, lam, jstar, j12, x12, t, X, U, near_tie, n_ties, s) \
+                        : launch_recover_t<MT, false, double>(p, b, lam, jstar, j12, x12, t, X, U, near_tie, n_ties, s); \
+    return cap ? launch_recover_t<MT, true, float>(p, b, lam, jstar, j12, x12, t, X, U, near_tie, n_ties, s)          \
+               : launch_recover_t<MT, false, float>(p, b, lam, jstar, j12, x12, t, X, U, near_tie, n_ties, s);
+    switch (p->mt) {
+    case 4: RA_REC(4)
+    case 8: RA_REC(8)
+    case 16: RA_REC(16)
+    default: RA_REC(32)
+    }
+#undef RA_REC
+}
+
+}  // namespace ra

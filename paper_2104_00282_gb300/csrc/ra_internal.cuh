@@ -1,0 +1,154 @@
+// Internal declarations shared by the libra translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ra.h"
+
+namespace ra {
+
+constexpr int kTile = 256;          // jobs per tile == threads per CTA of the streaming kernels
+constexpr int kMaxStages = 8;
+constexpr int kMaxLbfgsMem = 16;
+constexpr int kHist = 512;          // solver history ring length
+constexpr int kPartW = RA_MAX_M + 4; // doubles per block partial: h, U(X), U_lb(prev), spare, r[m]
+
+// Status word bits written by kernels (never trap: a kernel that gives up
+// records why and returns).
+constexpr int kStatusTimeout = 1;
+
+// Result slots of one dual evaluation (device, FP64).
+struct EvalOut {
+    double g;        // lambda^T R + sum h_i
+    double Ux;       // sum_i u_i(t_i) of the unscaled allocation
+    double Ulb_prev; // utility of the column-scaled allocation of the previous evaluation
+    double sumh;     // sum_i h_i
+    double q[RA_MAX_M];
+    double r[RA_MAX_M];
+};
+
+// Projected L-BFGS state of one solve, entirely in device memory.
+struct SolverState {
+    int32_t phase;       // 0: first evaluation pending; 1: line-search trial pending
+    int32_t done;
+    int32_t status;
+    int32_t k;           // accepted iterations
+    int32_t evals;
+    int32_t ls_iter;
+    int32_t ls_fail;
+    int32_t mem_count;
+    int32_t mem_head;
+    int32_t have_lb_prev; // the evaluation just finished carried a lagged lower bound
+    int32_t m;
+    int32_t mem;
+    int32_t max_evals;
+    int32_t update;       // 0 L-BFGS, 1 subgradient
+    int32_t hist_len;
+    int32_t pad_;
+    double tol;
+    double lam_floor;
+    double g_cur;
+    double step;
+    double g_best;
+    double U_best;
+    double gap;
+    double sg_a0;         // subgradient step scale
+    double lam_cur[RA_MAX_M];
+    double q_cur[RA_MAX_M];
+    double d[RA_MAX_M];
+    double lam_trial[RA_MAX_M];   // prices of the evaluation in flight
+    double lam_prev_eval[RA_MAX_M];
+    double lam_best[RA_MAX_M];
+    double lam_lb[RA_MAX_M];      // prices whose scaled allocation gave U_best
+    double s_lag[RA_MAX_M];       // column scaling of the previous evaluation (lower bound)
+    double R[RA_MAX_M];
+    double S[kMaxLbfgsMem][RA_MAX_M];
+    double Y[kMaxLbfgsMem][RA_MAX_M];
+    double rho[kMaxLbfgsMem];
+    double hist[kHist][4];        // eval, g, U_best, gap
+};
+
+}  // namespace ra
+
+struct ra_problem {
+    int64_t n;
+    int32_t m;
+    uint32_t flags;
+    const float *A;
+    const uint8_t *kind;
+    const float *w;
+    const float *param;
+    const double *R;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int mt;              // compile-time width used for this m (4, 8, 16, 32)
+    int stages;
+    int grid_dual;       // CTAs of the streaming dual kernel
+    int grid_aux;        // CTAs of the lighter passes
+    size_t smem_dual;
+    // workspace (library-owned)
+    double *partials;    // max(grid) * kPartW
+    unsigned *ticket;    // one counter per kernel family
+    int *status;
+    float2 *lbt[2];      // per job (t_P, t_Q): throughput from each used resource
+    uchar2 *lbj[2];      // per job (P, Q), 255 = none
+    ra::EvalOut *ev;     // evaluation result slots (2)
+    double *s_buf;       // m: column scaling for the lower-bound pass
+    ra::SolverState *st;
+    int32_t *graph_flag;
+    double *tmp;         // small scratch (m + 8 doubles)
+};
+
+namespace ra {
+
+struct DualParams {
+    const float *A;
+    const uint8_t *kind;
+    const float *w;
+    const float *param;
+    const double *R;
+    int64_t n;
+    int m;
+    const double *lam;        // m prices
+    // lagged lower bound (all NULL = off)
+    const float2 *lbt_prev;
+    const uchar2 *lbj_prev;
+    const double *s_prev;
+    // compact record of this evaluation (NULL = not written)
+    float2 *lbt_out;
+    uchar2 *lbj_out;
+    double *partials;
+    unsigned *ticket;
+    int *status;
+    EvalOut *out;
+    const int32_t *skip;      // when non-NULL and *skip != 0 the launch does nothing
+    // solver mode: record buffers selected by a device-side parity word and
+    // the lagged bound switched on by a device flag (NULL = fields above)
+    float2 *lbt_buf[2];
+    uchar2 *lbj_buf[2];
+    const int32_t *pingpong;
+    const int32_t *lag_on;
+};
+
+// Launchers (ra_dual.cu).
+cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t s);
+cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
+                               const EvalOut *src, double *U_lb, cudaStream_t s);
+cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s);
+cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);
+cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jstar, int32_t *j12,
+                           float *x12, float *t, float *X, double *U, uint8_t *near_tie,
+                           unsigned long long *n_ties, cudaStream_t s);
+cudaError_t configure_dual(ra_problem *p);
+
+// Solver (ra_solve.cu).
+ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, double *lambda_out,
+                double *lambda_lb, ra_solve_info *info);
+int32_t solve_history(ra_problem *p, double *hist, int32_t cap);
+
+// Error reporting (ra_api.cu).
+ra_status fail(ra_status s, const char *fmt, ...);
+
+}  // namespace ra

@@ -1,0 +1,291 @@
+"""Thin Python binding of the libra C ABI (``include/ra.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors; work is enqueued on the
+stream given at problem creation (torch's current stream by default).  The
+binding raises if ``libra.so`` has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libra.so")
+
+RA_OK, RA_EINVAL, RA_ENOMEM, RA_ECUDA, RA_ENOTCONV, RA_ETIMEOUT, RA_EUNBOUNDED = range(7)
+RA_U_LOG, RA_U_POWER, RA_U_LINCAP, RA_U_TARGET = range(4)
+RA_JOB_CAP, RA_NO_JOB_CAP, RA_FP64_JOBMATH, RA_VALIDATE = 0x0, 0x1, 0x2, 0x4
+RA_MAX_M = 32
+
+
+class RaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libra status {status}: {msg}")
+        self.status = status
+
+
+class ra_solve_opts(ctypes.Structure):
+    _fields_ = [("tol_rel", ctypes.c_double), ("max_evals", ctypes.c_int32),
+                ("lbfgs_mem", ctypes.c_int32), ("update", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("lam_floor", ctypes.c_double)]
+
+
+class ra_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("evals", ctypes.c_int32),
+                ("ls_fail", ctypes.c_int32), ("g", ctypes.c_double), ("U_lb", ctypes.c_double),
+                ("rel_gap", ctypes.c_double), ("gap_per_job", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        L.ra_problem_create.argtypes = [i64, i32, P, P, P, P, P, u32, P, ctypes.POINTER(P)]
+        L.ra_problem_create.restype = i32
+        L.ra_problem_destroy.argtypes = [P]
+        L.ra_problem_destroy.restype = None
+        L.ra_eval_dual.argtypes = [P, P, P, P, P]
+        L.ra_eval_dual.restype = i32
+        L.ra_eval_records.argtypes = [P, P, P]
+        L.ra_eval_records.restype = i32
+        L.ra_init_prices.argtypes = [P, P]
+        L.ra_init_prices.restype = i32
+        L.ra_solve_opts_default.argtypes = [ctypes.POINTER(ra_solve_opts)]
+        L.ra_solve_opts_default.restype = None
+        L.ra_solve.argtypes = [P, ctypes.POINTER(ra_solve_opts), P, P, P,
+                               ctypes.POINTER(ra_solve_info)]
+        L.ra_solve.restype = i32
+        L.ra_solve_history.argtypes = [P, P, i32]
+        L.ra_solve_history.restype = i32
+        L.ra_recover_primal.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
+        L.ra_recover_primal.restype = i32
+        L.ra_status_string.argtypes = [i32]
+        L.ra_status_string.restype = ctypes.c_char_p
+        L.ra_last_error.argtypes = []
+        L.ra_last_error.restype = ctypes.c_char_p
+        L.ra_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, ok=(RA_OK,)):
+    if status not in ok:
+        raise RaError(status, lib().ra_last_error().decode())
+    return status
+
+
+def _ptr(t, dtype=None, numel=None):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"tensor has {t.numel()} elements, need {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------------------- C ABI, same names
+
+def ra_problem_create(A, kind, w, param, R, flags=0, stream=None):
+    n, m = A.shape
+    h = ctypes.c_void_p()
+    _check(lib().ra_problem_create(n, m, _ptr(A, torch.float32), _ptr(kind, torch.uint8, n),
+                                   _ptr(w, torch.float32, n), _ptr(param, torch.float32, n),
+                                   _ptr(R, torch.float64, m), flags, _stream(stream),
+                                   ctypes.byref(h)))
+    return h
+
+
+def ra_problem_destroy(h):
+    lib().ra_problem_destroy(h)
+
+
+def ra_eval_dual(h, lam, g=None, q=None, U_lb=None):
+    _check(lib().ra_eval_dual(h, _ptr(lam, torch.float64), _ptr(g, torch.float64),
+                              _ptr(q, torch.float64), _ptr(U_lb, torch.float64)))
+
+
+def ra_eval_records(h, j12, t12):
+    _check(lib().ra_eval_records(h, _ptr(j12, torch.int32), _ptr(t12, torch.float32)))
+
+
+def ra_init_prices(h, lam1):
+    _check(lib().ra_init_prices(h, _ptr(lam1, torch.float64)))
+
+
+def ra_solve_opts_default():
+    o = ra_solve_opts()
+    lib().ra_solve_opts_default(ctypes.byref(o))
+    return o
+
+
+def ra_solve(h, lam_out, opts=None, lam0=None, lam_lb=None, allow_notconv=True):
+    info = ra_solve_info()
+    o = opts if opts is not None else ra_solve_opts_default()
+    ok = (RA_OK, RA_ENOTCONV) if allow_notconv else (RA_OK,)
+    _check(lib().ra_solve(h, ctypes.byref(o), _ptr(lam0, torch.float64),
+                          _ptr(lam_out, torch.float64), _ptr(lam_lb, torch.float64),
+                          ctypes.byref(info)), ok)
+    return info.as_dict()
+
+
+def ra_solve_history(h, cap=512):
+    import numpy as np
+    buf = np.zeros((cap, 4))
+    k = lib().ra_solve_history(h, ctypes.c_void_p(buf.ctypes.data), cap)
+    if k < 0:
+        raise RaError(RA_ECUDA, lib().ra_last_error().decode())
+    return buf[:k]
+
+
+def ra_recover_primal(h, lam, jstar=None, j12=None, x12=None, t=None, X=None, U=None,
+                      near_tie=None, count_ties=True):
+    cnt = ctypes.c_int64(0)
+    _check(lib().ra_recover_primal(h, _ptr(lam, torch.float64), _ptr(jstar, torch.int32),
+                                   _ptr(j12, torch.int32), _ptr(x12, torch.float32),
+                                   _ptr(t, torch.float32), _ptr(X, torch.float32),
+                                   _ptr(U, torch.float64), _ptr(near_tie, torch.uint8),
+                                   ctypes.byref(cnt) if count_ties else None))
+    return int(cnt.value)
+
+
+def ra_version():
+    return lib().ra_version().decode()
+
+
+# ----------------------------------------------------------------------------- convenience
+
+class AllocationProblem:
+    """Problem (e-res-alloc) bound to device tensors, in the spirit of the
+    paper's ``AllocationProblem`` (Section 6.1): ``solve()`` then ``prices``
+    and ``X``.  Tensors must stay alive with the object."""
+
+    def __init__(self, A, kind, w, param, R, job_cap=True, fp64_jobmath=False, validate=False,
+                 stream=None):
+        dev = A.device
+        self.A = A.contiguous()
+        self.kind = kind.to(dev, torch.uint8).contiguous()
+        self.w = w.to(dev, torch.float32).contiguous()
+        self.param = param.to(dev, torch.float32).contiguous()
+        self.R = R.to(dev, torch.float64).contiguous()
+        self.n, self.m = self.A.shape
+        flags = (0 if job_cap else RA_NO_JOB_CAP) | (RA_FP64_JOBMATH if fp64_jobmath else 0)
+        flags |= RA_VALIDATE if validate else 0
+        self.stream = stream
+        self.handle = ra_problem_create(self.A, self.kind, self.w, self.param, self.R, flags, stream)
+        self.prices = None
+        self.info = None
+
+    @classmethod
+    def from_numpy(cls, prob, device="cuda", **kw):
+        t = lambda a: torch.from_numpy(a).to(device)
+        return cls(t(prob.A), t(prob.kind), t(prob.w), t(prob.param), t(prob.R), **kw)
+
+    def eval_dual(self, lam, lower_bound=False):
+        dev = self.A.device
+        lam = torch.as_tensor(lam, dtype=torch.float64, device=dev).contiguous()
+        g = torch.empty(1, dtype=torch.float64, device=dev)
+        q = torch.empty(self.m, dtype=torch.float64, device=dev)
+        U = torch.empty(1, dtype=torch.float64, device=dev) if lower_bound else None
+        ra_eval_dual(self.handle, lam, g, q, U)
+        return g, q, U
+
+    def eval_records(self):
+        """(j12, t12) chosen by the last eval_dual(..., lower_bound=True)."""
+        j12 = torch.empty(2 * self.n, dtype=torch.int32, device=self.A.device)
+        t12 = torch.empty(2 * self.n, dtype=torch.float32, device=self.A.device)
+        ra_eval_records(self.handle, j12, t12)
+        return j12, t12
+
+    def init_prices(self):
+        lam = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
+        ra_init_prices(self.handle, lam)
+        return lam
+
+    def solve(self, tol=1e-6, max_evals=500, lam0=None, update="lbfgs", use_graph=True,
+              lbfgs_mem=10):
+        o = ra_solve_opts_default()
+        o.tol_rel = tol
+        o.max_evals = max_evals
+        o.lbfgs_mem = lbfgs_mem
+        o.update = 0 if update == "lbfgs" else 1
+        o.use_graph = 1 if use_graph else 0
+        lam = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
+        lam_lb = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
+        if lam0 is not None:
+            lam0 = torch.as_tensor(lam0, dtype=torch.float64, device=self.A.device).contiguous()
+        self.info = ra_solve(self.handle, lam, o, lam0, lam_lb)
+        self.prices = lam
+        self.prices_lb = lam_lb
+        return self.info
+
+    def history(self):
+        """Rows (evaluation, g, best U_lb, relative gap) of the last solve."""
+        return ra_solve_history(self.handle)
+
+    def verbose_log(self, every=5):
+        """The paper's verbose lines (Section 6.1): per-job utility, dual value, gap."""
+        h = self.history()
+        lines = []
+        for k, (ev, g, ub, gap) in enumerate(h):
+            if k % every == 0:
+                lines.append(f"iteration {int(ev):02d} | utility={ub / self.n:.6g} | "
+                             f"dual_value={g / self.n:.6g} | gap={gap:.2e}")
+        if len(h):
+            lines.append(f"Converged in {int(h[-1][0]):03d} evaluations, with residual "
+                         f"{(h[-1][1] - h[-1][2]) / self.n:.6g}")
+        return lines
+
+    def recover(self, lam=None, dense=False):
+        lam = self.prices if lam is None else torch.as_tensor(lam, dtype=torch.float64,
+                                                             device=self.A.device).contiguous()
+        dev = self.A.device
+        out = dict(jstar=torch.empty(self.n, dtype=torch.int32, device=dev),
+                   j12=torch.empty(2 * self.n, dtype=torch.int32, device=dev),
+                   x12=torch.empty(2 * self.n, dtype=torch.float32, device=dev),
+                   t=torch.empty(self.n, dtype=torch.float32, device=dev),
+                   U=torch.empty(1, dtype=torch.float64, device=dev),
+                   near_tie=torch.empty(self.n, dtype=torch.uint8, device=dev))
+        if dense:
+            out["X"] = torch.empty(self.n * self.m, dtype=torch.float32, device=dev)
+        out["n_near_ties"] = ra_recover_primal(self.handle, lam, out["jstar"], out["j12"],
+                                               out["x12"], out["t"], out.get("X"), out["U"],
+                                               out["near_tie"])
+        return out
+
+    @property
+    def X(self):
+        return self.recover(dense=True)["X"].view(self.n, self.m)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ra_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

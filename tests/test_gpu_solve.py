@@ -1,0 +1,162 @@
+"""GPU price discovery (ra_solve, Algorithm 2 on the device) against the
+FP64 CPU oracle.
+
+At sizes the oracle solves in seconds: the GPU's certified relative duality
+gap meets the tolerance, its bounds bracket the oracle's optimum, and the
+prices agree.  The GPU's certificate is re-checked by the oracle: g at the
+GPU's best prices and the column-scaled utility at the GPU's lower-bound
+prices, both evaluated in FP64 on the CPU.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2104_00282_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ra():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_00282_gb300 import build as B
+    B.build()
+    from paper_2104_00282_gb300 import ra as R
+    R.lib()
+    return R
+
+
+@pytest.fixture(scope="module")
+def oracle():
+    from oracle import oracle as O
+    O.lib()
+    return O
+
+
+def certify(O, prob, P, cap=True):
+    """Oracle-side certificate of the GPU's result (FP64)."""
+    lam = P.prices.cpu().numpy()
+    lam_lb = P.prices_lb.cpu().numpy()
+    g, _, _ = O.dual(prob, lam, cap=cap)
+    lb, _ = O.lower_bound(prob, lam_lb, cap=cap)
+    _, r_lb, U_lb_x = O.dual(prob, lam_lb, cap=cap)
+    if np.all(r_lb <= prob.R):
+        lb = max(lb, U_lb_x)
+    return g, lb, O.rel_gap(g, lb)
+
+
+def price_err(lam, ref):
+    return float(np.max(np.abs(lam - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+@pytest.mark.parametrize("make,tol,fp64", [
+    (lambda: W.config_hetero(n=200_000, m=8, seed=3), 1e-6, False),
+    (lambda: W.config_large(n=200_000, m=32, seed=3), 1e-6, False),
+    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.1), 1e-6, False),
+    (lambda: W.config_plain_small(), 1e-9, True),
+])
+def test_solve_matches_oracle(ra, oracle, make, tol, fp64):
+    prob = make()
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", fp64_jobmath=fp64)
+    info = P.solve(tol=tol, max_evals=800)
+    assert info["status"] == ra.RA_OK, info
+    assert info["rel_gap"] <= tol
+    ref = oracle.solve(prob, tol=min(tol, 1e-8) * 0.1, max_evals=2000)
+    # the GPU's bounds bracket the oracle's optimum
+    slack = 3e-6 if not fp64 else 1e-11
+    scale = max(abs(ref.g), 1.0)
+    assert info["g"] >= ref.U_lb - slack * scale
+    assert info["U_lb"] <= ref.g + slack * scale
+    # the oracle certifies the GPU's prices in FP64
+    g, lb, gap = certify(oracle, prob, P)
+    assert gap <= tol + (2e-6 if not fp64 else 1e-12), (g, lb, gap)
+    # prices: the dual optimum need not be unique (jobs sitting at kinks make g
+    # flat in some directions), so the GPU's prices must be dual-optimal --
+    # g(lambda_gpu) within the tolerance of the oracle's optimum -- and close
+    # to the oracle's where g is strictly convex.
+    assert g <= ref.g + (tol + slack) * scale
+    if not fp64:
+        assert price_err(P.prices.cpu().numpy(), ref.lam) <= 1e-3
+    P.close()
+
+
+def test_graph_and_host_loop_agree_bitwise(ra):
+    prob = W.config_hetero(n=150_000, m=8, seed=4)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    a = P.solve(tol=1e-7, use_graph=True)
+    la = P.prices.cpu().numpy().copy()
+    b = P.solve(tol=1e-7, use_graph=False)
+    lb = P.prices.cpu().numpy().copy()
+    c = P.solve(tol=1e-7, use_graph=True)
+    lc = P.prices.cpu().numpy().copy()
+    P.close()
+    assert a == b == c
+    assert np.array_equal(la, lb) and np.array_equal(la, lc)
+
+
+def test_single_resource_closed_form(ra):
+    n = 50_000
+    rng = np.random.default_rng(1)
+    A = rng.uniform(0.5, 1.0, (n, 1)).astype(np.float32)
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    R = np.array([0.3 * w.astype(np.float64).sum() / 2.0])
+    prob = W.Problem(A, np.zeros(n, np.uint8), w, np.zeros(n, np.float32), R)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    info = P.solve(tol=1e-8)
+    lam = P.prices.item()
+    P.close()
+    assert info["rel_gap"] <= 1e-8
+    assert lam == pytest.approx(w.astype(np.float64).sum() / R[0], rel=1e-6)
+
+
+def test_uncapped_fisher_market_spending(ra):
+    prob = W.random_small(100_000, 6, seed=13, kinds=(0,))
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=False)
+    info = P.solve(tol=1e-6, max_evals=800)
+    lam = P.prices.cpu().numpy()
+    P.close()
+    assert info["status"] == ra.RA_OK, info
+    assert float(lam @ prob.R) == pytest.approx(float(prob.w.astype(np.float64).sum()), rel=1e-5)
+
+
+def test_subgradient_update_converges(ra, oracle):
+    prob = W.config_hetero(n=50_000, m=4, seed=6)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    info = P.solve(tol=1e-2, update="subgradient", max_evals=3000)
+    P.close()
+    assert info["status"] == ra.RA_OK and info["rel_gap"] <= 1e-2
+    ref = oracle.solve(prob, tol=1e-8)
+    assert info["U_lb"] <= ref.g * (1 + 1e-9) + 1e-9 and info["g"] >= ref.U_lb - 1e-6 * abs(ref.U_lb)
+
+
+def test_warm_start_from_optimum_is_fast(ra):
+    prob = W.config_hetero(n=100_000, m=8, seed=7)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    cold = P.solve(tol=1e-6)
+    warm = P.solve(tol=1e-6, lam0=P.prices)
+    P.close()
+    assert warm["evals"] <= max(4, cold["evals"] // 3)
+
+
+def test_history_and_verbose_log(ra):
+    prob = W.paper_code_example(n=100_000, m=4, seed=0)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    info = P.solve(tol=1e-6)
+    h = P.history()
+    lines = P.verbose_log()
+    P.close()
+    assert len(h) == info["evals"]
+    gaps = h[:, 3][np.isfinite(h[:, 3])]
+    assert np.all(np.diff(gaps) <= 1e-15)            # best-so-far gap never increases
+    assert lines[0].startswith("iteration 01 | utility=")
+    assert "Converged" in lines[-1]
+
+
+def test_not_converged_is_reported(ra):
+    prob = W.config_large(n=50_000, m=32, seed=8)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    info = P.solve(tol=1e-14, max_evals=3)
+    P.close()
+    assert info["status"] == ra.RA_ENOTCONV and info["evals"] == 3
