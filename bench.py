@@ -144,11 +144,19 @@ def cpu_baseline(sample_n, seed=0):
     return dt, dt * (N_JOBS / sample_n), O.max_threads(), sol.evals, sol.gap
 
 
+def _sample_size(seconds):
+    """Jobs of the workload the oracle solves in about `seconds` (measured
+    about 2.5 us of host time per job and solve on 16 cores), at least 1e5."""
+    n = int(seconds / 2.5e-6)
+    return int(min(max(n, 100_000), N_JOBS) // 1000 * 1000)
+
+
 def run_reference(args):
     dist, rank, ws = _dist()
     if rank != 0:
         return
-    sample_n = args.cpu_sample
+    # bounded so that the whole --steps/--warmup run ends within about three minutes
+    sample_n = args.cpu_sample or _sample_size(min(20.0, 180.0 / max(args.steps + args.warmup, 1)))
     vals = []
     evals = gap = threads = None
     for k in range(args.warmup + args.steps):
@@ -196,13 +204,13 @@ def run_gpu(args):
     def step():
         return P.solve(tol=TOL, max_evals=args.max_evals)
 
-    for _ in range(args.warmup):
-        info = step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     times, infos = [], []
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            info = step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         for _ in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -265,16 +273,34 @@ def run_gpu(args):
     h2d = prob.A.nbytes + prob.kind.nbytes + prob.w.nbytes + prob.param.nbytes + prob.R.nbytes
     d2h = out.numel() * 8
 
+    # the same workload without the per-job cap (problem as stated with X >= 0 only)
+    P.close()
+    with torch.cuda.stream(stream):
+        Pn = ra.AllocationProblem.from_numpy(prob, dev, stream=stream, job_cap=False)
+    nc_times, nc_info = [], None
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        nc_info = Pn.solve(tol=TOL, max_evals=args.max_evals)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            nc_times.append(e0.elapsed_time(e1))
+    Pn.close()
+    no_cap = {"ms": statistics.median(nc_times), "evals": nc_info["evals"],
+              "rel_gap": nc_info["rel_gap"], "status": nc_info["status"]}
+
     if rank != 0:
-        P.close()
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        dt, scaled, threads, evals, gap = cpu_baseline(args.cpu_sample)
+        sample_n = args.cpu_sample or _sample_size(12.0)
+        dt, scaled, threads, evals, gap = cpu_baseline(sample_n)
         cpu = {"value": scaled, "unit": "ms", "cores": threads, "kind": "oracle",
-               "sample": f"oracle solve of the first {args.cpu_sample} jobs of the workload "
+               "sample": f"oracle solve of the first {sample_n} jobs of the workload "
                          f"(R scaled) took {dt:.0f} ms, {evals} evaluations, gap {gap:.2e}; "
-                         f"scaled x{N_JOBS // args.cpu_sample} to n=1e7 (linear in n)"}
+                         f"scaled x{N_JOBS / sample_n:g} to n=1e7 (linear in n)"}
     evals = [i["evals"] for i in infos]
     launches = sum(2 + 2 * e for e in evals) + 0
     line = {
@@ -297,20 +323,20 @@ def run_gpu(args):
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "no_job_cap": no_cap,
     }
     print(json.dumps(line), flush=True)
-    P.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_JOBS)
     ap.add_argument("--max-evals", type=int, default=400)
-    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="jobs in the oracle sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

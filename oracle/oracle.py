@@ -199,13 +199,51 @@ class _Converged(Exception):
     pass
 
 
+def master_lower_bound(cands, R):
+    """Lower bound from a convex combination of evaluated allocations.
+
+    ``cands`` is a list of (U_k, r_k): the utility of an allocation X^k whose
+    rows each solve the job constraints, and its usage r_k.  For weights
+    theta >= 0, sum theta = 1 with sum_k theta_k r_k <= R, the allocation
+    sum_k theta_k X^k is feasible for problem (e-res-alloc) and, since every
+    u_i is concave, its utility is at least sum_k theta_k U_k.  The best such
+    bound is an LP in theta (solved with scipy HiGHS).  Returns (bound, theta)
+    or (-inf, None) when no combination is feasible."""
+    from scipy.optimize import linprog
+    if not cands:
+        return -np.inf, None
+    U = np.array([c[0] for c in cands], np.float64)
+    Rm = np.array([c[1] for c in cands], np.float64)          # K x m
+    ok = np.isfinite(U) & np.all(np.isfinite(Rm), axis=1)
+    if not ok.any():
+        return -np.inf, None
+    U, Rm = U[ok], Rm[ok]
+    R = np.asarray(R, np.float64)
+    scale = np.where(R > 0, R, 1.0)
+    # the LP solver meets constraints to its tolerance only: tighten the
+    # limits by a margin larger than that tolerance, then verify exactly
+    res = linprog(-U / max(np.abs(U).max(), 1.0), A_ub=(Rm / scale).T,
+                  b_ub=R / scale * (1.0 - 1e-9), A_eq=np.ones((1, len(U))), b_eq=[1.0],
+                  bounds=[(0, None)] * len(U), method="highs",
+                  options=dict(primal_feasibility_tolerance=1e-10))
+    if res.status != 0:
+        return -np.inf, None
+    theta = np.maximum(res.x, 0.0)
+    theta /= theta.sum()
+    if np.any(theta @ Rm > R):
+        return -np.inf, None
+    return float(theta @ U), theta
+
+
 def solve(prob, cap=True, tol=1e-6, max_evals=400, method="hull", nthreads=0, lam0=None,
-          update="lbfgs", lam_floor=None, history=False, repair=True):
+          update="lbfgs", lam_floor=None, history=False, repair=True, master=True,
+          master_window=32):
     """Algorithm 2: evaluate g, q and U(X~) at each price vector, stop when the
     relative duality gap is <= tol, update the prices with L-BFGS (default) or
-    the projected subgradient method.  When the loop ends above ``tol`` and
-    ``repair`` is set, the tie-aware repair of ``repair_lower_bound`` is
-    tried at the best prices."""
+    the projected subgradient method.  With ``master`` the lower bound also
+    uses ``master_lower_bound`` over the last ``master_window`` evaluations.
+    When the loop ends above ``tol`` and ``repair`` is set, the tie-aware
+    repair of ``repair_lower_bound`` is tried at the best prices."""
     m = prob.m
     lam = init_prices(prob, cap, nthreads) if lam0 is None else np.asarray(lam0, np.float64).copy()
     if lam_floor is None:
@@ -217,11 +255,23 @@ def solve(prob, cap=True, tol=1e-6, max_evals=400, method="hull", nthreads=0, la
               hist=[])
     t0 = time.perf_counter()
 
+    cands = []
+    R = np.asarray(prob.R, np.float64)
+
     def evaluate(x):
         x = np.maximum(np.asarray(x, np.float64), lam_floor)
-        g, r, _ = dual(prob, x, cap, method, nthreads)
+        g, r, Ux = dual(prob, x, cap, method, nthreads)
         lb, s = lower_bound(prob, x, cap, method, nthreads, r=r)
         st["evals"] += 1
+        if master:
+            cands.append((Ux, r.copy()))
+            cands.append((lb, np.minimum(r, R)))
+            if len(cands) > 2 * master_window:
+                del cands[:2]
+            if st["evals"] >= 2 and rel_gap(min(st["g"], g), max(st["lb"], lb)) > tol:
+                mlb, _ = master_lower_bound(cands, R)
+                if mlb > lb:
+                    lb = mlb
         if g < st["g"]:
             st["g"], st["lam"] = g, x.copy()
         if lb > st["lb"]:

@@ -54,6 +54,12 @@ struct SolverState {
     double U_best;
     double gap;
     double sg_a0;         // subgradient step scale
+    double g_bt;          // best trial value of the current line search
+    double last_step;     // norm of the last accepted price step
+    int32_t sg_pending;   // the evaluation in flight is a fallback subgradient step
+    int32_t pad2_;
+    double lam_bt[RA_MAX_M];
+    double q_bt[RA_MAX_M];
     double lam_cur[RA_MAX_M];
     double q_cur[RA_MAX_M];
     double d[RA_MAX_M];

@@ -81,6 +81,9 @@ __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const d
         st->U_best = -__longlong_as_double(0x7ff0000000000000ll);
         st->gap = __longlong_as_double(0x7ff0000000000000ll);
         st->step = 1.0;
+        st->g_bt = __longlong_as_double(0x7ff0000000000000ll);
+        st->last_step = 0.05 * lmax;
+        st->sg_pending = 0;
         *pingpong = 0;
         *lag_on = 0;
     }
@@ -133,6 +136,117 @@ __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
         }
     }
     if (active) st->d[j] = d;
+}
+
+// Store the pair (s, y) = (lambda_t - lambda_cur, q_t - q_cur) when it has
+// positive curvature, then make lambda_t the current point.
+__device__ void accept_point(SolverState *st, int j, bool active, double g_t, double q_t,
+                             double lam_t, bool store_pair)
+{
+    if (store_pair && st->phase == 1) {
+        const double sv = active ? lam_t - st->lam_cur[j] : 0.0;
+        const double yv = active ? q_t - st->q_cur[j] : 0.0;
+        const double sy = wsum(sv * yv);
+        const double ss = wsum(sv * sv), yy = wsum(yv * yv);
+        if (sy > 1e-12 * sqrt(ss * yy) && sy > 0.0) {
+            const int idx = st->mem_head;
+            if (active) {
+                st->S[idx][j] = sv;
+                st->Y[idx][j] = yv;
+            }
+            __syncwarp();
+            if (j == 0) {
+                st->rho[idx] = 1.0 / sy;
+                st->mem_head = (idx + 1) % st->mem;
+                st->mem_count = min(st->mem_count + 1, st->mem);
+            }
+        }
+        if (j == 0) st->last_step = sqrt(ss);
+    }
+    __syncwarp();
+    if (active) {
+        st->lam_cur[j] = lam_t;
+        st->q_cur[j] = q_t;
+    }
+    if (j == 0) {
+        if (st->phase == 1) st->k = st->k + 1;
+        st->g_cur = g_t;
+        st->phase = 1;
+        st->ls_iter = 0;
+        st->step = 1.0;
+        st->g_bt = __longlong_as_double(0x7ff0000000000000ll);
+        st->sg_pending = 0;
+    }
+    __syncwarp();
+}
+
+// Projected L-BFGS step control.  A trial is accepted on the Armijo condition
+// g_t <= g_cur + 1e-4 q_cur^T (lambda_t - lambda_cur); otherwise the step is
+// cut by safeguarded quadratic interpolation (to [0.1, 0.5] of itself).  After
+// 12 cuts the best decreasing trial is taken; when no trial decreased g (a
+// kink of g: q_cur is only one subgradient) the memory is cleared and a
+// projected subgradient step of half the last step length is taken without a
+// decrease test -- the method's fallback (Section 5).  The best g and lower
+// bound are tracked separately, so non-monotone steps lose nothing.
+__device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double g_t, double q_t,
+                             double lam_t)
+{
+    const bool fin = isfinite(g_t);
+    if (st->sg_pending && !fin) {
+        if (j == 0) st->step = 0.25 * st->step;   // shorten the fallback step
+    } else if (st->phase == 0 || st->sg_pending) {
+        accept_point(st, j, active, g_t, q_t, lam_t, st->phase == 1);
+        lbfgs_direction(st, j, m, active);
+    } else {
+        const double dl = active ? lam_t - st->lam_cur[j] : 0.0;
+        const double slope = wsum(active ? st->q_cur[j] * dl : 0.0);
+        const bool armijo = fin && g_t <= st->g_cur + 1e-4 * slope;
+        if (armijo) {
+            accept_point(st, j, active, g_t, q_t, lam_t, true);
+            lbfgs_direction(st, j, m, active);
+        } else {
+            if (fin && g_t < st->g_bt) {
+                if (active) {
+                    st->lam_bt[j] = lam_t;
+                    st->q_bt[j] = q_t;
+                }
+                __syncwarp();
+                if (j == 0) st->g_bt = g_t;
+            }
+            __syncwarp();
+            const int iter = st->ls_iter + 1;
+            if (iter < 12) {
+                if (j == 0) {
+                    double cut = 0.1;
+                    const double den = g_t - st->g_cur - slope;
+                    if (fin && den > 0.0 && slope < 0.0) cut = fmin(0.5, fmax(0.1, -slope / (2.0 * den)));
+                    st->step = st->step * cut;
+                    st->ls_iter = iter;
+                }
+            } else if (st->g_bt < st->g_cur) {
+                const double lb = active ? st->lam_bt[j] : 0.0, qb = active ? st->q_bt[j] : 0.0;
+                accept_point(st, j, active, st->g_bt, qb, lb, true);
+                lbfgs_direction(st, j, m, active);
+            } else {
+                // kink: subgradient fallback from the current point
+                const double qn = sqrt(wsum(active ? st->q_cur[j] * st->q_cur[j] : 0.0));
+                const double len = 0.5 * st->last_step;
+                if (active) st->d[j] = qn > 0.0 ? -st->q_cur[j] * (len / qn) : 0.0;
+                if (j == 0) {
+                    st->ls_fail = st->ls_fail + 1;
+                    st->mem_count = 0;
+                    st->mem_head = 0;
+                    st->ls_iter = 0;
+                    st->step = 1.0;
+                    st->last_step = len;
+                    st->sg_pending = 1;
+                    st->g_bt = __longlong_as_double(0x7ff0000000000000ll);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (active) st->lam_trial[j] = fmax(st->lam_cur[j] + st->step * st->d[j], st->lam_floor);
 }
 
 // One update after the evaluation of st->lam_trial (results in *ev).
@@ -204,8 +318,8 @@ __global__ void __launch_bounds__(32)
     } else if (evals >= st->max_evals) {
         done = true;
         status = RA_ENOTCONV;
-    } else if (!(g_t == g_t)) {
-        done = true;
+    } else if (!isfinite(g_t) && st->phase == 0) {
+        done = true;             // the starting prices already give an unbounded dual
         status = RA_EUNBOUNDED;
     }
 
@@ -225,76 +339,7 @@ __global__ void __launch_bounds__(32)
             }
             if (j == 0) st->k = st->k + 1;
         } else {
-            bool accept;
-            if (st->phase == 0) {
-                accept = true;
-            } else {
-                const double dl = active ? lam_t - st->lam_cur[j] : 0.0;
-                const double slope = wsum(active ? st->q_cur[j] * dl : 0.0);
-                accept = g_t <= st->g_cur + 1e-4 * slope;
-            }
-            if (accept) {
-                if (st->phase == 1) {
-                    const double sv = active ? lam_t - st->lam_cur[j] : 0.0;
-                    const double yv = active ? q_t - st->q_cur[j] : 0.0;
-                    const double sy = wsum(sv * yv);
-                    const double ss = wsum(sv * sv), yy = wsum(yv * yv);
-                    if (sy > 1e-12 * sqrt(ss * yy) && sy > 0.0) {
-                        const int idx = st->mem_head;
-                        if (active) {
-                            st->S[idx][j] = sv;
-                            st->Y[idx][j] = yv;
-                        }
-                        __syncwarp();
-                        if (j == 0) {
-                            st->rho[idx] = 1.0 / sy;
-                            st->mem_head = (idx + 1) % st->mem;
-                            st->mem_count = min(st->mem_count + 1, st->mem);
-                        }
-                    }
-                    if (j == 0) st->k = st->k + 1;
-                }
-                if (active) {
-                    st->lam_cur[j] = lam_t;
-                    st->q_cur[j] = q_t;
-                }
-                if (j == 0) {
-                    st->g_cur = g_t;
-                    st->phase = 1;
-                    st->ls_iter = 0;
-                    st->step = 1.0;
-                }
-                __syncwarp();
-                lbfgs_direction(st, j, m, active);
-                __syncwarp();
-            } else {
-                // backtrack (halve the step); after 30 halvings restart from a
-                // scaled gradient step with the memory cleared
-                __syncwarp();
-                if (j == 0) {
-                    st->ls_iter = st->ls_iter + 1;
-                    st->step = 0.5 * st->step;
-                }
-                __syncwarp();
-                if (st->ls_iter > 30) {
-                    if (j == 0) {
-                        st->ls_fail = st->ls_fail + 1;
-                        st->mem_count = 0;
-                        st->mem_head = 0;
-                        st->ls_iter = 0;
-                        st->step = 1.0;
-                    }
-                    __syncwarp();
-                    lbfgs_direction(st, j, m, active);
-                    __syncwarp();
-                    if (j == 0 && st->ls_fail > 8) {
-                        st->done = 1;
-                        st->status = RA_ENOTCONV;
-                    }
-                }
-            }
-            __syncwarp();
-            if (active) st->lam_trial[j] = fmax(st->lam_cur[j] + st->step * st->d[j], st->lam_floor);
+            lbfgs_update(st, j, m, active, g_t, q_t, lam_t);
         }
     }
     __syncwarp();

@@ -430,3 +430,29 @@ def test_repaired_allocation_is_feasible_and_below_dual(oracle):
     assert lb <= sol.g + 1e-12 * abs(sol.g)
     assert lb >= plain
     assert oracle.rel_gap(sol.g, lb) < 0.1 * oracle.rel_gap(sol.g, plain)
+
+
+def test_master_bound_is_feasible_and_valid(oracle):
+    """A convex combination of subproblem allocations that meets r <= R is
+    feasible, and by concavity of the u_i its utility is at least the
+    combination of their utilities: the master bound never exceeds the
+    optimum, and it closes the gap where column scaling stalls at kinks."""
+    p = W.random_small(20_000, 5, seed=8, r_scale=0.1)
+    ref = oracle.solve(p, tol=1e-10, max_evals=600)
+    rng = np.random.default_rng(0)
+    lams = [ref.lam * rng.uniform(0.97, 1.03, p.m) for _ in range(24)]
+    cands, allocs = [], []
+    for lam in lams:
+        X, rec = oracle.allocation(p, lam)
+        U = oracle.utility_of(p, (p.A.astype(np.float64) * X).sum(1))
+        cands.append((U, X.sum(0)))
+        allocs.append(X)
+    lb, theta = oracle.master_lower_bound(cands, p.R)
+    assert np.isfinite(lb)
+    Xbar = sum(t * X for t, X in zip(theta, allocs))
+    assert np.all(Xbar.sum(0) <= p.R * (1 + 1e-12))
+    U_bar = oracle.utility_of(p, (p.A.astype(np.float64) * Xbar).sum(1))
+    assert U_bar >= lb - 1e-9 * abs(lb)                   # Jensen
+    assert lb <= ref.g + 1e-9 * abs(ref.g)                # weak duality
+    best_single = max(oracle.lower_bound(p, lam)[0] for lam in lams)
+    assert lb >= best_single - 1e-9 * abs(lb)
