@@ -34,8 +34,8 @@ METRIC = "time to 1e-6 rel. duality gap at n=1e7,m=32; dual-eval HBM GB/s vs pea
 N_JOBS, M_RES, TOL = 10_000_000, 32, 1e-6
 WORKLOAD = ("large single problem: n=1e7 jobs, m=32 resources, A_ij = s_j exp(0.75 z), "
             "s_j~U[0.25,8], FP32 row-major (1.28 GB); utilities 40% log, 40% power p~U[0.2,0.8], "
-            "20% linear with cap T~U[1,10]; w~U[0.5,2]; R_j~U[0.05,0.3] n; per-job cap 1^T x_i <= 1; "
-            "cold start (Eq. e-initialization) to 1e-6 relative duality gap")
+            "20% linear with cap T~U[1,10]; w~U[0.5,2]; R_j~U[0.05,0.3] n; maximize sum_i u_i(a_i^T x_i) "
+            "over X >= 0 with X^T 1 <= R; cold start (Eq. e-initialization) to 1e-6 relative duality gap")
 
 
 def _dist():
@@ -131,7 +131,7 @@ def ncu_traffic():
     return d.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(sample_n, seed=0):
+def cpu_baseline(sample_n, seed=0, cap=False):
     """Oracle solve (FP64, OpenMP, scipy L-BFGS-B) on the first sample_n jobs
     of the workload with R scaled to the sample; returns (ms for the sample,
     ms scaled linearly to n = 1e7, threads, evals)."""
@@ -139,15 +139,16 @@ def cpu_baseline(sample_n, seed=0):
     from paper_2104_00282_gb300 import workloads as W
     prob = W.config_large(n=sample_n, m=M_RES, seed=seed)
     t0 = time.perf_counter()
-    sol = O.solve(prob, tol=TOL, max_evals=400)
+    sol = O.solve(prob, cap=cap, tol=TOL, max_evals=400)
     dt = (time.perf_counter() - t0) * 1e3
     return dt, dt * (N_JOBS / sample_n), O.max_threads(), sol.evals, sol.gap
 
 
-def _sample_size(seconds):
-    """Jobs of the workload the oracle solves in about `seconds` (measured
-    about 2.5 us of host time per job and solve on 16 cores), at least 1e5."""
-    n = int(seconds / 2.5e-6)
+def _sample_size(seconds, cap):
+    """Jobs of the workload the oracle solves in about `seconds` on 16 host
+    cores: measured about 2.5 us per job and solve with the per-job cap (about
+    ten evaluations) and about 60 us without it (a few hundred); >= 1e5."""
+    n = int(seconds / (2.5e-6 if cap else 6e-5))
     return int(min(max(n, 100_000), N_JOBS) // 1000 * 1000)
 
 
@@ -156,11 +157,12 @@ def run_reference(args):
     if rank != 0:
         return
     # bounded so that the whole --steps/--warmup run ends within about three minutes
-    sample_n = args.cpu_sample or _sample_size(min(20.0, 180.0 / max(args.steps + args.warmup, 1)))
+    sample_n = args.cpu_sample or _sample_size(min(20.0, 180.0 / max(args.steps + args.warmup, 1)),
+                                               args.job_cap)
     vals = []
     evals = gap = threads = None
     for k in range(args.warmup + args.steps):
-        _, scaled, threads, evals, gap = cpu_baseline(sample_n, seed=0)
+        _, scaled, threads, evals, gap = cpu_baseline(sample_n, seed=0, cap=args.job_cap)
         if k >= args.warmup:
             vals.append(scaled)
     v = statistics.median(vals)
@@ -168,7 +170,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_JOBS, "m": M_RES, "tol_rel": TOL},
+        "config": {"workload": WORKLOAD, "n": N_JOBS, "m": M_RES, "tol_rel": TOL,
+                   "job_cap": args.job_cap},
         "cpu_baseline": {"value": v, "unit": "ms", "cores": threads, "kind": "oracle",
                          "sample": f"oracle solve of the first {sample_n} jobs (R scaled), "
                                    f"{evals} evaluations to gap {gap:.2e}, time scaled x{N_JOBS // sample_n} "
@@ -197,12 +200,13 @@ def run_gpu(args):
     prob = W.config_large(n=n, m=m, seed=rank)
     stream = torch.cuda.Stream()
     dev = torch.device("cuda", local)
+    cap = args.job_cap
+    use_graph = not args.no_graph
     with torch.cuda.stream(stream):
-        P = ra.AllocationProblem.from_numpy(prob, dev, stream=stream)
-        lam = torch.empty(m, dtype=torch.float64, device=dev)
+        P = ra.AllocationProblem.from_numpy(prob, dev, stream=stream, job_cap=cap)
 
     def step():
-        return P.solve(tol=TOL, max_evals=args.max_evals)
+        return P.solve(tol=TOL, max_evals=args.max_evals, use_graph=use_graph)
 
     times, infos = [], []
     with ClockSampler(local) as clk:
@@ -262,8 +266,8 @@ def run_gpu(args):
         with torch.cuda.stream(stream):
             Q = ra.AllocationProblem(hA.to(dev, non_blocking=True), hk.to(dev, non_blocking=True),
                                      hw.to(dev, non_blocking=True), hp.to(dev, non_blocking=True),
-                                     hR.to(dev, non_blocking=True), stream=stream)
-            Q.solve(tol=TOL, max_evals=args.max_evals)
+                                     hR.to(dev, non_blocking=True), stream=stream, job_cap=cap)
+            Q.solve(tol=TOL, max_evals=args.max_evals, use_graph=use_graph)
             out = Q.prices.to("cpu", non_blocking=False)
         Q.close()
         del Q
@@ -273,30 +277,31 @@ def run_gpu(args):
     h2d = prob.A.nbytes + prob.kind.nbytes + prob.w.nbytes + prob.param.nbytes + prob.R.nbytes
     d2h = out.numel() * 8
 
-    # the same workload without the per-job cap (problem as stated with X >= 0 only)
+    # the same workload in the other mode: with / without the paper's per-job
+    # time cap 1^T x_i <= 1 (problem (e-res-alloc))
     P.close()
     with torch.cuda.stream(stream):
-        Pn = ra.AllocationProblem.from_numpy(prob, dev, stream=stream, job_cap=False)
-    nc_times, nc_info = [], None
+        Po = ra.AllocationProblem.from_numpy(prob, dev, stream=stream, job_cap=not cap)
+    o_times, o_info = [], None
     for k in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        nc_info = Pn.solve(tol=TOL, max_evals=args.max_evals)
+        o_info = Po.solve(tol=TOL, max_evals=args.max_evals, use_graph=use_graph)
         e1.record(stream)
         e1.synchronize()
         if k > 0:
-            nc_times.append(e0.elapsed_time(e1))
-    Pn.close()
-    no_cap = {"ms": statistics.median(nc_times), "evals": nc_info["evals"],
-              "rel_gap": nc_info["rel_gap"], "status": nc_info["status"]}
+            o_times.append(e0.elapsed_time(e1))
+    Po.close()
+    other = {"ms": statistics.median(o_times), "evals": o_info["evals"],
+             "rel_gap": o_info["rel_gap"], "status": o_info["status"]}
 
     if rank != 0:
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        sample_n = args.cpu_sample or _sample_size(12.0)
-        dt, scaled, threads, evals, gap = cpu_baseline(sample_n)
+        sample_n = args.cpu_sample or _sample_size(12.0, cap)
+        dt, scaled, threads, evals, gap = cpu_baseline(sample_n, cap=cap)
         cpu = {"value": scaled, "unit": "ms", "cores": threads, "kind": "oracle",
                "sample": f"oracle solve of the first {sample_n} jobs of the workload "
                          f"(R scaled) took {dt:.0f} ms, {evals} evaluations, gap {gap:.2e}; "
@@ -308,6 +313,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m": m, "tol_rel": TOL,
+                   "job_cap": cap, "cuda_graph": use_graph,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs 1.37 GB per evaluation > 126 MB L2; no flush needed",
                    "precision": "per-job math f32; reductions, dual value, price update f64"},
@@ -316,14 +322,15 @@ def run_gpu(args):
                   "step_ms_all": times},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(),
-                     "kernel": "dual_tma_kernel (ra_eval_dual, no lower-bound record)",
+                     "kernel": f"dual_tma_kernel, {'with' if cap else 'no'} per-job cap "
+                               "(ra_eval_dual, no lower-bound record)",
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": eval_ms,
                      "peak_source": f"{peak_src} hbm_gbs (burst copy)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "no_job_cap": no_cap,
+        ("no_job_cap" if cap else "with_job_cap"): other,
     }
     print(json.dumps(line), flush=True)
 
@@ -338,6 +345,10 @@ def main():
     ap.add_argument("--max-evals", type=int, default=400)
     ap.add_argument("--cpu-sample", type=int, default=0, help="jobs in the oracle sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--job-cap", action="store_true",
+                    help="headline with the paper's per-job cap 1^T x_i <= 1 (default: X >= 0 only)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven solver loop (same kernels; lets ncu see every launch)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -127,6 +127,8 @@ typedef struct {
     int32_t update;       /* 0 = projected L-BFGS, 1 = projected subgradient (Section 5)        */
     int32_t use_graph;    /* 1 = run the loop as one CUDA graph with a device-side while node   */
     double lam_floor;     /* lower bound on prices; <0 selects 0 (cap) / 1e-12 max(lambda^1)    */
+    int32_t master_lb;    /* 1 = also bound U* by the master LP over evaluated allocations      */
+    int32_t pad_;
 } ra_solve_opts;
 
 typedef struct {
@@ -162,6 +164,19 @@ void ra_solve_opts_default(ra_solve_opts *opts);
  */
 ra_status ra_solve(ra_problem *prob, const ra_solve_opts *opts, const double *lambda0,
                    double *lambda_out, double *lambda_lb, ra_solve_info *info);
+
+/*
+ * ra_solve_certificate -- the allocation behind the lower bound U_lb of the
+ * last ra_solve, as a convex combination of subproblem allocations: entry k
+ * has weight theta[k] (summing to 1), prices lam[k*m .. k*m+m) and scaled[k]
+ * = 1 when that allocation was column-scaled to X diag(min(1, R/r)) (Section
+ * 5) before mixing.  The mixture meets sum_i x_i <= R, and since every u_i is
+ * concave its utility is at least U_lb.  theta, scaled: host arrays of
+ * RA_MAX_CERT entries; lam: host array of RA_MAX_CERT * m doubles.  Returns
+ * the number of entries written, or -1 on error.  Synchronises.
+ */
+#define RA_MAX_CERT 64
+int32_t ra_solve_certificate(ra_problem *prob, double *theta, double *lam, int32_t *scaled);
 
 /*
  * ra_solve_history -- per-evaluation log of the last ra_solve (the paper's

@@ -98,6 +98,8 @@ void ra_solve_opts_default(ra_solve_opts *o)
     o->update = 0;
     o->use_graph = 1;
     o->lam_floor = -1.0;
+    o->master_lb = 1;
+    o->pad_ = 0;
 }
 
 ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t *kind,
@@ -274,6 +276,15 @@ int32_t ra_solve_history(ra_problem *p, double *hist, int32_t cap)
         return -1;
     }
     return ra::solve_history(p, hist, cap);
+}
+
+int32_t ra_solve_certificate(ra_problem *p, double *theta, double *lam, int32_t *scaled)
+{
+    if (!p || !theta || !lam || !scaled) {
+        fail(RA_EINVAL, "NULL argument");
+        return -1;
+    }
+    return ra::solve_certificate(p, theta, lam, scaled);
 }
 
 ra_status ra_recover_primal(ra_problem *p, const double *lambda, int32_t *jstar, int32_t *j12,

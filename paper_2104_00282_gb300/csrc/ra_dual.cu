@@ -253,16 +253,32 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
         for (int step = 0; step < MT; ++step) {
             t = topt<Real>(kind, w, p, alpha, aP, aQ);
             if (t < aQ) break;
-            Real bdl = Real(1), bda = Real(0);
-            int kn = -1;
+            // next vertex: minimum slope (lam_k - lQ)/(a_k - aQ) over a_k > aQ,
+            // compared division-free, in four independent chains
+            Real cdl[4] = {Real(1), Real(1), Real(1), Real(1)};
+            Real cda[4] = {Real(0), Real(0), Real(0), Real(0)};
+            int ckn[4] = {-1, -1, -1, -1};
 #pragma unroll
             for (int k = 0; k < MT; ++k) {
                 const Real da = a[k] - aQ;
                 const Real dl = lam[k] - lQ;
-                if (da > Real(0) && dl * bda < bdl * da) {
-                    bdl = dl;
-                    bda = da;
-                    kn = k;
+                if (da > Real(0) && dl * cda[k & 3] < cdl[k & 3] * da) {
+                    cdl[k & 3] = dl;
+                    cda[k & 3] = da;
+                    ckn[k & 3] = k;
+                }
+            }
+            Real bdl = cdl[0], bda = cda[0];
+            int kn = ckn[0];
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                if (ckn[c] < 0) continue;
+                const Real lhs = cdl[c] * bda, rhs = bdl * cda[c];
+                if (kn < 0 || lhs < rhs ||
+                    (lhs == rhs && colof<MT>(ckn[c], rot) < colof<MT>(kn, rot))) {
+                    bdl = cdl[c];
+                    bda = cda[c];
+                    kn = ckn[c];
                 }
             }
             if (kn < 0) {  // aQ = max_j a_j: right end of the domain
@@ -299,6 +315,10 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
     }
 }
 
+template <int MT, typename Real>
+__device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int lane, bool grouped,
+                                            double &racc);
+
 // Warp-cooperative r accumulation: each lane's `row` (m entries of shared
 // memory that the lane alone owns) becomes its dense x_i; the 32 x m block is
 // then summed column-wise in a fixed order.  `racc` of lane c (< m) gains the
@@ -322,19 +342,30 @@ __device__ __forceinline__ void warp_rsum(Real *warp_rows, int m, int lane, bool
     if (s.cP >= 0) row[s.cP] = s.xP;
     if (s.cQ >= 0) row[s.cQ] = s.xQ;
     __syncwarp();
+    warp_colsum<MT, Real>(warp_rows, m, lane, grouped, racc);
+}
+
+// Column sums of a warp's 32 x m block of shared memory, in a fixed order with
+// four independent partial sums; lane c (< m) adds column c's total to racc.
+template <int MT, typename Real>
+__device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int lane, bool grouped,
+                                            double &racc)
+{
     if (grouped) {
         constexpr int G = 32 / MT;
         const int c = lane % MT, g = lane / MT;
-        Real cs = Real(0);
+        Real cs[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-        for (int k = 0; k < MT; ++k) cs += warp_rows[(g + k * G) * MT + c];
+        for (int k = 0; k < MT; ++k) cs[k & 3] += warp_rows[(g + k * G) * MT + c];
+        Real t = (cs[0] + cs[1]) + (cs[2] + cs[3]);
 #pragma unroll
-        for (int off = MT; off < 32; off <<= 1) cs += __shfl_xor_sync(kFull, cs, off);
-        if (g == 0) racc += static_cast<double>(cs);
+        for (int off = MT; off < 32; off <<= 1) t += __shfl_xor_sync(kFull, t, off);
+        if (g == 0) racc += static_cast<double>(t);
     } else if (lane < m) {
-        Real cs = Real(0);
-        for (int r = 0; r < 32; ++r) cs += warp_rows[r * m + lane];
-        racc += static_cast<double>(cs);
+        Real cs[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) cs[r & 3] += warp_rows[r * m + lane];
+        racc += static_cast<double>((cs[0] + cs[1]) + (cs[2] + cs[3]));
     }
     __syncwarp();
 }
@@ -348,10 +379,11 @@ __device__ __forceinline__ double warp_sum_d(double v)
 
 // Block stage + grid stage: per-thread FP64 values -> per-block partials
 // (fixed warp order) -> the last CTA to finish sums the partials in block
-// order and writes the EvalOut slots.  red is kWarps x kPartW shared doubles.
-__device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, double racc,
-                                    int m, bool lane_owns_col, const DualParams &P,
-                                    double (*red)[kPartW])
+// order.  Returns true in that CTA only, where red[0][0 .. m+4) then holds the
+// totals (h, U(X), lagged U_lb, spare, r_0..r_{m-1}).  red is kWarps x kPartW.
+__device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc, int m,
+                            bool lane_owns_col, double *partials, unsigned *ticket,
+                            double (*red)[kPartW])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ int is_last;
@@ -369,20 +401,31 @@ __device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, dou
     if (tid < m + 4) {
         double v = 0.0;
         for (int w = 0; w < kWarps; ++w) v += red[w][tid];
-        P.partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
+        partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(P.ticket, 1u) == gridDim.x - 1);
+    if (tid == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!is_last) return;
+    if (!is_last) return false;
     __threadfence();
     if (tid < m + 4) {
         double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&P.partials[static_cast<size_t>(b) * kPartW + tid]);
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[static_cast<size_t>(b) * kPartW + tid]);
         red[0][tid] = v;
     }
+    if (tid == 0) *ticket = 0u;  // ready for the next launch
     __syncthreads();
+    return true;
+}
+
+// Dual outputs (Section 3): g = lambda^T R + sum h_i, q = R - r.
+__device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, double racc,
+                                    int m, bool lane_owns_col, const DualParams &P,
+                                    double (*red)[kPartW])
+{
+    if (!grid_reduce(hsum, uxsum, lbsum, racc, m, lane_owns_col, P.partials, P.ticket, red)) return;
+    const int tid = threadIdx.x;
     if (tid < m) {
         P.out->r[tid] = red[0][4 + tid];
         P.out->q[tid] = P.R[tid] - red[0][4 + tid];
@@ -394,7 +437,6 @@ __device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, dou
         P.out->g = lr + red[0][0];
         P.out->Ux = red[0][1];
         P.out->Ulb_prev = red[0][2];
-        *P.ticket = 0u;  // ready for the next launch
     }
 }
 
@@ -406,8 +448,122 @@ struct StageLayout {
     static __host__ __device__ size_t bytes(int m) { return a_bytes(m) + kTile * 9; }
 };
 
-// Main streaming kernel, FP32 per-job arithmetic.  Full 256-job tiles come in
-// through the TMA ring; the ragged tail (n mod 256 jobs) is read directly.
+// Per-job stream over this CTA's share of the jobs.  Full 256-job tiles come
+// in through a ring of `stages` shared-memory buffers filled by 1-D bulk TMA
+// copies (one elected thread issues A's rows, w, param and kind of a tile and
+// arms the stage's mbarrier with the byte count); the ragged tail (n mod 256
+// jobs) is handled by one CTA from global memory.  For every job the callee
+// receives job(i, valid, row, kind, w, p, warp_rows): row points at the job's
+// m efficiencies in shared memory (nullptr in the tail), warp_rows at the 32 x
+// m block of rows the calling warp owns (tile rows or idle stage-0 space),
+// which the callee may overwrite once it has read its own row.  All 256
+// threads call job for every tile, valid or not, so warp collectives work.
+// Returns false if a bounded wait gave up (the status word is then set).
+template <int MT, class Job>
+__device__ bool stream_jobs(const float *A, const float *W, const float *Par, const uint8_t *Kind,
+                            long long n, int m, int stages, long long num_full,
+                            unsigned char *smem, uint64_t *bars, int *status, Job &&job)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t a_bytes = StageLayout<MT>::a_bytes(m);
+    const size_t st_bytes = StageLayout<MT>::bytes(m);
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const long long G = gridDim.x;
+    const long long n_my = (num_full > blockIdx.x) ? (num_full - blockIdx.x + G - 1) / G : 0;
+    auto issue = [&](long long it) {
+        if (it >= n_my) return;
+        const long long tile = blockIdx.x + it * G;
+        const int st = static_cast<int>(it % stages);
+        unsigned char *base = smem + st * st_bytes;
+        const long long j0 = tile * kTile;
+        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
+        bulk_load(base, A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
+        bulk_load(base + a_bytes, W + j0, kTile * 4, &bars[st]);
+        bulk_load(base + a_bytes + kTile * 4, Par + j0, kTile * 4, &bars[st]);
+        bulk_load(base + a_bytes + kTile * 8, Kind + j0, kTile, &bars[st]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < stages; ++s) issue(s);
+
+    for (long long it = 0; it < n_my; ++it) {
+        const int st = static_cast<int>(it % stages);
+        const uint32_t parity = static_cast<uint32_t>((it / stages) & 1);
+        const bool ok = mbar_wait_bounded(&bars[st], parity);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(status, kStatusTimeout);
+                // let copies already in flight land before the CTA exits (bounded)
+                for (long long it2 = it; it2 < n_my && it2 < it + stages; ++it2)
+                    (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1));
+            }
+            __syncthreads();
+            return false;
+        }
+        unsigned char *base = smem + st * st_bytes;
+        float *a_s = reinterpret_cast<float *>(base);
+        const float *w_s = reinterpret_cast<const float *>(base + a_bytes);
+        const float *p_s = reinterpret_cast<const float *>(base + a_bytes + kTile * 4);
+        const uint8_t *k_s = base + a_bytes + kTile * 8;
+        const long long i = (blockIdx.x + it * G) * kTile + tid;
+        job(i, true, a_s + tid * m, static_cast<int>(k_s[tid]), w_s[tid], p_s[tid],
+            a_s + warp * 32 * m);
+        __syncthreads();  // stage fully consumed
+        if (tid == 0) {
+            fence_proxy_async();
+            issue(it + stages);
+        }
+    }
+    // ragged tail: jobs [num_full * 256, n), one CTA, direct loads
+    const long long tail0 = num_full * kTile;
+    if (tail0 < n && blockIdx.x == static_cast<unsigned>(num_full % G)) {
+        const long long i = tail0 + tid;
+        const bool valid = i < n;
+        float *scratch = reinterpret_cast<float *>(smem);  // stage 0 is idle now
+        job(i, valid, nullptr, valid ? static_cast<int>(Kind[i]) : RA_U_LINCAP,
+            valid ? W[i] : 1.0f, valid ? Par[i] : 0.0f, scratch + warp * 32 * m);
+    }
+    return true;
+}
+
+// Load job i's efficiencies into register slots (slot k = column colof(k, rot)).
+template <int MT>
+__device__ __forceinline__ void load_row(float (&a)[MT], const float *row, const float *A,
+                                         long long i, bool valid, int m, bool grouped, int rot)
+{
+    constexpr int C = MT / 4;
+    if (row != nullptr && grouped) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float4 v = reinterpret_cast<const float4 *>(row)[(c + rot) & (C - 1)];
+            a[4 * c + 0] = v.x;
+            a[4 * c + 1] = v.y;
+            a[4 * c + 2] = v.z;
+            a[4 * c + 3] = v.w;
+        }
+    } else if (row != nullptr) {
+#pragma unroll
+        for (int k = 0; k < MT; ++k) a[k] = k < m ? row[k] : 0.0f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            const int c = colof<MT>(k, rot);
+            a[k] = (valid && c < m) ? __ldg(&A[i * m + c]) : 0.0f;
+        }
+    }
+}
+
+template <int MT>
+__device__ __forceinline__ unsigned char *align128(unsigned char *p)
+{
+    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 127) &
+                                             ~static_cast<uintptr_t>(127));
+}
+
+// Main streaming kernel, FP32 per-job arithmetic (Sections 3 and 4).
 template <int MT, bool CAP, bool LAG, bool REC>
 __global__ void __launch_bounds__(kTile, 2)
     dual_tma_kernel(DualParams P, int stages, long long num_full)
@@ -420,7 +576,7 @@ __global__ void __launch_bounds__(kTile, 2)
 
     if (P.skip != nullptr && *P.skip != 0) return;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int m = P.m;
     const bool grouped = (m == MT);
     const float2 *lbt_prev = P.lbt_prev;
@@ -437,21 +593,12 @@ __global__ void __launch_bounds__(kTile, 2)
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
     constexpr int C = MT / 4;
     const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~static_cast<uintptr_t>(127));
-    const size_t a_bytes = StageLayout<MT>::a_bytes(m);
-    const size_t st_bytes = StageLayout<MT>::bytes(m);
 
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<float>(P.lam[tid]) : Fn<float>::inf();
         s_s[tid] = (LAG && lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
     }
-    if (tid == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
     __syncthreads();
-
     float lam_r[MT], mu_r[MT];
 #pragma unroll
     for (int k = 0; k < MT; ++k) {
@@ -460,30 +607,21 @@ __global__ void __launch_bounds__(kTile, 2)
         mu_r[k] = inv_price<float>(lam_s[c]);
     }
 
-    const long long G = gridDim.x;
-    const long long n_my = (num_full > blockIdx.x) ? (num_full - blockIdx.x + G - 1) / G : 0;
-
-    auto issue = [&](long long it) {
-        if (it >= n_my) return;
-        const long long tile = blockIdx.x + it * G;
-        const int st = static_cast<int>(it % stages);
-        unsigned char *base = smem + st * st_bytes;
-        const long long j0 = tile * kTile;
-        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
-        bulk_load(base, P.A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
-        bulk_load(base + a_bytes, P.w + j0, kTile * 4, &bars[st]);
-        bulk_load(base + a_bytes + kTile * 4, P.param + j0, kTile * 4, &bars[st]);
-        bulk_load(base + a_bytes + kTile * 8, P.kind + j0, kTile, &bars[st]);
-    };
-    if (tid == 0)
-        for (int s = 0; s < stages; ++s) issue(s);
-
     double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
-    bool aborted = false;
-
-    auto finish_job = [&](long long i, bool valid, int kind, float w, float p,
-                          const JobSol<float> &s, float *warp_rows) {
+    auto job = [&](long long i, bool valid, const float *row, int kind, float w, float p,
+                   float *warp_rows) {
+        float a[MT];
+        load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
+        JobSol<float> s;
+        s.cP = s.cQ = -1;
+        s.xP = s.xQ = 0.f;
         if (valid) {
+            auto fetch = [&](int k, float &av, float &lv) {
+                const int c = colof<MT>(k, rot);
+                av = row != nullptr ? row[c] : __ldg(&P.A[i * m + c]);
+                lv = lam_s[c];
+            };
+            solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
             hsum += static_cast<double>(s.h);
             uxsum += static_cast<double>(util<float>(kind, w, p, s.t));
             if (LAG && lag) {
@@ -501,95 +639,74 @@ __global__ void __launch_bounds__(kTile, 2)
         }
         warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, s, racc);
     };
+    unsigned char *smem = align128<MT>(smem_dyn);
+    stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job);
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, m, grouped ? (lane / MT == 0) : true, P, red);
+}
 
-    long long it_fail = 0;
-    for (long long it = 0; it < n_my; ++it) {
-        const int st = static_cast<int>(it % stages);
-        const uint32_t parity = static_cast<uint32_t>((it / stages) & 1);
-        const bool ok = mbar_wait_bounded(&bars[st], parity);
-        if (__syncthreads_or(!ok)) {
-            aborted = true;
-            it_fail = it;
-            break;
-        }
-        unsigned char *base = smem + st * st_bytes;
-        float *a_s = reinterpret_cast<float *>(base);
-        const float *w_s = reinterpret_cast<const float *>(base + a_bytes);
-        const float *p_s = reinterpret_cast<const float *>(base + a_bytes + kTile * 4);
-        const uint8_t *k_s = base + a_bytes + kTile * 8;
-        const long long i = (blockIdx.x + it * G) * kTile + tid;
-
+// Initial prices, Eq. e-initialization:
+//   lambda^1 = (1/n) sum_i u_i'(a_i^T x0) a_i,  x0 = R / (kappa n),
+// streamed through the same TMA ring: each job scales its own row in shared
+// memory by d_i = u_i'(a_i^T x0) and the warp sums the rows column-wise.
+template <int MT>
+__global__ void __launch_bounds__(kTile, 2)
+    init_tma_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
+                    const double *R, long long n, int m, int cap, int stages, long long num_full,
+                    double *partials, unsigned *ticket, int *status, double *lam1)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t bars[kMaxStages];
+    __shared__ float x0_s[RA_MAX_M];
+    __shared__ double red[kWarps][kPartW];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool grouped = (m == MT);
+    constexpr int C = MT / 4;
+    const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
+    if (tid == 0) {
+        double kappa = 0.0;
+        for (int j = 0; j < m; ++j) kappa += R[j] / static_cast<double>(n);
+        const double div = (cap && kappa > 1.0) ? kappa : 1.0;
+        for (int j = 0; j < RA_MAX_M; ++j)
+            x0_s[j] = j < m ? static_cast<float>(R[j] / (static_cast<double>(n) * div)) : 0.0f;
+    }
+    __syncthreads();
+    float x0_r[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) x0_r[k] = x0_s[colof<MT>(k, rot)];
+    double racc = 0.0;
+    auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
+                   float *warp_rows) {
         float a[MT];
-        const float *row = a_s + tid * m;
+        load_row<MT>(a, row, A, i, valid, m, grouped, rot);
+        float tc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < MT; ++k) tc[k & 3] = fmaf(a[k], x0_r[k], tc[k & 3]);
+        const float t = (tc[0] + tc[1]) + (tc[2] + tc[3]);
+        float d = 0.0f;
+        if (valid) {
+            if (kd == RA_U_LOG) d = wi / t;
+            else if (kd == RA_U_POWER) d = wi * pi * exp2f((pi - 1.0f) * log2f(t));
+            else d = t < pi ? wi : 0.0f;  // supergradient of w min(t, T) (+ const)
+        }
+        // own row <- d * a, in column order, then warp column sums
+        float *own = warp_rows + lane * m;
         if (grouped) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float4 v = reinterpret_cast<const float4 *>(row)[(c + rot) & (C - 1)];
-                a[4 * c + 0] = v.x;
-                a[4 * c + 1] = v.y;
-                a[4 * c + 2] = v.z;
-                a[4 * c + 3] = v.w;
-            }
+            for (int c = 0; c < C; ++c)
+                reinterpret_cast<float4 *>(own)[(c + rot) & (C - 1)] =
+                    make_float4(d * a[4 * c], d * a[4 * c + 1], d * a[4 * c + 2], d * a[4 * c + 3]);
         } else {
 #pragma unroll
-            for (int k = 0; k < MT; ++k) a[k] = k < m ? row[k] : 0.0f;
+            for (int k = 0; k < MT; ++k)
+                if (k < m) own[colof<MT>(k, rot)] = d * a[k];
         }
-        const int kind = k_s[tid];
-        const float w = w_s[tid], p = p_s[tid];
-        JobSol<float> s;
-        auto fetch = [&](int k, float &av, float &lv) {
-            const int c = colof<MT>(k, rot);
-            av = row[c];
-            lv = lam_s[c];
-        };
-        solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
-        finish_job(i, true, kind, w, p, s, a_s + warp * 32 * m);
-        __syncthreads();  // stage fully consumed
-        if (tid == 0) {
-            fence_proxy_async();
-            issue(it + stages);
-        }
-    }
-
-    if (aborted) {
-        if (tid == 0) {
-            atomicOr(P.status, kStatusTimeout);
-            // let copies already in flight land before the CTA exits (bounded)
-            for (long long it2 = it_fail; it2 < n_my && it2 < it_fail + stages; ++it2)
-                (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1));
-        }
-        __syncthreads();
-    } else {
-        // ragged tail: jobs [num_full * 256, n), one block, direct loads
-        const long long tail0 = num_full * kTile;
-        if (tail0 < P.n && blockIdx.x == static_cast<unsigned>(num_full % G)) {
-            const long long i = tail0 + tid;
-            const bool valid = i < P.n;
-            float a[MT];
-#pragma unroll
-            for (int k = 0; k < MT; ++k) {
-                const int c = colof<MT>(k, rot);
-                a[k] = (valid && c < m) ? __ldg(&P.A[i * m + c]) : 0.0f;
-            }
-            const int kind = valid ? P.kind[i] : RA_U_LINCAP;
-            const float w = valid ? P.w[i] : 1.0f, p = valid ? P.param[i] : 0.0f;
-            JobSol<float> s;
-            auto fetch = [&](int k, float &av, float &lv) {
-                const int c = colof<MT>(k, rot);
-                av = __ldg(&P.A[i * m + c]);
-                lv = lam_s[c];
-            };
-            if (valid) {
-                solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
-            } else {
-                s.cP = s.cQ = -1;
-                s.xP = s.xQ = 0.f;
-            }
-            float *scratch = reinterpret_cast<float *>(smem);  // stage 0 is idle now
-            finish_job(i, valid, kind, w, p, s, scratch + warp * 32 * m);
-        }
-    }
-    reduce_and_finalize(hsum, uxsum, lbsum, racc, m, grouped ? (lane / MT == 0) : true, P, red);
+        __syncwarp();
+        warp_colsum<MT, float>(warp_rows, m, lane, grouped, racc);
+    };
+    unsigned char *smem = align128<MT>(smem_dyn);
+    stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
+    if (grid_reduce(0.0, 0.0, 0.0, racc, m, grouped ? (lane / MT == 0) : true, partials, ticket, red))
+        if (tid < m) lam1[tid] = red[0][4 + tid] / static_cast<double>(n);
 }
 
 // ---------------------------------------------------------------------------- simple kernel
@@ -725,91 +842,6 @@ __global__ void __launch_bounds__(kTile)
         *U_lb = v;
         *ticket = 0u;
     }
-}
-
-// ---------------------------------------------------------------------------- initialisation
-
-// Eq. e-initialization: lambda^1 = (1/n) sum_i u_i'(a_i^T x0) a_i,
-// x0 = R / (kappa n).  Per-thread FP32 sums over chunks of 16 jobs are
-// flushed into FP64; warps, blocks and the grid are summed in fixed order.
-template <int MT>
-__global__ void __launch_bounds__(kTile)
-    init_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
-                const double *R, long long n, int m, int cap, double *partials, unsigned *ticket,
-                double *lam1)
-{
-    __shared__ float x0_s[RA_MAX_M];
-    __shared__ double red[kWarps][RA_MAX_M];
-    __shared__ int is_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        double kappa = 0.0;
-        for (int j = 0; j < m; ++j) kappa += R[j] / static_cast<double>(n);
-        const double div = (cap && kappa > 1.0) ? kappa : 1.0;
-        for (int j = 0; j < RA_MAX_M; ++j)
-            x0_s[j] = j < m ? static_cast<float>(R[j] / (static_cast<double>(n) * div)) : 0.0f;
-    }
-    __syncthreads();
-    double acc[MT];
-    float part[MT];
-#pragma unroll
-    for (int k = 0; k < MT; ++k) {
-        acc[k] = 0.0;
-        part[k] = 0.0f;
-    }
-    int cnt = 0;
-    for (long long i = static_cast<long long>(blockIdx.x) * kTile + tid; i < n;
-         i += static_cast<long long>(gridDim.x) * kTile) {
-        float a[MT];
-        float t = 0.f;
-#pragma unroll
-        for (int k = 0; k < MT; ++k) {
-            a[k] = k < m ? __ldg(&A[i * m + k]) : 0.0f;
-            t = fmaf(a[k], x0_s[k], t);
-        }
-        const int kd = kind[i];
-        const float wi = w[i], pi = param[i];
-        float d;
-        if (kd == RA_U_LOG) d = wi / t;
-        else if (kd == RA_U_POWER) d = wi * pi * exp2f((pi - 1.0f) * log2f(t));
-        else d = t < pi ? wi : 0.0f;
-#pragma unroll
-        for (int k = 0; k < MT; ++k) part[k] = fmaf(d, a[k], part[k]);
-        if (++cnt == 16) {
-#pragma unroll
-            for (int k = 0; k < MT; ++k) {
-                acc[k] += static_cast<double>(part[k]);
-                part[k] = 0.0f;
-            }
-            cnt = 0;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < MT; ++k) {
-        acc[k] += static_cast<double>(part[k]);
-        acc[k] = warp_sum_d(acc[k]);
-    }
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < MT; ++k) red[warp][k] = acc[k];
-    __syncthreads();
-    if (tid < m) {
-        double v = 0.0;
-        for (int k = 0; k < kWarps; ++k) v += red[k][tid];
-        partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    if (tid < m) {
-        double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[static_cast<size_t>(b) * kPartW + tid]);
-        lam1[tid] = v / static_cast<double>(n);
-    }
-    if (tid == 0) *ticket = 0u;
 }
 
 // ---------------------------------------------------------------------------- recovery
@@ -1003,6 +1035,15 @@ cudaError_t configure_dual(ra_problem *p)
     const size_t sb = StageLayout<4>::bytes(m);  // layout does not depend on MT
     p->smem_dual = p->stages * sb + 128;
     cudaError_t e;
+#define RA_IATTR(MT)                                                                               \
+    if ((e = cudaFuncSetAttribute(init_tma_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  110 * 1024)) != cudaSuccess)                                     \
+        return e;
+    RA_IATTR(4)
+    RA_IATTR(8)
+    RA_IATTR(16)
+    RA_IATTR(32)
+#undef RA_IATTR
     if ((e = set_attrs_mt<4, true>()) != cudaSuccess) return e;
     if ((e = set_attrs_mt<8, true>()) != cudaSuccess) return e;
     if ((e = set_attrs_mt<16, true>()) != cudaSuccess) return e;
@@ -1058,16 +1099,22 @@ cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaSt
 
 cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s)
 {
-    long long blocks = (p->n + kTile - 1) / kTile;
-    if (blocks > p->grid_aux) blocks = p->grid_aux;
+    const long long num_full = p->n / kTile;
+    int grid = p->grid_dual;
+    if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
     const int cap = !(p->flags & RA_NO_JOB_CAP);
-    const int b = static_cast<int>(blocks);
+#define RA_INIT(MT)                                                                                \
+    init_tma_kernel<MT><<<grid, kTile, p->smem_dual, s>>>(p->A, p->kind, p->w, p->param, p->R,      \
+                                                          p->n, p->m, cap, p->stages, num_full,    \
+                                                          p->partials, p->ticket + 2, p->status,   \
+                                                          lam1)
     switch (p->mt) {
-    case 4: init_kernel<4><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
-    case 8: init_kernel<8><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
-    case 16: init_kernel<16><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
-    default: init_kernel<32><<<b, kTile, 0, s>>>(p->A, p->kind, p->w, p->param, p->R, p->n, p->m, cap, p->partials, p->ticket + 2, lam1); break;
+    case 4: RA_INIT(4); break;
+    case 8: RA_INIT(8); break;
+    case 16: RA_INIT(16); break;
+    default: RA_INIT(32); break;
     }
+#undef RA_INIT
     return cudaGetLastError();
 }
 

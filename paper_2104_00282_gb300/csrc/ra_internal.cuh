@@ -13,6 +13,7 @@ constexpr int kMaxStages = 8;
 constexpr int kMaxLbfgsMem = 16;
 constexpr int kHist = 512;          // solver history ring length
 constexpr int kPartW = RA_MAX_M + 4; // doubles per block partial: h, U(X), U_lb(prev), spare, r[m]
+constexpr int kCand = 64;           // master-LP candidates kept (two per evaluation)
 
 // Status word bits written by kernels (never trap: a kernel that gives up
 // records why and returns).
@@ -60,6 +61,26 @@ struct SolverState {
     int32_t pad2_;
     double lam_bt[RA_MAX_M];
     double q_bt[RA_MAX_M];
+    // master-LP lower bound: candidates (utility, usage) of evaluated
+    // allocations, unscaled and column-scaled, with the prices that made them
+    int32_t cand_count;
+    int32_t cand_head;
+    int32_t use_master;
+    int32_t master_ok;      // the best lower bound came from the master LP
+    double U_master;        // value of the last master LP (-inf if none)
+    int32_t mu_ok;          // mu_lp holds the LP's resource duals
+    int32_t pad3_;
+    double mu_lp[RA_MAX_M]; // minimiser of the cutting-plane model of g (LP duals)
+    double r_prev[RA_MAX_M];
+    double cand_U[kCand];
+    int32_t cand_scaled[kCand];
+    double cand_r[kCand][RA_MAX_M];
+    double cand_lam[kCand][RA_MAX_M];
+    double lp_theta[kCand]; // weights found by the last master LP (over cand slots)
+    double theta[kCand];    // certificate of the best lower bound
+    double theta_lam[kCand][RA_MAX_M];
+    int32_t theta_scaled[kCand];
+    int32_t theta_n;
     double lam_cur[RA_MAX_M];
     double q_cur[RA_MAX_M];
     double d[RA_MAX_M];
@@ -153,6 +174,7 @@ cudaError_t configure_dual(ra_problem *p);
 ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, double *lambda_out,
                 double *lambda_lb, ra_solve_info *info);
 int32_t solve_history(ra_problem *p, double *hist, int32_t cap);
+int32_t solve_certificate(ra_problem *p, double *theta, double *lam, int32_t *scaled);
 
 // Error reporting (ra_api.cu).
 ra_status fail(ra_status s, const char *fmt, ...);

@@ -47,7 +47,8 @@ __device__ __forceinline__ int wmin_i(int v)
 // initial prices have already been written to st->lam_trial.
 __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const double *R, int m,
                                     double tol, int max_evals, int mem, int update,
-                                    double lam_floor, int cap, int32_t *pingpong, int32_t *lag_on)
+                                    double lam_floor, int cap, int use_master, int32_t *pingpong,
+                                    int32_t *lag_on)
 {
     const int j = threadIdx.x;
     double l = 0.0;
@@ -84,6 +85,12 @@ __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const d
         st->g_bt = __longlong_as_double(0x7ff0000000000000ll);
         st->last_step = 0.05 * lmax;
         st->sg_pending = 0;
+        st->cand_count = 0;
+        st->cand_head = 0;
+        st->use_master = use_master;
+        st->master_ok = 0;
+        st->theta_n = 0;
+        st->U_master = -__longlong_as_double(0x7ff0000000000000ll);
         *pingpong = 0;
         *lag_on = 0;
     }
@@ -138,6 +145,203 @@ __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
     if (active) st->d[j] = d;
 }
 
+// ---------------------------------------------------------------------------- master LP
+
+constexpr int kLpRows = RA_MAX_M + 2;              // m resource rows, convexity, objective
+constexpr int kLpCols = kCand + RA_MAX_M + 1;      // candidates, slacks, right-hand side
+constexpr int kLpThreads = 256;
+
+// Lower bound from the evaluated allocations (the paper's column-scaled
+// allocations and the raw subproblem solutions): weights theta >= 0,
+// sum theta = 1, sum_k theta_k r_k <= R make sum_k theta_k X^k feasible, and by
+// concavity of every u_i its utility is >= sum_k theta_k U_k.  The best such
+// bound is the LP  max sum theta_k U_k  over that set, solved here by a dense
+// tableau simplex in FP64 (Bland's rule) started from the best single
+// feasible candidate.  The weights are re-checked against the constraints in
+// FP64 before the bound is used.
+__global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, const EvalOut *ev)
+{
+    __shared__ double T[kLpRows][kLpCols];
+    __shared__ double fac[kLpRows];
+    __shared__ double Rs[RA_MAX_M];
+    __shared__ int basis[RA_MAX_M + 1];
+    __shared__ int s_enter, s_leave, s_slotU, s_slotS, s_k0, s_run;
+    __shared__ double s_uscale;
+    const int tid = threadIdx.x;
+    if (st->done) return;
+    const int m = st->m;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    // append this evaluation's raw allocation and the previous one's scaled allocation
+    if (tid == 0) {
+        int count = st->cand_count, head = st->cand_head;
+        bool fin = isfinite(ev->Ux);
+        for (int j = 0; j < m; ++j) fin = fin && isfinite(ev->r[j]);
+        int su = -1, ss = -1;
+        if (fin) {
+            su = head;
+            head = (head + 1) % kCand;
+            count = min(count + 1, kCand);
+        }
+        if (st->have_lb_prev && isfinite(ev->Ulb_prev)) {
+            ss = head;
+            head = (head + 1) % kCand;
+            count = min(count + 1, kCand);
+        }
+        st->cand_count = count;
+        st->cand_head = head;
+        if (su >= 0) {
+            st->cand_U[su] = ev->Ux;
+            st->cand_scaled[su] = 0;
+        }
+        if (ss >= 0) {
+            st->cand_U[ss] = ev->Ulb_prev;
+            st->cand_scaled[ss] = 1;
+        }
+        s_slotU = su;
+        s_slotS = ss;
+        s_run = st->use_master && count >= 2 && !(st->gap <= st->tol);
+        st->U_master = -inf;
+        st->mu_ok = 0;
+    }
+    __syncthreads();
+    if (tid < m) {
+        if (s_slotU >= 0) {
+            st->cand_r[s_slotU][tid] = ev->r[tid];
+            st->cand_lam[s_slotU][tid] = st->lam_trial[tid];
+        }
+        if (s_slotS >= 0) {
+            st->cand_r[s_slotS][tid] = fmin(st->r_prev[tid], st->R[tid]);
+            st->cand_lam[s_slotS][tid] = st->lam_prev_eval[tid];
+        }
+        Rs[tid] = st->R[tid] > 0.0 ? st->R[tid] : 1.0;
+    }
+    __syncthreads();
+    if (!s_run) return;
+    const int N = st->cand_count;
+    const int cols = N + m + 1, rhs = N + m;
+    // best single feasible candidate
+    if (tid == 0) {
+        int k0 = -1;
+        double best = -inf, us = 1.0;
+        for (int k = 0; k < N; ++k) {
+            us = fmax(us, fabs(st->cand_U[k]));
+            bool feas = true;
+            for (int j = 0; j < m; ++j) feas = feas && st->cand_r[k][j] <= st->R[j];
+            if (feas && st->cand_U[k] > best) {
+                best = st->cand_U[k];
+                k0 = k;
+            }
+        }
+        s_k0 = k0;
+        s_uscale = us;
+    }
+    __syncthreads();
+    const int k0 = s_k0;
+    if (k0 < 0) return;
+    const double us = s_uscale;
+    for (int idx = tid; idx < (m + 2) * cols; idx += kLpThreads) {
+        const int i = idx / cols, c = idx % cols;
+        double v = 0.0;
+        if (i < m) {                                   // resource rows, basis: slack i
+            if (c < N) v = c == k0 ? 0.0 : (st->cand_r[c][i] - st->cand_r[k0][i]) / Rs[i];
+            else if (c < rhs) v = (c - N == i) ? 1.0 : 0.0;
+            else v = (st->R[i] - st->cand_r[k0][i]) / Rs[i];
+        } else if (i == m) {                           // convexity row, basis: theta_k0
+            v = c < N ? 1.0 : (c == rhs ? 1.0 : 0.0);
+        } else {                                       // reduced costs; rhs holds -value
+            if (c < N) v = c == k0 ? 0.0 : (st->cand_U[c] - st->cand_U[k0]) / us;
+            else if (c == rhs) v = -st->cand_U[k0] / us;
+        }
+        T[i][c] = v;
+    }
+    if (tid < m) basis[tid] = N + tid;
+    if (tid == 0) basis[m] = k0;
+    __syncthreads();
+    for (int iter = 0; iter < 8 * kLpRows; ++iter) {
+        if (tid == 0) {
+            s_enter = 0x7fffffff;
+            s_leave = -1;
+        }
+        __syncthreads();
+        for (int c = tid; c < N + m; c += kLpThreads)
+            if (T[m + 1][c] > 1e-12) atomicMin(&s_enter, c);
+        __syncthreads();
+        const int e = s_enter;
+        if (e == 0x7fffffff) break;                    // optimal
+        if (tid < 32) {
+            // ratio test over the m + 1 constraint rows; ties to the lowest basis index
+            double br = inf;
+            int bb = 0x7fffffff, brow = -1;
+            for (int i = tid; i <= m; i += 32) {
+                const double a = T[i][e];
+                if (a > 1e-12) {
+                    const double rr = fmax(T[i][rhs], 0.0) / a;
+                    if (rr < br || (rr == br && basis[i] < bb)) {
+                        br = rr;
+                        bb = basis[i];
+                        brow = i;
+                    }
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double orr = __shfl_xor_sync(0xffffffffu, br, off);
+                const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+                const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
+                if (orr < br || (orr == br && ob < bb)) {
+                    br = orr;
+                    bb = ob;
+                    brow = orow;
+                }
+            }
+            if (tid == 0) s_leave = brow;
+        }
+        __syncthreads();
+        const int pr = s_leave;
+        if (pr < 0) break;                             // unbounded direction (cannot occur)
+        if (tid < m + 2) fac[tid] = T[tid][e];
+        __syncthreads();
+        const double piv = fac[pr];
+        for (int c = tid; c < cols; c += kLpThreads) T[pr][c] /= piv;
+        __syncthreads();
+        for (int idx = tid; idx < (m + 2) * cols; idx += kLpThreads) {
+            const int i = idx / cols, c = idx % cols;
+            if (i != pr) T[i][c] -= fac[i] * T[pr][c];
+        }
+        if (tid == 0) basis[pr] = e;
+        __syncthreads();
+    }
+    // weights, exact re-check and the bound in original units
+    if (tid < kCand) st->lp_theta[tid] = 0.0;
+    __syncthreads();
+    if (tid == 0) {
+        double tsum = 0.0;
+        for (int i = 0; i <= m; ++i)
+            if (basis[i] < N) {
+                const double th = fmax(T[i][rhs], 0.0);
+                st->lp_theta[basis[i]] = th;
+                tsum += th;
+            }
+        bool ok = tsum > 0.5;
+        double U = 0.0;
+        if (ok) {
+            for (int k = 0; k < N; ++k) {
+                st->lp_theta[k] /= tsum;
+                U += st->lp_theta[k] * st->cand_U[k];
+            }
+            for (int j = 0; j < m && ok; ++j) {
+                double r = 0.0;
+                for (int k = 0; k < N; ++k) r += st->lp_theta[k] * st->cand_r[k][j];
+                ok = r <= st->R[j] * (1.0 + 1e-12);
+            }
+        }
+        st->U_master = ok ? U : -inf;
+    }
+    // resource duals of the scaled LP: mu_j = -(reduced cost of slack j) us / Rs_j;
+    // (mu, nu) minimise the cutting-plane model max_k [U_k + mu^T (R - r_k)] of g
+    if (tid < m) st->mu_lp[tid] = fmax(-T[m + 1][N + tid], 0.0) * us / Rs[tid];
+    if (tid == 0) st->mu_ok = isfinite(st->U_master) ? 1 : 0;
+}
+
 // Store the pair (s, y) = (lambda_t - lambda_cur, q_t - q_cur) when it has
 // positive curvature, then make lambda_t the current point.
 __device__ void accept_point(SolverState *st, int j, bool active, double g_t, double q_t,
@@ -188,10 +392,37 @@ __device__ void accept_point(SolverState *st, int j, bool active, double g_t, do
 // projected subgradient step of half the last step length is taken without a
 // decrease test -- the method's fallback (Section 5).  The best g and lower
 // bound are tracked separately, so non-monotone steps lose nothing.
+// Trial halfway towards the minimiser of the cutting-plane model (the master
+// LP's duals), taken without a decrease test: it adds cuts on the far side
+// of the kink the iterates are stuck at, which is what the master bound
+// needs to close the gap when g is not differentiable at its minimum.
+__device__ void bundle_step(SolverState *st, int j, bool active)
+{
+    if (active) st->d[j] = 0.5 * (st->mu_lp[j] - st->lam_cur[j]);
+    if (j == 0) {
+        st->mem_count = 0;
+        st->mem_head = 0;
+        st->ls_iter = 0;
+        st->step = 1.0;
+        st->sg_pending = 1;
+        st->g_bt = __longlong_as_double(0x7ff0000000000000ll);
+    }
+    __syncwarp();
+}
+
+// The dual has stopped improving by more than a tenth of the tolerance while
+// the gap is still open: the lower bound, not g, is what is left to close.
+__device__ bool dual_stalled(const SolverState *st, double g_prev, double g_new)
+{
+    return st->mu_ok && st->use_master && st->phase == 1 &&
+           g_prev - g_new < 0.1 * st->tol * fmax(fabs(g_new), 1.0);
+}
+
 __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double g_t, double q_t,
                              double lam_t)
 {
     const bool fin = isfinite(g_t);
+    const double g_prev = st->g_cur;
     if (st->sg_pending && !fin) {
         if (j == 0) st->step = 0.25 * st->step;   // shorten the fallback step
     } else if (st->phase == 0 || st->sg_pending) {
@@ -202,8 +433,10 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
         const double slope = wsum(active ? st->q_cur[j] * dl : 0.0);
         const bool armijo = fin && g_t <= st->g_cur + 1e-4 * slope;
         if (armijo) {
+            const bool stalled = dual_stalled(st, g_prev, g_t);
             accept_point(st, j, active, g_t, q_t, lam_t, true);
-            lbfgs_direction(st, j, m, active);
+            if (stalled) bundle_step(st, j, active);
+            else lbfgs_direction(st, j, m, active);
         } else {
             if (fin && g_t < st->g_bt) {
                 if (active) {
@@ -225,8 +458,13 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
                 }
             } else if (st->g_bt < st->g_cur) {
                 const double lb = active ? st->lam_bt[j] : 0.0, qb = active ? st->q_bt[j] : 0.0;
+                const bool stalled = dual_stalled(st, g_prev, st->g_bt);
                 accept_point(st, j, active, st->g_bt, qb, lb, true);
-                lbfgs_direction(st, j, m, active);
+                if (stalled) bundle_step(st, j, active);
+                else lbfgs_direction(st, j, m, active);
+            } else if (st->mu_ok && st->use_master) {
+                if (j == 0) st->ls_fail = st->ls_fail + 1;
+                bundle_step(st, j, active);
             } else {
                 // kink: subgradient fallback from the current point
                 const double qn = sqrt(wsum(active ? st->q_cur[j] * st->q_cur[j] : 0.0));
@@ -272,16 +510,50 @@ __global__ void __launch_bounds__(32)
     // and U(X) itself whenever X(lambda_t) already meets r <= R
     double U_best = st->U_best;
     const double lam_pe = active ? st->lam_prev_eval[j] : 0.0;
+    // certificate of the best bound: one allocation with weight 1, or the
+    // master LP's mixture (copied, since the candidate ring moves on)
+    int cert = 0;     // 1 scaled previous, 2 raw current, 3 master mixture
     if (st->have_lb_prev && ev->Ulb_prev > U_best) {
         U_best = ev->Ulb_prev;
-        if (active) st->lam_lb[j] = lam_pe;
+        cert = 1;
     }
     const int feasible = wmin_i(active ? (q_t >= 0.0 ? 1 : 0) : 1);
     if (feasible && ev->Ux > U_best) {
         U_best = ev->Ux;
-        if (active) st->lam_lb[j] = lam_t;
+        cert = 2;
     }
-    if (active) st->lam_prev_eval[j] = lam_t;
+    if (st->use_master && st->U_master > U_best) {
+        U_best = st->U_master;
+        cert = 3;
+    }
+    if (cert == 1 || cert == 2) {
+        if (active) {
+            st->lam_lb[j] = cert == 1 ? lam_pe : lam_t;
+            st->theta_lam[0][j] = cert == 1 ? lam_pe : lam_t;
+        }
+        if (j == 0) {
+            st->theta_n = 1;
+            st->theta[0] = 1.0;
+            st->theta_scaled[0] = cert == 1;
+            st->master_ok = 0;
+        }
+    } else if (cert == 3) {
+        const int N = st->cand_count;
+        for (int k = 0; k < N; ++k)
+            if (active) st->theta_lam[k][j] = st->cand_lam[k][j];
+        for (int k = j; k < N; k += 32) {
+            st->theta[k] = st->lp_theta[k];
+            st->theta_scaled[k] = st->cand_scaled[k];
+        }
+        if (j == 0) {
+            st->theta_n = N;
+            st->master_ok = 1;
+        }
+    }
+    if (active) {
+        st->lam_prev_eval[j] = lam_t;
+        st->r_prev[j] = r_t;
+    }
     double g_best = st->g_best;
     const bool improved = g_t < g_best;
     if (improved) {
@@ -377,6 +649,23 @@ int32_t solve_history(ra_problem *p, double *hist, int32_t cap)
     return e == cudaSuccess ? len : -1;
 }
 
+int32_t solve_certificate(ra_problem *p, double *theta, double *lam, int32_t *scaled)
+{
+    int32_t nk = 0;
+    SolverState *st = p->st;
+    cudaError_t e = cudaMemcpyAsync(&nk, &st->theta_n, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess || nk < 0 || nk > kCand) return -1;
+    if (nk == 0) return 0;
+    e = cudaMemcpyAsync(theta, st->theta, sizeof(double) * nk, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scaled, st->theta_scaled, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, p->stream);
+    for (int k = 0; k < nk && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(lam + static_cast<size_t>(k) * p->m, st->theta_lam[k], sizeof(double) * p->m,
+                            cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return e == cudaSuccess ? nk : -1;
+}
+
 ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, double *lambda_out,
                 double *lambda_lb, ra_solve_info *info)
 {
@@ -403,7 +692,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     }
     solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, p->m, opts.tol_rel, opts.max_evals,
                                          opts.lbfgs_mem, opts.update, opts.lam_floor, cap,
-                                         pingpong, lag_on);
+                                         opts.master_lb, pingpong, lag_on);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
@@ -453,6 +742,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 cudaError_t e1 = launch_dual(p, dp, s);
+                master_kernel<<<1, kLpThreads, 0, s>>>(st, p->ev);
                 solver_update_kernel<<<1, 32, 0, s>>>(st, p->ev, pingpong, lag_on, p->status, cond,
                                                       1, nullptr);
                 cudaError_t e2 = cudaGetLastError();
@@ -477,6 +767,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             for (int k = 0; k < 8; ++k) {
                 if ((e = launch_dual(p, dp, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
+                master_kernel<<<1, kLpThreads, 0, s>>>(st, p->ev);
                 solver_update_kernel<<<1, 32, 0, s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
                                                       done_flag);
             }

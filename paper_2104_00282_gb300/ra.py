@@ -30,7 +30,8 @@ class RaError(RuntimeError):
 class ra_solve_opts(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("max_evals", ctypes.c_int32),
                 ("lbfgs_mem", ctypes.c_int32), ("update", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("lam_floor", ctypes.c_double)]
+                ("use_graph", ctypes.c_int32), ("lam_floor", ctypes.c_double),
+                ("master_lb", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class ra_solve_info(ctypes.Structure):
@@ -67,6 +68,8 @@ def lib():
         L.ra_solve.argtypes = [P, ctypes.POINTER(ra_solve_opts), P, P, P,
                                ctypes.POINTER(ra_solve_info)]
         L.ra_solve.restype = i32
+        L.ra_solve_certificate.argtypes = [P, P, P, P]
+        L.ra_solve_certificate.restype = i32
         L.ra_solve_history.argtypes = [P, P, i32]
         L.ra_solve_history.restype = i32
         L.ra_recover_primal.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
@@ -151,6 +154,23 @@ def ra_solve(h, lam_out, opts=None, lam0=None, lam_lb=None, allow_notconv=True):
     return info.as_dict()
 
 
+RA_MAX_CERT = 64
+
+
+def ra_solve_certificate(h, m):
+    """(theta, lam (k x m), scaled) describing the allocation behind U_lb."""
+    import numpy as np
+    theta = np.zeros(RA_MAX_CERT)
+    lam = np.zeros((RA_MAX_CERT, m))
+    scaled = np.zeros(RA_MAX_CERT, np.int32)
+    k = lib().ra_solve_certificate(h, ctypes.c_void_p(theta.ctypes.data),
+                                   ctypes.c_void_p(lam.ctypes.data),
+                                   ctypes.c_void_p(scaled.ctypes.data))
+    if k < 0:
+        raise RaError(RA_ECUDA, lib().ra_last_error().decode())
+    return theta[:k], lam[:k], scaled[:k].astype(bool)
+
+
 def ra_solve_history(h, cap=512):
     import numpy as np
     buf = np.zeros((cap, 4))
@@ -225,8 +245,9 @@ class AllocationProblem:
         return lam
 
     def solve(self, tol=1e-6, max_evals=500, lam0=None, update="lbfgs", use_graph=True,
-              lbfgs_mem=10):
+              lbfgs_mem=10, master_lb=True):
         o = ra_solve_opts_default()
+        o.master_lb = 1 if master_lb else 0
         o.tol_rel = tol
         o.max_evals = max_evals
         o.lbfgs_mem = lbfgs_mem
@@ -240,6 +261,11 @@ class AllocationProblem:
         self.prices = lam
         self.prices_lb = lam_lb
         return self.info
+
+    def certificate(self):
+        """(theta, lam, scaled): the allocation behind the last solve's U_lb is
+        sum_k theta_k X(lam_k) (column-scaled where scaled[k])."""
+        return ra_solve_certificate(self.handle, self.m)
 
     def history(self):
         """Rows (evaluation, g, best U_lb, relative gap) of the last solve."""
