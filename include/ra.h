@@ -204,6 +204,40 @@ ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jst
                             float *x12, float *t, float *X_dense, double *U, uint8_t *near_tie,
                             int64_t *n_near_ties);
 
+/*
+ * ra_eval_dual_static -- g(lambda) and q = R - r exactly as ra_eval_dual
+ * computes them, but without creating a problem and without allocating any
+ * device memory.  (The paper has no counterpart; this is a deployment aid.)
+ *
+ * For callers that must not allocate: code running while a CUDA stream is
+ * being captured into a graph (allocation calls break or are refused during
+ * capture), latency-bound serving loops with a no-allocation rule (cudaMalloc
+ * can synchronise the device), and hosts whose framework owns all device
+ * memory through its own pool.
+ *
+ * Arguments are those of ra_problem_create plus lambda (m FP64 device prices)
+ * and the outputs g (1 FP64, device) and q (m FP64, device); flags may only
+ * be RA_JOB_CAP or RA_NO_JOB_CAP (FP32 per-job arithmetic).  All pointers are
+ * device pointers; A, kind, w, param must be 16-byte aligned.  Work is
+ * enqueued on `stream`.
+ *
+ * Scratch: one static device array of about 296 KB in this library, which
+ * every GPU that loads libra.so keeps until the process exits.  It holds the
+ * per-CTA partial sums of at most 1024 CTAs; a GPU whose evaluation would use
+ * more CTAs is refused with RA_EINVAL.  Any n and 1 <= m <= RA_MAX_M are
+ * accepted.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (the kernel's counters are cleared on the stream
+ * before each launch): calls whose work overlaps on the GPU -- on different
+ * streams or devices sharing a context -- race and must be serialised by the
+ * caller.
+ */
+ra_status ra_eval_dual_static(int64_t n, int32_t m, const float *A, const uint8_t *kind,
+                              const float *w, const float *param, const double *R,
+                              const double *lambda, uint32_t flags, void *stream, double *g,
+                              double *q);
+
 /* Static strings; ra_last_error() is thread-local and valid until the next call. */
 const char *ra_status_string(ra_status s);
 const char *ra_last_error(void);

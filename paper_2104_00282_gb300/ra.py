@@ -74,6 +74,8 @@ def lib():
         L.ra_solve_history.restype = i32
         L.ra_recover_primal.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
         L.ra_recover_primal.restype = i32
+        L.ra_eval_dual_static.argtypes = [i64, i32, P, P, P, P, P, P, u32, P, P, P]
+        L.ra_eval_dual_static.restype = i32
         L.ra_status_string.argtypes = [i32]
         L.ra_status_string.restype = ctypes.c_char_p
         L.ra_last_error.argtypes = []
@@ -189,6 +191,17 @@ def ra_recover_primal(h, lam, jstar=None, j12=None, x12=None, t=None, X=None, U=
                                    _ptr(U, torch.float64), _ptr(near_tie, torch.uint8),
                                    ctypes.byref(cnt) if count_ties else None))
     return int(cnt.value)
+
+
+def ra_eval_dual_static(A, kind, w, param, R, lam, g, q, flags=0, stream=None):
+    """ra_eval_dual without a problem object and without device allocation
+    (static scratch inside libra.so; see include/ra.h)."""
+    n, m = A.shape
+    _check(lib().ra_eval_dual_static(n, m, _ptr(A, torch.float32), _ptr(kind, torch.uint8, n),
+                                     _ptr(w, torch.float32, n), _ptr(param, torch.float32, n),
+                                     _ptr(R, torch.float64, m), _ptr(lam, torch.float64, m), flags,
+                                     _stream(stream), _ptr(g, torch.float64, 1),
+                                     _ptr(q, torch.float64, m)))
 
 
 def ra_version():
