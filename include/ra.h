@@ -180,10 +180,12 @@ int32_t ra_solve_certificate(ra_problem *prob, double *theta, double *lam, int32
 
 /*
  * ra_solve_history -- per-evaluation log of the last ra_solve (the paper's
- * verbose output, Section 6.1): rows of (evaluation, g, best U_lb, relative
- * gap).  hist: host buffer of 4*cap doubles.  Returns the number of rows
- * written (<= cap) or -1 on error.  Synchronises.
+ * verbose output, Section 6.1): rows of RA_HIST_COLS doubles (evaluation, g,
+ * best U_lb, relative gap, master-LP bound of that evaluation or -inf, its
+ * simplex pivots).  hist: host buffer of RA_HIST_COLS*cap doubles.  Returns
+ * the number of rows written (<= cap) or -1 on error.  Synchronises.
  */
+#define RA_HIST_COLS 6
 int32_t ra_solve_history(ra_problem *prob, double *hist, int32_t cap);
 
 /*

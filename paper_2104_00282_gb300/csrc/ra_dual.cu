@@ -123,11 +123,12 @@ template <> struct Fn<double> {
 // zero price becomes a huge finite mu instead of +inf, so that zero-price
 // resources still compare by efficiency: the lower hull then leaves the
 // origin along lambda = 0 straight to the most efficient free resource (the
-// farthest collinear point), and no two free resources tie at +inf.
+// farthest collinear point), and no two free resources tie at +inf.  In FP32
+// prices below 1e-30 count as zero (their inverse would overflow).
 template <typename Real> __device__ __forceinline__ Real inv_price(Real lam);
 template <> __device__ __forceinline__ float inv_price<float>(float lam)
 {
-    return lam > 0.0f ? 1.0f / lam : (lam == 0.0f ? 5.192296858534828e33f /* 2^112 */ : 0.0f);
+    return lam > 1e-30f ? 1.0f / lam : (lam >= 0.0f ? 5.192296858534828e33f /* 2^112 */ : 0.0f);
 }
 template <> __device__ __forceinline__ double inv_price<double>(double lam)
 {
@@ -142,6 +143,21 @@ __device__ __forceinline__ Real util(int kind, Real w, Real p, Real t)
     if (kind == RA_U_POWER) return t > Real(0) ? w * Fn<Real>::exp2(p * Fn<Real>::log2(t)) : Real(0);
     if (kind == RA_U_LINCAP) return w * fmin(t, p);
     return w * fmin(t - p, Real(0));
+}
+
+// FP32: every kind is evaluated with one logarithm and one exponential
+// (CUDA's fast intrinsics __logf/__expf, absolute error about 2^-21 in the
+// logarithm) and the result selected by kind, so a warp holding mixed kinds
+// does not serialise one code path per kind.
+template <>
+__device__ __forceinline__ float util<float>(int kind, float w, float p, float t)
+{
+    const float L = __logf(t);
+    const float ul = w * L;
+    const float up = t > 0.0f ? w * __expf(p * L) : 0.0f;
+    const float uc = w * fminf(t, p);
+    const float ut = w * fminf(t - p, 0.0f);
+    return kind == RA_U_LOG ? ul : kind == RA_U_POWER ? up : kind == RA_U_LINCAP ? uc : ut;
 }
 
 // Smallest maximiser of u(t) - alpha t on [lo, hi]:
@@ -161,6 +177,26 @@ __device__ __forceinline__ Real topt(int kind, Real w, Real p, Real alpha, Real 
         t = p;
     }
     return fmin(fmax(t, lo), hi);
+}
+
+// FP32 variant of topt with the same selection structure: log w/alpha,
+// power exp(log(w p / alpha) / (1 - p)), both through the fast intrinsics.
+template <>
+__device__ __forceinline__ float topt<float>(int kind, float w, float p, float alpha, float lo,
+                                             float hi)
+{
+    const float tl = __fdividef(w, alpha);
+    const float tp = __expf(__fdividef(__logf(__fdividef(w * p, alpha)), 1.0f - p));
+    float t;
+    if (kind <= RA_U_POWER) {
+        if (!(alpha > 0.0f)) return hi;
+        t = kind == RA_U_LOG ? tl : tp;
+    } else {
+        if (w <= alpha) return lo;
+        if (alpha < 0.0f) return hi;
+        t = p;
+    }
+    return fminf(fmaxf(t, lo), hi);
 }
 
 // Slot k of a per-thread register array holds column colof(k): rows are read
@@ -610,6 +646,14 @@ __global__ void __launch_bounds__(kTile, 2)
     double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
     auto job = [&](long long i, bool valid, const float *row, int kind, float w, float p,
                    float *warp_rows) {
+        // the previous evaluation's record is read first so that its latency
+        // overlaps this job's solve
+        float2 tp = make_float2(0.f, 0.f);
+        uchar2 jp = make_uchar2(255, 255);
+        if (LAG && lag && valid) {
+            tp = lbt_prev[i];
+            jp = lbj_prev[i];
+        }
         float a[MT];
         load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
         JobSol<float> s;
@@ -625,8 +669,6 @@ __global__ void __launch_bounds__(kTile, 2)
             hsum += static_cast<double>(s.h);
             uxsum += static_cast<double>(util<float>(kind, w, p, s.t));
             if (LAG && lag) {
-                const float2 tp = lbt_prev[i];
-                const uchar2 jp = lbj_prev[i];
                 float tt = 0.f;
                 if (jp.x != 255) tt += s_s[jp.x] * tp.x;
                 if (jp.y != 255) tt += s_s[jp.y] * tp.y;

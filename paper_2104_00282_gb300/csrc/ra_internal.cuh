@@ -11,7 +11,8 @@ namespace ra {
 constexpr int kTile = 256;          // jobs per tile == threads per CTA of the streaming kernels
 constexpr int kMaxStages = 8;
 constexpr int kMaxLbfgsMem = 16;
-constexpr int kHist = 512;          // solver history ring length
+constexpr int kHist = 512;          // solver history length
+constexpr int kHistCols = 6;        // eval, g, best U_lb, gap, master-LP value, LP pivots
 constexpr int kPartW = RA_MAX_M + 4; // doubles per block partial: h, U(X), U_lb(prev), spare, r[m]
 constexpr int kCand = 64;           // master-LP candidates kept (two per evaluation)
 
@@ -68,9 +69,12 @@ struct SolverState {
     int32_t use_master;
     int32_t master_ok;      // the best lower bound came from the master LP
     double U_master;        // value of the last master LP (-inf if none)
+    int32_t lp_iters;       // pivots of the last master LP
+    int32_t pad4_;
     int32_t mu_ok;          // mu_lp holds the LP's resource duals
     int32_t pad3_;
     double mu_lp[RA_MAX_M]; // minimiser of the cutting-plane model of g (LP duals)
+    double q_best[RA_MAX_M];// subgradient at the best dual point
     double r_prev[RA_MAX_M];
     double cand_U[kCand];
     int32_t cand_scaled[kCand];
@@ -93,7 +97,7 @@ struct SolverState {
     double S[kMaxLbfgsMem][RA_MAX_M];
     double Y[kMaxLbfgsMem][RA_MAX_M];
     double rho[kMaxLbfgsMem];
-    double hist[kHist][4];        // eval, g, U_best, gap
+    double hist[kHist][kHistCols];
 };
 
 }  // namespace ra

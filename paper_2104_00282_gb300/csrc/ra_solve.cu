@@ -159,14 +159,27 @@ constexpr int kLpThreads = 256;
 // tableau simplex in FP64 (Bland's rule) started from the best single
 // feasible candidate.  The weights are re-checked against the constraints in
 // FP64 before the bound is used.
+struct LpShared {
+    double T[kLpRows][kLpCols];
+    double Cr[kCand][RA_MAX_M];                        // candidate usage, staged
+    double CU[kCand];                                  // candidate utility, staged
+};
+
 __global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, const EvalOut *ev)
 {
-    __shared__ double T[kLpRows][kLpCols];
+    extern __shared__ __align__(16) unsigned char lp_dyn[];
+    LpShared &S = *reinterpret_cast<LpShared *>(lp_dyn);
+    auto &T = S.T;
+    auto &Cr = S.Cr;
+    auto &CU = S.CU;
+    __shared__ double th[kCand];
     __shared__ double fac[kLpRows];
-    __shared__ double Rs[RA_MAX_M];
+    __shared__ double Rr[RA_MAX_M];                    // R
+    __shared__ double Ri[RA_MAX_M];                    // 1 / row scale
     __shared__ int basis[RA_MAX_M + 1];
-    __shared__ int s_enter, s_leave, s_slotU, s_slotS, s_k0, s_run;
-    __shared__ double s_uscale;
+    __shared__ int feas[kCand];
+    __shared__ int s_enter, s_leave, s_slotU, s_slotS, s_k0, s_run, s_degen, s_iters, s_ok;
+    __shared__ double s_ius, s_U;
     const int tid = threadIdx.x;
     if (st->done) return;
     const int m = st->m;
@@ -199,9 +212,13 @@ __global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, con
         }
         s_slotU = su;
         s_slotS = ss;
-        s_run = st->use_master && count >= 2 && !(st->gap <= st->tol);
+        // the bound matters most near convergence: while the gap is above
+        // 1e-2 the LP runs on every fourth evaluation only
+        s_run = st->use_master && count >= 2 && !(st->gap <= st->tol) &&
+                (st->gap < 1e-2 || (st->evals & 3) == 0);
         st->U_master = -inf;
         st->mu_ok = 0;
+        st->lp_iters = 0;
     }
     __syncthreads();
     if (tid < m) {
@@ -213,133 +230,194 @@ __global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, con
             st->cand_r[s_slotS][tid] = fmin(st->r_prev[tid], st->R[tid]);
             st->cand_lam[s_slotS][tid] = st->lam_prev_eval[tid];
         }
-        Rs[tid] = st->R[tid] > 0.0 ? st->R[tid] : 1.0;
+        Rr[tid] = st->R[tid];
+        Ri[tid] = st->R[tid] > 0.0 ? 1.0 / st->R[tid] : 1.0;
     }
     __syncthreads();
     if (!s_run) return;
     const int N = st->cand_count;
     const int cols = N + m + 1, rhs = N + m;
-    // best single feasible candidate
+    // stage the candidates in shared memory (coalesced, all threads)
+    for (int idx = tid; idx < N * m; idx += kLpThreads) Cr[idx / m][idx % m] = st->cand_r[idx / m][idx % m];
+    if (tid < N) CU[tid] = st->cand_U[tid];
+    __syncthreads();
+    if (tid < N) {
+        int f = isfinite(CU[tid]) ? 1 : 0;
+        for (int j = 0; j < m; ++j) f &= Cr[tid][j] <= Rr[j] ? 1 : 0;
+        feas[tid] = f;
+    }
+    __syncthreads();
+    // best single feasible candidate (the starting basis) and the objective scale
     if (tid == 0) {
         int k0 = -1;
         double best = -inf, us = 1.0;
         for (int k = 0; k < N; ++k) {
-            us = fmax(us, fabs(st->cand_U[k]));
-            bool feas = true;
-            for (int j = 0; j < m; ++j) feas = feas && st->cand_r[k][j] <= st->R[j];
-            if (feas && st->cand_U[k] > best) {
-                best = st->cand_U[k];
+            if (isfinite(CU[k])) us = fmax(us, fabs(CU[k]));
+            if (feas[k] && CU[k] > best) {
+                best = CU[k];
                 k0 = k;
             }
         }
         s_k0 = k0;
-        s_uscale = us;
+        s_ius = 1.0 / us;
     }
     __syncthreads();
     const int k0 = s_k0;
     if (k0 < 0) return;
-    const double us = s_uscale;
+    const double ius = s_ius;
     for (int idx = tid; idx < (m + 2) * cols; idx += kLpThreads) {
         const int i = idx / cols, c = idx % cols;
         double v = 0.0;
         if (i < m) {                                   // resource rows, basis: slack i
-            if (c < N) v = c == k0 ? 0.0 : (st->cand_r[c][i] - st->cand_r[k0][i]) / Rs[i];
+            if (c < N) v = (c == k0 || !isfinite(CU[c])) ? 0.0 : (Cr[c][i] - Cr[k0][i]) * Ri[i];
             else if (c < rhs) v = (c - N == i) ? 1.0 : 0.0;
-            else v = (st->R[i] - st->cand_r[k0][i]) / Rs[i];
+            else v = (Rr[i] - Cr[k0][i]) * Ri[i];
         } else if (i == m) {                           // convexity row, basis: theta_k0
             v = c < N ? 1.0 : (c == rhs ? 1.0 : 0.0);
         } else {                                       // reduced costs; rhs holds -value
-            if (c < N) v = c == k0 ? 0.0 : (st->cand_U[c] - st->cand_U[k0]) / us;
-            else if (c == rhs) v = -st->cand_U[k0] / us;
+            if (c < N) v = (c == k0 || !isfinite(CU[c])) ? 0.0 : (CU[c] - CU[k0]) * ius;
+            else if (c == rhs) v = -CU[k0] * ius;
         }
         T[i][c] = v;
     }
     if (tid < m) basis[tid] = N + tid;
-    if (tid == 0) basis[m] = k0;
+    if (tid == 0) {
+        basis[m] = k0;
+        s_degen = 0;
+        s_iters = 0;
+    }
     __syncthreads();
     for (int iter = 0; iter < 8 * kLpRows; ++iter) {
-        if (tid == 0) {
-            s_enter = 0x7fffffff;
-            s_leave = -1;
-        }
-        __syncthreads();
-        for (int c = tid; c < N + m; c += kLpThreads)
-            if (T[m + 1][c] > 1e-12) atomicMin(&s_enter, c);
-        __syncthreads();
-        const int e = s_enter;
-        if (e == 0x7fffffff) break;                    // optimal
+        // pricing: largest reduced cost (Dantzig); after a run of degenerate
+        // pivots switch to the lowest index with a positive one (Bland),
+        // which cannot cycle
+        const bool bland = s_degen > kLpRows;
         if (tid < 32) {
-            // ratio test over the m + 1 constraint rows; ties to the lowest basis index
-            double br = inf;
-            int bb = 0x7fffffff, brow = -1;
-            for (int i = tid; i <= m; i += 32) {
-                const double a = T[i][e];
-                if (a > 1e-12) {
-                    const double rr = fmax(T[i][rhs], 0.0) / a;
-                    if (rr < br || (rr == br && basis[i] < bb)) {
-                        br = rr;
-                        bb = basis[i];
-                        brow = i;
-                    }
+            // reduced costs are in units of max|U_k|: 1e-11 is far below any
+            // gap that matters and above the rounding the pivots accumulate
+            double bv = 1e-11;
+            int bc = 0x7fffffff;
+            for (int c = tid; c < N + m; c += 32) {
+                const double d = T[m + 1][c];
+                if (bland ? (d > 1e-11 && c < bc) : (d > bv)) {
+                    bv = d;
+                    bc = c;
                 }
             }
             for (int off = 16; off > 0; off >>= 1) {
-                const double orr = __shfl_xor_sync(0xffffffffu, br, off);
-                const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
-                const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
-                if (orr < br || (orr == br && ob < bb)) {
-                    br = orr;
-                    bb = ob;
-                    brow = orow;
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                if (bland ? (oc < bc) : (ov > bv || (ov == bv && oc < bc))) {
+                    bv = ov;
+                    bc = oc;
                 }
             }
-            if (tid == 0) s_leave = brow;
+            // ratio test over the m + 1 constraint rows, division-free:
+            // rhs_i / a_i < rhs_b / a_b  <=>  rhs_i a_b < rhs_b a_i  (a > 0);
+            // ties to the lowest basis index
+            int brow = -1, bb = 0x7fffffff;
+            double bnum = 0.0, bden = 1.0;
+            if (bc != 0x7fffffff) {
+                for (int i = tid; i <= m; i += 32) {
+                    const double a = T[i][bc];
+                    if (a > 1e-12) {
+                        const double num = fmax(T[i][rhs], 0.0);
+                        const double l = num * bden, r = bnum * a;
+                        if (brow < 0 || l < r || (l == r && basis[i] < bb)) {
+                            bnum = num;
+                            bden = a;
+                            bb = basis[i];
+                            brow = i;
+                        }
+                    }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double onum = __shfl_xor_sync(0xffffffffu, bnum, off);
+                    const double oden = __shfl_xor_sync(0xffffffffu, bden, off);
+                    const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+                    const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
+                    if (orow < 0) continue;
+                    const double l = onum * bden, r = bnum * oden;
+                    if (brow < 0 || l < r || (l == r && ob < bb)) {
+                        bnum = onum;
+                        bden = oden;
+                        bb = ob;
+                        brow = orow;
+                    }
+                }
+            }
+            if (tid == 0) {
+                s_enter = bc;
+                s_leave = brow;
+                s_degen = (brow >= 0 && bnum <= 0.0) ? s_degen + 1 : 0;
+            }
         }
         __syncthreads();
-        const int pr = s_leave;
-        if (pr < 0) break;                             // unbounded direction (cannot occur)
+        const int e = s_enter, pr = s_leave;
+        if (e == 0x7fffffff || pr < 0) break;          // optimal (or no bounded step)
         if (tid < m + 2) fac[tid] = T[tid][e];
         __syncthreads();
-        const double piv = fac[pr];
-        for (int c = tid; c < cols; c += kLpThreads) T[pr][c] /= piv;
+        const double ipiv = 1.0 / fac[pr];
+        for (int c = tid; c < cols; c += kLpThreads) T[pr][c] *= ipiv;
         __syncthreads();
         for (int idx = tid; idx < (m + 2) * cols; idx += kLpThreads) {
             const int i = idx / cols, c = idx % cols;
             if (i != pr) T[i][c] -= fac[i] * T[pr][c];
         }
-        if (tid == 0) basis[pr] = e;
+        if (tid == 0) {
+            basis[pr] = e;
+            s_iters = iter + 1;
+        }
         __syncthreads();
     }
-    // weights, exact re-check and the bound in original units
-    if (tid < kCand) st->lp_theta[tid] = 0.0;
+    // weights, exact re-check against the limits, and the bound in original units
+    if (tid < kCand) th[tid] = 0.0;
     __syncthreads();
     if (tid == 0) {
         double tsum = 0.0;
         for (int i = 0; i <= m; ++i)
             if (basis[i] < N) {
-                const double th = fmax(T[i][rhs], 0.0);
-                st->lp_theta[basis[i]] = th;
-                tsum += th;
+                const double t = fmax(T[i][rhs], 0.0);
+                th[basis[i]] = t;
+                tsum += t;
             }
-        bool ok = tsum > 0.5;
+        s_ok = tsum > 0.5;
+        const double inv = s_ok ? 1.0 / tsum : 0.0;
         double U = 0.0;
-        if (ok) {
-            for (int k = 0; k < N; ++k) {
-                st->lp_theta[k] /= tsum;
-                U += st->lp_theta[k] * st->cand_U[k];
-            }
-            for (int j = 0; j < m && ok; ++j) {
-                double r = 0.0;
-                for (int k = 0; k < N; ++k) r += st->lp_theta[k] * st->cand_r[k][j];
-                ok = r <= st->R[j] * (1.0 + 1e-12);
-            }
+        for (int k = 0; k < N; ++k) {
+            th[k] *= inv;
+            if (th[k] > 0.0) U += th[k] * CU[k];
         }
-        st->U_master = ok ? U : -inf;
+        s_U = U;
     }
-    // resource duals of the scaled LP: mu_j = -(reduced cost of slack j) us / Rs_j;
+    __syncthreads();
+    if (tid < m && s_ok) {
+        double r = 0.0;
+        for (int k = 0; k < N; ++k)
+            if (th[k] > 0.0) r += th[k] * Cr[k][tid];
+        if (!(r <= Rr[tid] * (1.0 + 1e-12))) atomicAnd(&s_ok, 0);
+    }
+    __syncthreads();
+    if (tid < kCand) st->lp_theta[tid] = tid < N ? th[tid] : 0.0;
+    // resource duals of the scaled LP: mu_j = -(reduced cost of slack j) max|U| / R_j;
     // (mu, nu) minimise the cutting-plane model max_k [U_k + mu^T (R - r_k)] of g
-    if (tid < m) st->mu_lp[tid] = fmax(-T[m + 1][N + tid], 0.0) * us / Rs[tid];
-    if (tid == 0) st->mu_ok = isfinite(st->U_master) ? 1 : 0;
+    if (tid < m) st->mu_lp[tid] = fmax(-T[m + 1][N + tid], 0.0) * Ri[tid] / ius;
+    if (tid == 0) {
+        st->U_master = s_ok ? s_U : -inf;
+        st->mu_ok = s_ok ? 1 : 0;
+        st->lp_iters = s_iters;
+    }
+}
+
+// lambda_trial = max(v, floor); with a zero floor, prices below 1e-12 of the
+// largest one, or below 1e-30, are set to exactly zero (the FP32 kernels
+// treat prices under 1e-30 as zero: their inverse would overflow and tie).
+__device__ void set_trial(SolverState *st, int j, bool active, double v)
+{
+    v = active ? fmax(v, st->lam_floor) : 0.0;
+    const double vmax = wmax(v);
+    if (st->lam_floor == 0.0 && (v < 1e-12 * vmax || v < 1e-30)) v = 0.0;
+    if (active) st->lam_trial[j] = v;
 }
 
 // Store the pair (s, y) = (lambda_t - lambda_cur, q_t - q_cur) when it has
@@ -484,7 +562,7 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
         }
     }
     __syncwarp();
-    if (active) st->lam_trial[j] = fmax(st->lam_cur[j] + st->step * st->d[j], st->lam_floor);
+    set_trial(st, j, active, st->lam_cur[j] + st->step * st->d[j]);
 }
 
 // One update after the evaluation of st->lam_trial (results in *ev).
@@ -558,7 +636,10 @@ __global__ void __launch_bounds__(32)
     const bool improved = g_t < g_best;
     if (improved) {
         g_best = g_t;
-        if (active) st->lam_best[j] = lam_t;
+        if (active) {
+            st->lam_best[j] = lam_t;
+            st->q_best[j] = q_t;
+        }
     }
     // column scaling of this evaluation, consumed by the next pass
     if (active) st->s_lag[j] = r_t > st->R[j] ? st->R[j] / r_t : 1.0;
@@ -577,6 +658,8 @@ __global__ void __launch_bounds__(32)
             st->hist[h][1] = g_t;
             st->hist[h][2] = U_best;
             st->hist[h][3] = gap;
+            st->hist[h][4] = st->U_master;
+            st->hist[h][5] = st->lp_iters;
             st->hist_len = h + 1;
         }
     }
@@ -605,10 +688,8 @@ __global__ void __launch_bounds__(32)
                 if (j == 0) st->phase = 1;
             }
             const double a = st->sg_a0 / sqrt(static_cast<double>(evals));
-            if (active) {
-                st->lam_cur[j] = lam_t;
-                st->lam_trial[j] = fmax(lam_t - a * q_t, st->lam_floor);
-            }
+            if (active) st->lam_cur[j] = lam_t;
+            set_trial(st, j, active, lam_t - a * q_t);
             if (j == 0) st->k = st->k + 1;
         } else {
             lbfgs_update(st, j, m, active, g_t, q_t, lam_t);
@@ -644,7 +725,7 @@ int32_t solve_history(ra_problem *p, double *hist, int32_t cap)
     if (e != cudaSuccess) return -1;
     if (len > cap) len = cap;
     if (len <= 0) return 0;
-    e = cudaMemcpyAsync(hist, p->st->hist, sizeof(double) * 4 * len, cudaMemcpyDeviceToHost, p->stream);
+    e = cudaMemcpyAsync(hist, p->st->hist, sizeof(double) * kHistCols * len, cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     return e == cudaSuccess ? len : -1;
 }
@@ -696,6 +777,9 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
+    if ((e = cudaFuncSetAttribute(master_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
+        return fail(RA_ECUDA, "master kernel attribute: %s", cudaGetErrorString(e));
     DualParams dp{};
     dp.A = p->A;
     dp.kind = p->kind;
@@ -742,7 +826,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 cudaError_t e1 = launch_dual(p, dp, s);
-                master_kernel<<<1, kLpThreads, 0, s>>>(st, p->ev);
+                master_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev);
                 solver_update_kernel<<<1, 32, 0, s>>>(st, p->ev, pingpong, lag_on, p->status, cond,
                                                       1, nullptr);
                 cudaError_t e2 = cudaGetLastError();
@@ -767,7 +851,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             for (int k = 0; k < 8; ++k) {
                 if ((e = launch_dual(p, dp, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
-                master_kernel<<<1, kLpThreads, 0, s>>>(st, p->ev);
+                master_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev);
                 solver_update_kernel<<<1, 32, 0, s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
                                                       done_flag);
             }

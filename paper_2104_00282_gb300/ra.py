@@ -157,6 +157,7 @@ def ra_solve(h, lam_out, opts=None, lam0=None, lam_lb=None, allow_notconv=True):
 
 
 RA_MAX_CERT = 64
+RA_HIST_COLS = 6
 
 
 def ra_solve_certificate(h, m):
@@ -175,7 +176,7 @@ def ra_solve_certificate(h, m):
 
 def ra_solve_history(h, cap=512):
     import numpy as np
-    buf = np.zeros((cap, 4))
+    buf = np.zeros((cap, RA_HIST_COLS))
     k = lib().ra_solve_history(h, ctypes.c_void_p(buf.ctypes.data), cap)
     if k < 0:
         raise RaError(RA_ECUDA, lib().ra_last_error().decode())
@@ -281,14 +282,15 @@ class AllocationProblem:
         return ra_solve_certificate(self.handle, self.m)
 
     def history(self):
-        """Rows (evaluation, g, best U_lb, relative gap) of the last solve."""
+        """Rows (evaluation, g, best U_lb, relative gap, master-LP bound, LP
+        pivots) of the last solve."""
         return ra_solve_history(self.handle)
 
     def verbose_log(self, every=5):
         """The paper's verbose lines (Section 6.1): per-job utility, dual value, gap."""
         h = self.history()
         lines = []
-        for k, (ev, g, ub, gap) in enumerate(h):
+        for k, (ev, g, ub, gap) in enumerate(h[:, :4]):
             if k % every == 0:
                 lines.append(f"iteration {int(ev):02d} | utility={ub / self.n:.6g} | "
                              f"dual_value={g / self.n:.6g} | gap={gap:.2e}")
