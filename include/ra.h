@@ -240,6 +240,60 @@ ra_status ra_eval_dual_static(int64_t n, int32_t m, const float *A, const uint8_
                               const double *lambda, uint32_t flags, void *stream, double *g,
                               double *q);
 
+/*
+ * Batched price discovery (a throughput mode; the paper solves one problem at
+ * a time, Algorithm 2 of Section 5): P independent problems of the form
+ * (e-res-alloc), each with its own n_p, m_p, data and capacities, solved
+ * together on one GPU.  Each loop trip evaluates the dual of every problem
+ * still iterating in one streaming pass per width class (m <= 4, 8, 16, 32),
+ * then runs each problem's master LP and price update (one CTA per problem);
+ * a problem whose relative gap has met tol_rel, or that has reached
+ * max_evals, drops out of all three.  Per problem the arithmetic is that of
+ * ra_solve.
+ */
+typedef struct ra_batch ra_batch; /* opaque; owns its device workspace */
+
+/*
+ * ra_batch_create -- describe P problems.  n, m: host arrays of P sizes
+ * (1 <= n_p <= 2^31, 1 <= m_p <= RA_MAX_M).  A, kind, w, param, R: host arrays
+ * of P DEVICE pointers laid out as in ra_problem_create (A row-major n_p x
+ * m_p, A/kind/w/param 16-byte aligned); the data is not copied and must stay
+ * valid until ra_batch_destroy.  flags: RA_JOB_CAP or RA_NO_JOB_CAP.
+ * Allocates about 20 bytes per job (two generations of the 10-byte
+ * lower-bound record) plus about 100 KB of solver state per problem.
+ * Returns RA_EINVAL on bad sizes, NULL pointers or misalignment (naming the
+ * problem), RA_ENOMEM when the workspace does not fit.
+ */
+ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const float *const *A,
+                          const uint8_t *const *kind, const float *const *w,
+                          const float *const *param, const double *const *R, uint32_t flags,
+                          void *stream, ra_batch **out);
+
+/* Waits for the batch's stream, then frees its workspace. */
+void ra_batch_destroy(ra_batch *b);
+
+/* Length of the concatenated price vector, sum_p m_p (problem p's prices
+ * follow those of problems 0 .. p-1), or -1 for NULL. */
+int64_t ra_batch_prices(const ra_batch *b);
+
+/*
+ * ra_batch_solve -- solve every problem of the batch.
+ *   opts        host, may be NULL (defaults of ra_solve; one set for all)
+ *   lambda0     device, sum_p m_p FP64 start prices (concatenated), or NULL
+ *               for Eq. e-initialization of each problem
+ *   lambda_out  device, sum_p m_p FP64: each problem's prices with the best
+ *               dual value
+ *   infos       host, P records as ra_solve returns them
+ *   seconds     host, P doubles or NULL: device time from the start of the
+ *               call's GPU work until problem p stopped (its time to
+ *               tolerance)
+ * Synchronises.  RA_ENOTCONV / RA_EUNBOUNDED when at least one problem ended
+ * that way (its infos entry says which); RA_ETIMEOUT when a device wait gave
+ * up (all results are then unreliable).
+ */
+ra_status ra_batch_solve(ra_batch *b, const ra_solve_opts *opts, const double *lambda0,
+                         double *lambda_out, ra_solve_info *infos, double *seconds);
+
 /* Static strings; ra_last_error() is thread-local and valid until the next call. */
 const char *ra_status_string(ra_status s);
 const char *ra_last_error(void);

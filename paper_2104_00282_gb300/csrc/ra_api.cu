@@ -311,4 +311,200 @@ ra_status ra_recover_primal(ra_problem *p, const double *lambda, int32_t *jstar,
     return RA_OK;
 }
 
+
+// ---------------------------------------------------------------------------- batches
+
+void ra_batch_destroy(ra_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    cudaFree(b->probs);
+    cudaFree(b->st);
+    cudaFree(b->ev);
+    cudaFree(b->pingpong);
+    cudaFree(b->lag_on);
+    cudaFree(b->lam_off);
+    cudaFree(b->active);
+    cudaFree(b->ticket);
+    cudaFree(b->status);
+    cudaFree(b->t0);
+    cudaFree(b->info);
+    cudaFree(b->secs);
+    cudaFree(b->lam_tmp);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(b->lbt_pool[k]);
+        cudaFree(b->lbj_pool[k]);
+    }
+    for (int c = 0; c < 4; ++c) {
+        cudaFree(b->chunk_prob[c]);
+        cudaFree(b->chunk_tile0[c]);
+        cudaFree(b->chunk_ntiles[c]);
+        cudaFree(b->partials[c]);
+    }
+    delete[] b->n_h;
+    delete[] b->m_h;
+    delete[] b->lam_off_h;
+    delete b;
+}
+
+ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const float *const *A,
+                          const uint8_t *const *kind, const float *const *w,
+                          const float *const *param, const double *const *R, uint32_t flags,
+                          void *stream, ra_batch **out)
+{
+    ra::g_err[0] = 0;
+    if (!out) return fail(RA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (P < 1) return fail(RA_EINVAL, "P = %d must be >= 1", P);
+    if (!n || !m || !A || !kind || !w || !param || !R) return fail(RA_EINVAL, "an argument array is NULL");
+    if (flags & ~RA_NO_JOB_CAP) return fail(RA_EINVAL, "only RA_NO_JOB_CAP may be set (flags 0x%x)", flags);
+    long long total = 0, m_total = 0;
+    for (int p = 0; p < P; ++p) {
+        if (n[p] < 1 || n[p] > (int64_t(1) << 31))
+            return fail(RA_EINVAL, "problem %d: n = %lld must lie in [1, 2^31]", p, (long long)n[p]);
+        if (m[p] < 1 || m[p] > RA_MAX_M)
+            return fail(RA_EINVAL, "problem %d: m = %d must lie in [1, %d]", p, m[p], RA_MAX_M);
+        if (!A[p] || !kind[p] || !w[p] || !param[p] || !R[p])
+            return fail(RA_EINVAL, "problem %d: a data pointer is NULL", p);
+        if (!ra::aligned16(A[p]) || !ra::aligned16(kind[p]) || !ra::aligned16(w[p]) ||
+            !ra::aligned16(param[p]))
+            return fail(RA_EINVAL, "problem %d: A, kind, w and param must be 16-byte aligned", p);
+        total += n[p];
+        m_total += m[p];
+    }
+    ra_batch *b = new (std::nothrow) ra_batch();
+    if (!b) return fail(RA_ENOMEM, "host allocation failed");
+    memset(b, 0, sizeof(*b));
+    b->P = P;
+    b->flags = flags;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->n_h = new (std::nothrow) long long[P];
+    b->m_h = new (std::nothrow) int[P];
+    b->lam_off_h = new (std::nothrow) long long[P];
+    if (!b->n_h || !b->m_h || !b->lam_off_h) {
+        ra_batch_destroy(b);
+        return fail(RA_ENOMEM, "host allocation failed");
+    }
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) {
+        ra_batch_destroy(b);
+        return fail(RA_ECUDA, "device query: %s", cudaGetErrorString(e));
+    }
+    // problems -> width classes -> chunks of up to kChunkTiles tiles
+    std::vector<ra::BatchProblem> probs(P);
+    std::vector<int32_t> cp[4], ct0[4], cnt[4];
+    long long job_off = 0;
+    for (int p = 0; p < P; ++p) {
+        b->n_h[p] = n[p];
+        b->m_h[p] = m[p];
+        b->lam_off_h[p] = b->m_total;
+        b->m_total += m[p];
+        ra::BatchProblem &q = probs[p];
+        q.A = A[p];
+        q.kind = kind[p];
+        q.w = w[p];
+        q.param = param[p];
+        q.R = R[p];
+        q.n = n[p];
+        q.m = m[p];
+        q.cls = m[p] <= 4 ? 0 : m[p] <= 8 ? 1 : m[p] <= 16 ? 2 : 3;
+        const int c = q.cls;
+        const long long tiles = (n[p] + ra::kTile - 1) / ra::kTile;
+        q.chunk_begin = static_cast<int>(cp[c].size());
+        for (long long t0 = 0; t0 < tiles; t0 += ra::kChunkTiles) {
+            cp[c].push_back(p);
+            ct0[c].push_back(static_cast<int32_t>(t0));
+            cnt[c].push_back(static_cast<int32_t>(tiles - t0 < ra::kChunkTiles ? tiles - t0 : ra::kChunkTiles));
+        }
+        q.chunk_end = static_cast<int>(cp[c].size());
+        q.lbt[0] = q.lbt[1] = nullptr;
+        q.lbj[0] = q.lbj[1] = nullptr;
+        job_off += n[p];
+    }
+    bool ok = true;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
+    };
+    alloc(reinterpret_cast<void **>(&b->probs), sizeof(ra::BatchProblem) * P);
+    alloc(reinterpret_cast<void **>(&b->st), sizeof(ra::SolverState) * P);
+    alloc(reinterpret_cast<void **>(&b->ev), sizeof(ra::EvalOut) * P);
+    alloc(reinterpret_cast<void **>(&b->pingpong), sizeof(int32_t) * P);
+    alloc(reinterpret_cast<void **>(&b->lag_on), sizeof(int32_t) * P);
+    alloc(reinterpret_cast<void **>(&b->lam_off), sizeof(long long) * P);
+    alloc(reinterpret_cast<void **>(&b->active), sizeof(int32_t) * 4);
+    alloc(reinterpret_cast<void **>(&b->ticket), sizeof(unsigned) * P);
+    alloc(reinterpret_cast<void **>(&b->status), sizeof(int) * 4);
+    alloc(reinterpret_cast<void **>(&b->t0), sizeof(unsigned long long));
+    alloc(reinterpret_cast<void **>(&b->info), sizeof(ra_solve_info) * P);
+    alloc(reinterpret_cast<void **>(&b->secs), sizeof(double) * P);
+    alloc(reinterpret_cast<void **>(&b->lam_tmp), sizeof(double) * b->m_total);
+    for (int k = 0; k < 2; ++k) {
+        alloc(reinterpret_cast<void **>(&b->lbt_pool[k]), sizeof(float2) * total);
+        alloc(reinterpret_cast<void **>(&b->lbj_pool[k]), sizeof(uchar2) * total);
+    }
+    for (int c = 0; c < 4; ++c) {
+        b->nchunks[c] = static_cast<int>(cp[c].size());
+        if (!b->nchunks[c]) continue;
+        alloc(reinterpret_cast<void **>(&b->chunk_prob[c]), sizeof(int32_t) * b->nchunks[c]);
+        alloc(reinterpret_cast<void **>(&b->chunk_tile0[c]), sizeof(int32_t) * b->nchunks[c]);
+        alloc(reinterpret_cast<void **>(&b->chunk_ntiles[c]), sizeof(int32_t) * b->nchunks[c]);
+        alloc(reinterpret_cast<void **>(&b->partials[c]), sizeof(double) * ra::kPartW * b->nchunks[c]);
+    }
+    if (!ok) {
+        (void)cudaGetLastError();
+        ra_batch_destroy(b);
+        return fail(RA_ENOMEM, "batch workspace allocation (about %lld bytes of records) failed",
+                    (long long)(20 * total));
+    }
+    job_off = 0;
+    for (int p = 0; p < P; ++p) {
+        for (int k = 0; k < 2; ++k) {
+            probs[p].lbt[k] = b->lbt_pool[k] + job_off;
+            probs[p].lbj[k] = b->lbj_pool[k] + job_off;
+        }
+        job_off += n[p];
+    }
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+        if (!b->nchunks[c]) continue;
+        int per_sm = 0;
+        e = ra::batch_configure(4 << c, &per_sm);
+        if (e != cudaSuccess) break;
+        if (per_sm < 1) per_sm = 1;
+        const long long g = static_cast<long long>(b->num_sms) * per_sm;
+        b->grid[c] = static_cast<int>(g < b->nchunks[c] ? g : b->nchunks[c]);
+        const long long gi = static_cast<long long>(b->num_sms) * 4;
+        b->grid_init[c] = static_cast<int>(gi < b->nchunks[c] ? gi : b->nchunks[c]);
+        e = cudaMemcpy(b->chunk_prob[c], cp[c].data(), sizeof(int32_t) * b->nchunks[c], cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->chunk_tile0[c], ct0[c].data(), sizeof(int32_t) * b->nchunks[c], cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->chunk_ntiles[c], cnt[c].data(), sizeof(int32_t) * b->nchunks[c], cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(b->probs, probs.data(), sizeof(ra::BatchProblem) * P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->lam_off, b->lam_off_h, sizeof(long long) * P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->ticket, 0, sizeof(unsigned) * P);
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(b->st, 0, sizeof(ra::SolverState) * P);
+    if (e == cudaSuccess) e = cudaMemset(b->ev, 0, sizeof(ra::EvalOut) * P);
+    if (e == cudaSuccess) e = cudaMemset(b->pingpong, 0, sizeof(int32_t) * P);
+    if (e == cudaSuccess) e = cudaMemset(b->lag_on, 0, sizeof(int32_t) * P);
+    if (e != cudaSuccess) {
+        ra_batch_destroy(b);
+        return fail(RA_ECUDA, "batch workspace init: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return RA_OK;
+}
+
+ra_status ra_batch_solve(ra_batch *b, const ra_solve_opts *opts, const double *lambda0,
+                         double *lambda_out, ra_solve_info *infos, double *seconds)
+{
+    if (!b) return fail(RA_EINVAL, "NULL batch");
+    return ra::batch_solve(b, opts, lambda0, lambda_out, infos, seconds);
+}
+
+int64_t ra_batch_prices(const ra_batch *b) { return b ? static_cast<int64_t>(b->m_total) : -1; }
+
 }  // extern "C"

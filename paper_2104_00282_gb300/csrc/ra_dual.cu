@@ -751,6 +751,352 @@ __global__ void __launch_bounds__(kTile, 2)
         if (tid < m) lam1[tid] = red[0][4 + tid] / static_cast<double>(n);
 }
 
+// ---------------------------------------------------------------------------- batched kernels
+
+// Column sums of a warp's x block without shared memory: column c is summed
+// by a butterfly over the lanes' (at most two) nonzeros and lane c adds it.
+template <typename Real>
+__device__ __forceinline__ void warp_rsum_shfl(int m, int lane, const JobSol<Real> &s, double &racc)
+{
+    for (int c = 0; c < m; ++c) {
+        float v = (s.cP == c ? static_cast<float>(s.xP) : 0.f) + (s.cQ == c ? static_cast<float>(s.xQ) : 0.f);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == c) racc += static_cast<double>(v);
+    }
+}
+
+// Sequence of tiles of this CTA in a batched evaluation: chunks blockIdx.x,
+// blockIdx.x + G, ... of the class's chunk list, each a run of up to
+// kChunkTiles tiles of one problem; chunks of problems already converged
+// are skipped.  The producer (TMA issuer) and the consumers walk the same
+// sequence with separate cursors.
+struct TileCursor {
+    long long c;     // chunk index (>= nchunks: end)
+    int k;           // tile within the chunk
+};
+
+__device__ __forceinline__ bool chunk_live(const BatchDualArgs &B, long long c)
+{
+    return B.st[B.chunk_prob[c]].done == 0;
+}
+
+__device__ __forceinline__ void cursor_first(const BatchDualArgs &B, TileCursor &cur)
+{
+    cur.c = blockIdx.x;
+    cur.k = 0;
+    while (cur.c < B.nchunks && !chunk_live(B, cur.c)) cur.c += gridDim.x;
+}
+
+__device__ __forceinline__ void cursor_next(const BatchDualArgs &B, TileCursor &cur)
+{
+    if (++cur.k < B.chunk_ntiles[cur.c]) return;
+    cur.k = 0;
+    do {
+        cur.c += gridDim.x;
+    } while (cur.c < B.nchunks && !chunk_live(B, cur.c));
+}
+
+__device__ __forceinline__ bool tile_full(const BatchDualArgs &B, const TileCursor &cur)
+{
+    const BatchProblem &P = B.probs[B.chunk_prob[cur.c]];
+    const long long t = B.chunk_tile0[cur.c] + cur.k;
+    return (t + 1) * kTile <= P.n;
+}
+
+// Batched dual evaluation for every live problem of one width class.  Per
+// tile the work is exactly that of dual_tma_kernel (TMA ring for full tiles,
+// direct loads for a problem's ragged last tile); prices are reloaded at each
+// chunk start, and each chunk's sums go to its own FP64 partial slot.  The
+// last chunk of a problem to finish (per-problem ticket) adds that problem's
+// partials in chunk order and writes its EvalOut, so the results equal a
+// deterministic single-problem evaluation up to the order of additions.
+template <int MT, bool CAP>
+__global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t bars[kMaxStages];
+    __shared__ float lam_s[RA_MAX_M];
+    __shared__ float s_s[RA_MAX_M];
+    __shared__ double red[kWarps][kPartW];
+    __shared__ int is_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int C = MT / 4;
+    const int stages = B.stages;
+    unsigned char *smem = align128<MT>(smem_dyn);
+    if (tid == 0) {
+        for (int s2 = 0; s2 < stages; ++s2) mbar_init(&bars[s2], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // producer: issue the next full tile of the sequence into its stage
+    TileCursor prod;
+    long long issued = 0;
+    if (tid == 0) cursor_first(B, prod);
+    auto issue_next = [&]() {
+        while (prod.c < B.nchunks && !tile_full(B, prod)) cursor_next(B, prod);
+        if (prod.c >= B.nchunks) return;
+        const BatchProblem &P = B.probs[B.chunk_prob[prod.c]];
+        const int m = P.m;
+        const long long j0 = static_cast<long long>(B.chunk_tile0[prod.c] + prod.k) * kTile;
+        const size_t a_bytes = static_cast<size_t>(kTile) * m * 4;
+        const size_t st_bytes = a_bytes + kTile * 9;
+        const int st = static_cast<int>(issued % stages);
+        unsigned char *base = smem + st * StageLayout<MT>::bytes(MT);
+        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
+        bulk_load(base, P.A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
+        bulk_load(base + a_bytes, P.w + j0, kTile * 4, &bars[st]);
+        bulk_load(base + a_bytes + kTile * 4, P.param + j0, kTile * 4, &bars[st]);
+        bulk_load(base + a_bytes + kTile * 8, P.kind + j0, kTile, &bars[st]);
+        ++issued;
+        cursor_next(B, prod);
+    };
+    if (tid == 0)
+        for (int s2 = 0; s2 < stages; ++s2) issue_next();
+
+    TileCursor cur;
+    cursor_first(B, cur);
+    long long consumed = 0;
+    float lam_r[MT], mu_r[MT];
+    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
+    while (cur.c < B.nchunks) {
+        const int p = B.chunk_prob[cur.c];
+        const BatchProblem &P = B.probs[p];
+        const int m = P.m;
+        const bool grouped = (m == MT);
+        const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
+        const int pp = B.pingpong[p] & 1;
+        const bool lag = B.lag_on[p] != 0;
+        const float2 *lbt_prev = P.lbt[pp];
+        const uchar2 *lbj_prev = P.lbj[pp];
+        float2 *lbt_out = P.lbt[pp ^ 1];
+        uchar2 *lbj_out = P.lbj[pp ^ 1];
+        if (cur.k == 0) {  // chunk start: this problem's prices
+            __syncthreads();
+            if (tid < RA_MAX_M) {
+                lam_s[tid] = tid < m ? static_cast<float>(B.st[p].lam_trial[tid]) : Fn<float>::inf();
+                s_s[tid] = (lag && tid < m) ? static_cast<float>(B.st[p].s_lag[tid]) : 1.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                const int c = colof<MT>(k, rot);
+                lam_r[k] = lam_s[c];
+                mu_r[k] = inv_price<float>(lam_s[c]);
+            }
+            hsum = uxsum = lbsum = racc = 0.0;
+        }
+        const long long t = B.chunk_tile0[cur.c] + cur.k;
+        const bool full = (t + 1) * kTile <= P.n;
+        const long long i = t * kTile + tid;
+        const bool valid = i < P.n;
+        const float *row = nullptr;
+        float *warp_rows;
+        int kind = RA_U_LINCAP;
+        float w = 1.0f, pr = 0.0f;
+        int st = 0;
+        if (full) {
+            st = static_cast<int>(consumed % stages);
+            const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>((consumed / stages) & 1));
+            if (__syncthreads_or(!ok)) {
+                // a copy never completed: record it, let the copies still in
+                // flight land (bounded) and give up
+                if (tid == 0) {
+                    atomicOr(B.status, kStatusTimeout);
+                    for (long long it2 = consumed; it2 < issued; ++it2)
+                        (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1));
+                }
+                __syncthreads();
+                return;
+            }
+            unsigned char *base = smem + st * StageLayout<MT>::bytes(MT);
+            const size_t a_bytes = static_cast<size_t>(kTile) * m * 4;
+            float *a_s = reinterpret_cast<float *>(base);
+            row = a_s + tid * m;
+            warp_rows = a_s + warp * 32 * m;
+            kind = base[a_bytes + kTile * 8 + tid];
+            w = reinterpret_cast<const float *>(base + a_bytes)[tid];
+            pr = reinterpret_cast<const float *>(base + a_bytes + kTile * 4)[tid];
+        } else {
+            // ragged last tile of a problem: direct loads (every stage of the
+            // ring may hold a copy in flight, so no shared scratch is used)
+            warp_rows = nullptr;
+            if (valid) {
+                kind = P.kind[i];
+                w = P.w[i];
+                pr = P.param[i];
+            }
+        }
+        float2 tp = make_float2(0.f, 0.f);
+        uchar2 jp = make_uchar2(255, 255);
+        if (lag && valid) {
+            tp = lbt_prev[i];
+            jp = lbj_prev[i];
+        }
+        float a[MT];
+        load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
+        JobSol<float> sol;
+        sol.cP = sol.cQ = -1;
+        sol.xP = sol.xQ = 0.f;
+        if (valid) {
+            auto fetch = [&](int k, float &av, float &lv) {
+                const int c = colof<MT>(k, rot);
+                av = row != nullptr ? row[c] : __ldg(&P.A[i * m + c]);
+                lv = lam_s[c];
+            };
+            solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, pr, sol);
+            hsum += static_cast<double>(sol.h);
+            uxsum += static_cast<double>(util<float>(kind, w, pr, sol.t));
+            if (lag) {
+                float tt = 0.f;
+                if (jp.x != 255) tt += s_s[jp.x] * tp.x;
+                if (jp.y != 255) tt += s_s[jp.y] * tp.y;
+                lbsum += static_cast<double>(util<float>(kind, w, pr, tt));
+            }
+            lbt_out[i] = make_float2(sol.tP, sol.tQ);
+            lbj_out[i] = make_uchar2(sol.cP >= 0 ? sol.cP : 255, sol.cQ >= 0 ? sol.cQ : 255);
+        }
+        if (full) warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, sol, racc);
+        else warp_rsum_shfl<float>(m, lane, sol, racc);
+        __syncthreads();  // stage consumed
+        if (full) {
+            ++consumed;
+            if (tid == 0) {
+                fence_proxy_async();
+                issue_next();
+            }
+        }
+        // chunk end: block sums -> this chunk's partial slot -> per-problem ticket
+        const bool chunk_end = cur.k + 1 >= B.chunk_ntiles[cur.c];
+        if (chunk_end) {
+            double h = warp_sum_d(hsum), ux = warp_sum_d(uxsum), lb = warp_sum_d(lbsum);
+            if (lane == 0) {
+                red[warp][0] = h;
+                red[warp][1] = ux;
+                red[warp][2] = lb;
+                red[warp][3] = 0.0;
+            }
+            if (lane < m) red[warp][4 + lane] = (grouped ? (lane / MT == 0) : true) ? racc : 0.0;
+            __syncthreads();
+            if (tid < m + 4) {
+                double v = 0.0;
+                for (int w2 = 0; w2 < kWarps; ++w2) v += red[w2][tid];
+                B.partials[static_cast<size_t>(cur.c) * kPartW + tid] = v;
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const unsigned nch = static_cast<unsigned>(P.chunk_end - P.chunk_begin);
+                is_last = (atomicAdd(&B.ticket[p], 1u) == nch - 1);
+            }
+            __syncthreads();
+            if (is_last) {
+                __threadfence();
+                if (tid < m + 4) {
+                    double v = 0.0;
+                    for (int c2 = P.chunk_begin; c2 < P.chunk_end; ++c2)
+                        v += __ldcg(&B.partials[static_cast<size_t>(c2) * kPartW + tid]);
+                    red[0][tid] = v;
+                }
+                __syncthreads();
+                EvalOut *out = B.ev + p;
+                if (tid < m) {
+                    out->r[tid] = red[0][4 + tid];
+                    out->q[tid] = P.R[tid] - red[0][4 + tid];
+                }
+                if (tid == 0) {
+                    double lr = 0.0;
+                    for (int j = 0; j < m; ++j) lr += B.st[p].lam_trial[j] * P.R[j];
+                    out->sumh = red[0][0];
+                    out->g = lr + red[0][0];
+                    out->Ux = red[0][1];
+                    out->Ulb_prev = red[0][2];
+                    B.ticket[p] = 0u;
+                }
+            }
+            __syncthreads();
+            hsum = uxsum = lbsum = racc = 0.0;
+        }
+        cursor_next(B, cur);
+    }
+}
+
+// Batched Eq. e-initialization (once per batch solve): direct loads, one
+// FP64 partial per chunk, per-problem ticket and fixed-order final sum.
+template <int MT>
+__global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, double *lam1,
+                                                           const long long *lam_off)
+{
+    __shared__ float x0_s[RA_MAX_M];
+    __shared__ double red[kWarps][kPartW];
+    __shared__ int is_last;
+    __shared__ float rows[kTile * MT];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (long long c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
+        const int p = B.chunk_prob[c];
+        const BatchProblem &P = B.probs[p];
+        const int m = P.m;
+        __syncthreads();
+        if (tid == 0) {
+            double kappa = 0.0;
+            for (int j = 0; j < m; ++j) kappa += P.R[j] / static_cast<double>(P.n);
+            const double div = (B.cap && kappa > 1.0) ? kappa : 1.0;
+            for (int j = 0; j < RA_MAX_M; ++j)
+                x0_s[j] = j < m ? static_cast<float>(P.R[j] / (static_cast<double>(P.n) * div)) : 0.0f;
+        }
+        __syncthreads();
+        double racc = 0.0;
+        for (int k = 0; k < B.chunk_ntiles[c]; ++k) {
+            const long long i = static_cast<long long>(B.chunk_tile0[c] + k) * kTile + tid;
+            const bool valid = i < P.n;
+            float a[MT];
+            float tc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                a[j] = (valid && j < m) ? __ldg(&P.A[i * m + j]) : 0.0f;
+                tc[j & 3] = fmaf(a[j], x0_s[j], tc[j & 3]);
+            }
+            const float t = (tc[0] + tc[1]) + (tc[2] + tc[3]);
+            float d = 0.0f;
+            if (valid) {
+                const int kd = P.kind[i];
+                const float wi = P.w[i], pi = P.param[i];
+                if (kd == RA_U_LOG) d = wi / t;
+                else if (kd == RA_U_POWER) d = wi * pi * exp2f((pi - 1.0f) * log2f(t));
+                else d = t < pi ? wi : 0.0f;
+            }
+            float *own = rows + tid * m;
+#pragma unroll
+            for (int j = 0; j < MT; ++j)
+                if (j < m) own[j] = d * a[j];
+            __syncwarp();
+            warp_colsum<MT, float>(rows + warp * 32 * m, m, lane, false, racc);
+        }
+        if (lane < m) red[warp][4 + lane] = racc;
+        __syncthreads();
+        if (tid < m) {
+            double v = 0.0;
+            for (int w2 = 0; w2 < kWarps; ++w2) v += red[w2][4 + tid];
+            B.partials[static_cast<size_t>(c) * kPartW + tid] = v;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) is_last = (atomicAdd(&B.ticket[p], 1u) == static_cast<unsigned>(P.chunk_end - P.chunk_begin) - 1);
+        __syncthreads();
+        if (is_last) {
+            __threadfence();
+            if (tid < m) {
+                double v = 0.0;
+                for (int c2 = P.chunk_begin; c2 < P.chunk_end; ++c2)
+                    v += __ldcg(&B.partials[static_cast<size_t>(c2) * kPartW + tid]);
+                lam1[lam_off[p] + tid] = v / static_cast<double>(P.n);
+            }
+            if (tid == 0) B.ticket[p] = 0u;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------- simple kernel
 
 // One thread per job with direct global loads; used for FP64 per-job
@@ -1193,6 +1539,73 @@ cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jsta
     default: RA_REC(32)
     }
 #undef RA_REC
+}
+
+
+int batch_stages(int mt)
+{
+    switch (mt) {
+    case 4: return mt_stages<4>(4);
+    case 8: return mt_stages<8>(8);
+    case 16: return mt_stages<16>(16);
+    default: return mt_stages<32>(32);
+    }
+}
+
+size_t batch_smem(int mt) { return batch_stages(mt) * StageLayout<4>::bytes(mt) + 128; }
+
+cudaError_t batch_configure(int mt, int *blocks_per_sm)
+{
+    const void *fn = nullptr;
+    switch (mt) {
+    case 4: fn = reinterpret_cast<const void *>(batch_dual_kernel<4, true>); break;
+    case 8: fn = reinterpret_cast<const void *>(batch_dual_kernel<8, true>); break;
+    case 16: fn = reinterpret_cast<const void *>(batch_dual_kernel<16, true>); break;
+    default: fn = reinterpret_cast<const void *>(batch_dual_kernel<32, true>); break;
+    }
+    cudaError_t e;
+#define RA_BATTR(MT)                                                                               \
+    if ((e = cudaFuncSetAttribute(batch_dual_kernel<MT, true>,                                    \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+        cudaSuccess)                                                                               \
+        return e;                                                                                  \
+    if ((e = cudaFuncSetAttribute(batch_dual_kernel<MT, false>,                                   \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+        cudaSuccess)                                                                               \
+        return e;
+    RA_BATTR(4)
+    RA_BATTR(8)
+    RA_BATTR(16)
+    RA_BATTR(32)
+#undef RA_BATTR
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kTile, batch_smem(mt));
+}
+
+cudaError_t launch_batch_dual(int mt, const BatchDualArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+#define RA_BD(MT)                                                                                  \
+    if (a.cap) batch_dual_kernel<MT, true><<<grid, kTile, smem, s>>>(a);                          \
+    else batch_dual_kernel<MT, false><<<grid, kTile, smem, s>>>(a);
+    switch (mt) {
+    case 4: RA_BD(4) break;
+    case 8: RA_BD(8) break;
+    case 16: RA_BD(16) break;
+    default: RA_BD(32) break;
+    }
+#undef RA_BD
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init(int mt, const BatchDualArgs &a, double *lam1, const long long *lam_off,
+                              int grid, cudaStream_t s)
+{
+    switch (mt) {
+    case 4: batch_init_kernel<4><<<grid, kTile, 0, s>>>(a, lam1, lam_off); break;
+    case 8: batch_init_kernel<8><<<grid, kTile, 0, s>>>(a, lam1, lam_off); break;
+    case 16: batch_init_kernel<16><<<grid, kTile, 0, s>>>(a, lam1, lam_off); break;
+    default: batch_init_kernel<32><<<grid, kTile, 0, s>>>(a, lam1, lam_off); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace ra

@@ -6,6 +6,8 @@
 
 #include "ra.h"
 
+struct ra_batch;
+
 namespace ra {
 
 constexpr int kTile = 256;          // jobs per tile == threads per CTA of the streaming kernels
@@ -75,6 +77,8 @@ struct SolverState {
     int32_t pad3_;
     double mu_lp[RA_MAX_M]; // minimiser of the cutting-plane model of g (LP duals)
     double q_best[RA_MAX_M];// subgradient at the best dual point
+    unsigned long long t_start; // device global timer (ns) at setup
+    unsigned long long t_done;  // device global timer (ns) when the solve stopped
     double r_prev[RA_MAX_M];
     double cand_U[kCand];
     int32_t cand_scaled[kCand];
@@ -163,6 +167,41 @@ struct DualParams {
     const int32_t *lag_on;
 };
 
+// One problem of a batch (device copy).
+struct BatchProblem {
+    const float *A;
+    const uint8_t *kind;
+    const float *w;
+    const float *param;
+    const double *R;
+    long long n;
+    int m;
+    int cls;              // width class: MT = 4 << cls
+    int chunk_begin;      // this problem's chunks in its class's chunk list
+    int chunk_end;
+    float2 *lbt[2];
+    uchar2 *lbj[2];
+};
+
+constexpr int kChunkTiles = 16;  // tiles of one problem per chunk (batched evaluation)
+
+struct BatchDualArgs {
+    const BatchProblem *probs;
+    SolverState *st;
+    EvalOut *ev;
+    const int32_t *pingpong;
+    const int32_t *lag_on;
+    const int32_t *chunk_prob;
+    const int32_t *chunk_tile0;
+    const int32_t *chunk_ntiles;
+    int nchunks;
+    double *partials;     // nchunks x kPartW
+    unsigned *ticket;     // per problem
+    int *status;
+    int stages;
+    int cap;
+};
+
 // Launchers (ra_dual.cu).
 cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t s);
 cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
@@ -173,6 +212,12 @@ cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jsta
                            float *x12, float *t, float *X, double *U, uint8_t *near_tie,
                            unsigned long long *n_ties, cudaStream_t s);
 cudaError_t configure_dual(ra_problem *p);
+cudaError_t launch_batch_dual(int mt, const BatchDualArgs &a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_init(int mt, const BatchDualArgs &a, double *lam1_concat,
+                              const long long *lam_off, int grid, cudaStream_t s);
+int batch_stages(int mt);
+size_t batch_smem(int mt);
+cudaError_t batch_configure(int mt, int *blocks_per_sm);
 
 // Solver (ra_solve.cu).
 ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, double *lambda_out,
@@ -180,7 +225,44 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
 int32_t solve_history(ra_problem *p, double *hist, int32_t cap);
 int32_t solve_certificate(ra_problem *p, double *theta, double *lam, int32_t *scaled);
 
+ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0,
+                      double *lambda_out, ra_solve_info *infos, double *seconds);
+
 // Error reporting (ra_api.cu).
 ra_status fail(ra_status s, const char *fmt, ...);
 
 }  // namespace ra
+
+struct ra_batch {
+    int P;
+    uint32_t flags;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    long long *n_h;            // host copies
+    int *m_h;
+    long long *lam_off_h;      // offset of problem p's prices in the concatenated vector
+    long long m_total;
+    ra::BatchProblem *probs;   // device, P
+    ra::SolverState *st;       // device, P
+    ra::EvalOut *ev;           // device, P
+    int32_t *pingpong;         // device, P
+    int32_t *lag_on;           // device, P
+    long long *lam_off;        // device, P
+    int32_t *active;           // device, 1: problems still iterating
+    unsigned *ticket;          // device, P
+    int *status;               // device
+    float2 *lbt_pool[2];
+    uchar2 *lbj_pool[2];
+    double *lam_tmp;           // device, m_total
+    int nchunks[4];
+    int32_t *chunk_prob[4];
+    int32_t *chunk_tile0[4];
+    int32_t *chunk_ntiles[4];
+    double *partials[4];
+    int grid[4];               // CTAs of the batched dual pass per class
+    int grid_init[4];
+    unsigned long long *t0;    // device: global timer at the start of the solve
+    ra_solve_info *info;       // device, P
+    double *secs;              // device, P
+};

@@ -43,12 +43,18 @@ __device__ __forceinline__ int wmin_i(int v)
     return v;
 }
 
-// Set the solver's first trial point and constants.  lam0 may be NULL when the
-// initial prices have already been written to st->lam_trial.
-__global__ void solver_setup_kernel(SolverState *st, const double *lam0, const double *R, int m,
-                                    double tol, int max_evals, int mem, int update,
-                                    double lam_floor, int cap, int use_master, int32_t *pingpong,
-                                    int32_t *lag_on)
+__device__ __forceinline__ unsigned long long device_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Set one solver's first trial point and constants (one warp).  lam0 may be
+// NULL when the initial prices have already been written to st->lam_trial.
+__device__ void setup_one(SolverState *st, const double *lam0, const double *R, int m, double tol,
+                          int max_evals, int mem, int update, double lam_floor, int cap,
+                          int use_master, int32_t *pingpong, int32_t *lag_on)
 {
     const int j = threadIdx.x;
     double l = 0.0;
@@ -91,8 +97,49 @@ __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const d
         st->master_ok = 0;
         st->theta_n = 0;
         st->U_master = -__longlong_as_double(0x7ff0000000000000ll);
+        st->t_start = device_ns();
+        st->t_done = 0ull;
         *pingpong = 0;
         *lag_on = 0;
+    }
+}
+
+__global__ void solver_setup_kernel(SolverState *st, const double *lam0, const double *R, int m,
+                                    double tol, int max_evals, int mem, int update,
+                                    double lam_floor, int cap, int use_master, int32_t *pingpong,
+                                    int32_t *lag_on)
+{
+    setup_one(st, lam0, R, m, tol, max_evals, mem, update, lam_floor, cap, use_master, pingpong,
+              lag_on);
+}
+
+// Batched setup: block p sets up problem p; its starting prices are
+// lam0[lam_off[p] .. + m_p).
+__global__ void batch_setup_kernel(SolverState *st, const BatchProblem *probs, const double *lam0,
+                                   const long long *lam_off, double tol, int max_evals, int mem,
+                                   int update, double lam_floor, int cap, int use_master,
+                                   int32_t *pingpong, int32_t *lag_on)
+{
+    const int p = blockIdx.x;
+    setup_one(st + p, lam0 + lam_off[p], probs[p].R, probs[p].m, tol, max_evals, mem, update,
+              lam_floor, cap, use_master, pingpong + p, lag_on + p);
+}
+
+// Graph condition of the batched loop: continue while any problem iterates.
+__global__ void __launch_bounds__(1024)
+    batch_any_active_kernel(const SolverState *st, int P, cudaGraphConditionalHandle cond,
+                            int use_cond, int32_t *active)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) mine |= st[p].done == 0;
+    if (__syncthreads_or(mine) && threadIdx.x == 0) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *active = any;
+        if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
     }
 }
 
@@ -181,6 +228,8 @@ __global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, con
     __shared__ int s_enter, s_leave, s_slotU, s_slotS, s_k0, s_run, s_degen, s_iters, s_ok;
     __shared__ double s_ius, s_U;
     const int tid = threadIdx.x;
+    st += blockIdx.x;  // block b: problem b of a batch (one block for a single solve)
+    ev += blockIdx.x;
     if (st->done) return;
     const int m = st->m;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
@@ -572,6 +621,10 @@ __global__ void __launch_bounds__(32)
                          int32_t *done_host_flag)
 {
     const int j = threadIdx.x;
+    st += blockIdx.x;  // block b: problem b of a batch (one block for a single solve)
+    ev += blockIdx.x;
+    pingpong += blockIdx.x;
+    lag_on += blockIdx.x;
     const int m = st->m;
     const bool active = j < m;
     if (st->done) {
@@ -700,6 +753,7 @@ __global__ void __launch_bounds__(32)
         if (done) {
             st->done = 1;
             st->status = status;
+            st->t_done = device_ns();
         }
         *pingpong = *pingpong ^ 1;  // this evaluation's records become "previous"
         *lag_on = 1;
@@ -707,6 +761,33 @@ __global__ void __launch_bounds__(32)
         const int fin = st->done;
         if (done_host_flag) *done_host_flag = fin;
         if (use_cond) cudaGraphSetConditional(cond, fin ? 0u : 1u);
+    }
+}
+
+__global__ void stamp_kernel(unsigned long long *t) { *t = device_ns(); }
+
+// Per-problem results of a batched solve: best prices into the concatenated
+// output, the info record and the seconds from the batch start (t0) until
+// the problem's solve stopped.
+__global__ void batch_finish_kernel(const SolverState *st, const BatchProblem *probs,
+                                    const long long *lam_off, const unsigned long long *t0,
+                                    double *lam_out, ra_solve_info *info, double *secs)
+{
+    const int p = blockIdx.x, j = threadIdx.x;
+    const SolverState *S = st + p;
+    if (j < S->m) lam_out[lam_off[p] + j] = S->lam_best[j];
+    if (j == 0) {
+        ra_solve_info r;
+        r.status = S->status;
+        r.iters = S->k;
+        r.evals = S->evals;
+        r.ls_fail = S->ls_fail;
+        r.g = S->g_best;
+        r.U_lb = S->U_best;
+        r.rel_gap = S->gap;
+        r.gap_per_job = (S->g_best - S->U_best) / static_cast<double>(probs[p].n);
+        info[p] = r;
+        secs[p] = S->t_done > *t0 ? static_cast<double>(S->t_done - *t0) * 1e-9 : 0.0;
     }
 }
 
@@ -897,6 +978,151 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if (h.status == RA_ETIMEOUT) return fail(RA_ETIMEOUT, "a device wait gave up during the solve");
     if (h.status == RA_EUNBOUNDED) return fail(RA_EUNBOUNDED, "dual value not finite: a price reached zero without the per-job cap");
     if (h.status == RA_ENOTCONV) return fail(RA_ENOTCONV, "stopped after %d evaluations at relative gap %.3e", h.evals, h.gap);
+    return RA_OK;
+}
+
+
+// Batched price discovery: P independent problems advance together, one
+// evaluation each per loop trip (the batched dual pass of every width class,
+// then the master LP and the price update with one block per problem); a
+// problem that has met its gap test is skipped by all three.  The loop is a
+// graph while-node that stops when no problem is left iterating.
+ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0,
+                      double *lambda_out, ra_solve_info *infos, double *seconds)
+{
+    ra_solve_opts opts;
+    ra_solve_opts_default(&opts);
+    if (o) opts = *o;
+    if (opts.lbfgs_mem < 1 || opts.lbfgs_mem > kMaxLbfgsMem)
+        return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
+    if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
+    if (!(opts.tol_rel >= 0.0)) return fail(RA_EINVAL, "tol_rel must be >= 0");
+    if (!lambda_out || !infos) return fail(RA_EINVAL, "lambda_out and infos must not be NULL");
+    cudaStream_t s = b->stream;
+    cudaError_t e;
+    const int P = b->P;
+    const int cap = !(b->flags & RA_NO_JOB_CAP);
+    if ((e = cudaMemsetAsync(b->status, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->ticket, 0, sizeof(unsigned) * P, s)) != cudaSuccess)
+        return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    stamp_kernel<<<1, 1, 0, s>>>(b->t0);
+
+    BatchDualArgs args[4];
+    for (int c = 0; c < 4; ++c) {
+        BatchDualArgs &a = args[c];
+        a.probs = b->probs;
+        a.st = b->st;
+        a.ev = b->ev;
+        a.pingpong = b->pingpong;
+        a.lag_on = b->lag_on;
+        a.chunk_prob = b->chunk_prob[c];
+        a.chunk_tile0 = b->chunk_tile0[c];
+        a.chunk_ntiles = b->chunk_ntiles[c];
+        a.nchunks = b->nchunks[c];
+        a.partials = b->partials[c];
+        a.ticket = b->ticket;
+        a.status = b->status;
+        a.stages = batch_stages(4 << c);
+        a.cap = cap;
+    }
+    const double *lam0 = lambda0;
+    if (!lam0) {
+        // Eq. e-initialization for every problem; the done flags read by the
+        // chunk walk are not consulted by this pass
+        for (int c = 0; c < 4; ++c) {
+            if (!b->nchunks[c]) continue;
+            if ((e = launch_batch_init(4 << c, args[c], b->lam_tmp, b->lam_off, b->grid_init[c], s)) !=
+                cudaSuccess)
+                return fail(RA_ECUDA, "batched init launch: %s", cudaGetErrorString(e));
+        }
+        lam0 = b->lam_tmp;
+    }
+    batch_setup_kernel<<<P, 32, 0, s>>>(b->st, b->probs, lam0, b->lam_off, opts.tol_rel,
+                                        opts.max_evals, opts.lbfgs_mem, opts.update, opts.lam_floor,
+                                        cap, opts.master_lb, b->pingpong, b->lag_on);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return fail(RA_ECUDA, "batched setup launch: %s", cudaGetErrorString(e));
+    if ((e = cudaFuncSetAttribute(master_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
+        return fail(RA_ECUDA, "master kernel attribute: %s", cudaGetErrorString(e));
+
+    auto body = [&](cudaGraphConditionalHandle cond, int use_cond) -> cudaError_t {
+        for (int c = 0; c < 4; ++c) {
+            if (!b->nchunks[c]) continue;
+            cudaError_t e1 = launch_batch_dual(4 << c, args[c], b->grid[c], batch_smem(4 << c), s);
+            if (e1 != cudaSuccess) return e1;
+        }
+        master_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev);
+        solver_update_kernel<<<P, 32, 0, s>>>(b->st, b->ev, b->pingpong, b->lag_on, b->status, cond,
+                                              0, nullptr);
+        batch_any_active_kernel<<<1, 1024, 0, s>>>(b->st, P, cond, use_cond, b->active);
+        return cudaGetLastError();
+    };
+
+    bool graph_ok = false;
+    if (opts.use_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphConditionalHandle cond;
+        bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+        ok = ok && cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) ==
+                       cudaSuccess;
+        cudaGraphNode_t node;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t g_body = cp.conditional.phGraph_out[0];
+            ok = cudaStreamBeginCaptureToGraph(s, g_body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                cudaError_t e1 = body(cond, 1);
+                cudaError_t e3 = cudaStreamEndCapture(s, &g_body);
+                ok = e1 == cudaSuccess && e3 == cudaSuccess;
+            }
+        }
+        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        ok = ok && cudaGraphLaunch(exec, s) == cudaSuccess;
+        if (ok) graph_ok = true;
+        if (!ok) (void)cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    if (!graph_ok) {
+        // host-driven loop: 8 trips per check of the device's "any active" word
+        int32_t active_h = 1;
+        cudaGraphConditionalHandle none{};
+        for (int it = 0; it < opts.max_evals && active_h; it += 8) {
+            for (int k = 0; k < 8; ++k)
+                if ((e = body(none, 0)) != cudaSuccess)
+                    return fail(RA_ECUDA, "batched loop launch: %s", cudaGetErrorString(e));
+            if ((e = cudaMemcpyAsync(&active_h, b->active, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return fail(RA_ECUDA, "batched loop: %s", cudaGetErrorString(e));
+        }
+    }
+    batch_finish_kernel<<<P, 32, 0, s>>>(b->st, b->probs, b->lam_off, b->t0, lambda_out, b->info,
+                                         b->secs);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return fail(RA_ECUDA, "batched finish launch: %s", cudaGetErrorString(e));
+    e = cudaMemcpyAsync(infos, b->info, sizeof(ra_solve_info) * P, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && seconds)
+        e = cudaMemcpyAsync(seconds, b->secs, sizeof(double) * P, cudaMemcpyDeviceToHost, s);
+    int kstatus = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kstatus, b->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "batched results: %s", cudaGetErrorString(e));
+    if (kstatus != 0) return fail(RA_ETIMEOUT, "a device wait gave up during the batched solve");
+    int n_unb = 0, n_nc = 0;
+    for (int p = 0; p < P; ++p) {
+        n_unb += infos[p].status == RA_EUNBOUNDED;
+        n_nc += infos[p].status == RA_ENOTCONV;
+    }
+    if (n_unb) return fail(RA_EUNBOUNDED, "%d of %d problems have an unbounded dual", n_unb, P);
+    if (n_nc) return fail(RA_ENOTCONV, "%d of %d problems stopped before the gap test passed", n_nc, P);
     return RA_OK;
 }
 

@@ -76,6 +76,14 @@ def lib():
         L.ra_recover_primal.restype = i32
         L.ra_eval_dual_static.argtypes = [i64, i32, P, P, P, P, P, P, u32, P, P, P]
         L.ra_eval_dual_static.restype = i32
+        L.ra_batch_create.argtypes = [i32, P, P, P, P, P, P, P, u32, P, ctypes.POINTER(P)]
+        L.ra_batch_create.restype = i32
+        L.ra_batch_destroy.argtypes = [P]
+        L.ra_batch_destroy.restype = None
+        L.ra_batch_prices.argtypes = [P]
+        L.ra_batch_prices.restype = i64
+        L.ra_batch_solve.argtypes = [P, ctypes.POINTER(ra_solve_opts), P, P, P, P]
+        L.ra_batch_solve.restype = i32
         L.ra_status_string.argtypes = [i32]
         L.ra_status_string.restype = ctypes.c_char_p
         L.ra_last_error.argtypes = []
@@ -205,6 +213,41 @@ def ra_eval_dual_static(A, kind, w, param, R, lam, g, q, flags=0, stream=None):
                                      _ptr(q, torch.float64, m)))
 
 
+def ra_batch_create(n, m, A_ptrs, kind_ptrs, w_ptrs, param_ptrs, R_ptrs, flags=0, stream=None):
+    """n, m: P sizes; *_ptrs: P device addresses (ints) laid out as for
+    ra_problem_create."""
+    P = len(n)
+    arr = lambda ctype, vals: (ctype * P)(*vals)
+    h = ctypes.c_void_p()
+    _check(lib().ra_batch_create(P, arr(ctypes.c_int64, n), arr(ctypes.c_int32, m),
+                                 arr(ctypes.c_void_p, A_ptrs), arr(ctypes.c_void_p, kind_ptrs),
+                                 arr(ctypes.c_void_p, w_ptrs), arr(ctypes.c_void_p, param_ptrs),
+                                 arr(ctypes.c_void_p, R_ptrs), flags, _stream(stream),
+                                 ctypes.byref(h)))
+    return h
+
+
+def ra_batch_destroy(h):
+    lib().ra_batch_destroy(h)
+
+
+def ra_batch_prices(h):
+    return int(lib().ra_batch_prices(h))
+
+
+def ra_batch_solve(h, P, lam_out, opts=None, lam0=None, allow_notconv=True):
+    """Returns (list of P info dicts, numpy seconds to each problem's stop)."""
+    import numpy as np
+    infos = (ra_solve_info * P)()
+    secs = np.zeros(P)
+    o = opts if opts is not None else ra_solve_opts_default()
+    ok = (RA_OK, RA_ENOTCONV) if allow_notconv else (RA_OK,)
+    _check(lib().ra_batch_solve(h, ctypes.byref(o), _ptr(lam0, torch.float64),
+                                _ptr(lam_out, torch.float64), ctypes.cast(infos, ctypes.c_void_p),
+                                ctypes.c_void_p(secs.ctypes.data)), ok)
+    return [infos[k].as_dict() for k in range(P)], secs
+
+
 def ra_version():
     return lib().ra_version().decode()
 
@@ -323,6 +366,83 @@ class AllocationProblem:
     def close(self):
         if getattr(self, "handle", None):
             ra_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _pack(arrays, align_elems=16):
+    """Concatenate 1-D numpy arrays with every segment starting on a multiple
+    of align_elems elements; returns (buffer, offsets)."""
+    import numpy as np
+    offs, pos = [], 0
+    for a in arrays:
+        offs.append(pos)
+        pos += (a.size + align_elems - 1) // align_elems * align_elems
+    buf = np.zeros(max(pos, align_elems), dtype=arrays[0].dtype)
+    for a, o in zip(arrays, offs):
+        buf[o:o + a.size] = a.ravel()
+    return buf, offs
+
+
+class AllocationBatch:
+    """P independent problems solved together (batched price discovery).
+    Each problem's arrays live in one packed device buffer per field, every
+    segment 16-byte aligned."""
+
+    def __init__(self, problems, job_cap=True, device="cuda", stream=None, pinned=False):
+        import numpy as np
+        self.P = len(problems)
+        self.n = [int(p.A.shape[0]) for p in problems]
+        self.m = [int(p.A.shape[1]) for p in problems]
+        host = {}
+        for f, dt in (("A", np.float32), ("kind", np.uint8), ("w", np.float32),
+                      ("param", np.float32), ("R", np.float64)):
+            buf, offs = _pack([np.ascontiguousarray(getattr(p, f), dtype=dt).ravel() for p in problems])
+            t = torch.from_numpy(buf)
+            if pinned:
+                t = t.pin_memory()
+            host[f] = (t, offs)
+        self.dev = {f: t.to(device, non_blocking=pinned) for f, (t, _) in host.items()}
+        self.offs = {f: o for f, (_, o) in host.items()}
+        self.h2d_bytes = sum(t.numel() * t.element_size() for t, _ in host.values())
+        esz = {"A": 4, "kind": 1, "w": 4, "param": 4, "R": 8}
+        ptrs = {f: [self.dev[f].data_ptr() + o * esz[f] for o in self.offs[f]] for f in esz}
+        self.flags = 0 if job_cap else RA_NO_JOB_CAP
+        self.stream = stream
+        self.handle = ra_batch_create(self.n, self.m, ptrs["A"], ptrs["kind"], ptrs["w"],
+                                      ptrs["param"], ptrs["R"], self.flags, stream)
+        self.m_total = ra_batch_prices(self.handle)
+        self.lam_off = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
+        self.prices = None
+
+    def solve(self, tol=1e-6, max_evals=500, lam0=None, use_graph=True, master_lb=True,
+              lbfgs_mem=10):
+        o = ra_solve_opts_default()
+        o.tol_rel = tol
+        o.max_evals = max_evals
+        o.use_graph = 1 if use_graph else 0
+        o.master_lb = 1 if master_lb else 0
+        o.lbfgs_mem = lbfgs_mem
+        dev = self.dev["A"].device
+        lam = torch.empty(self.m_total, dtype=torch.float64, device=dev)
+        if lam0 is not None:
+            lam0 = torch.as_tensor(lam0, dtype=torch.float64, device=dev).contiguous()
+        self.infos, self.seconds = ra_batch_solve(self.handle, self.P, lam, o, lam0)
+        self.prices = lam
+        return self.infos, self.seconds
+
+    def prices_of(self, k):
+        o = int(self.lam_off[k])
+        return self.prices[o:o + self.m[k]]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ra_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

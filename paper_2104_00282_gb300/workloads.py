@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -142,6 +143,17 @@ def batched_shapes(P: int = 4096, seed: int = 0, n_lo: int = 100, n_hi: int = 20
 def batched_problem(k: int, n: int, m: int, seed: int = 0) -> Problem:
     """Problem k of the batched workload: heterogeneous-hardware recipe."""
     return config_hetero(n=int(n), m=int(m), seed=seed, recipe=40, idx=k)
+
+
+def batched_workload(P: int = 4096, seed: int = 0, threads: int | None = None):
+    """The P problems of the batched workload (shapes from ``batched_shapes``),
+    generated on a thread pool; each problem has its own seeded stream, so
+    the result does not depend on the thread count."""
+    from concurrent.futures import ThreadPoolExecutor
+    n, m = batched_shapes(P, seed)
+    threads = threads or min(32, os.cpu_count() or 1)
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda k: batched_problem(k, n[k], m[k], seed), range(P)))
 
 
 def warmstart_problem(k: int, seed: int = 0, m: int = 16, n_lo: int = 10_000,
