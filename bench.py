@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-6 rel. duality gap at n=1e7,m=32; dual-eval HBM GB/s vs peak"
 N_JOBS, M_RES, TOL = 10_000_000, 32, 1e-6
+BATCH_MAX_EVALS = 500
 WORKLOAD = ("large single problem: n=1e7 jobs, m=32 resources, A_ij = s_j exp(0.75 z), "
             "s_j~U[0.25,8], FP32 row-major (1.28 GB); utilities 40% log, 40% power p~U[0.2,0.8], "
             "20% linear with cap T~U[1,10]; w~U[0.5,2]; R_j~U[0.05,0.3] n; maximize sum_i u_i(a_i^T x_i) "
@@ -353,14 +354,14 @@ def run_batch(args, dev, stream):
     n, m = W.batched_shapes(P)
     probs = W.batched_workload(P)
     with torch.cuda.stream(stream):
-        B = ra.AllocationBatch(probs, job_cap=args.job_cap, device=dev, stream=stream)
+        B = ra.AllocationBatch(probs, job_cap=True, device=dev, stream=stream)
     del probs
     times, secs, infos = [], None, None
     for k in range(4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        infos, secs = B.solve(tol=TOL, max_evals=args.max_evals)
+        infos, secs = B.solve(tol=TOL, max_evals=BATCH_MAX_EVALS)
         e1.record(stream)
         e1.synchronize()
         if k > 0:
@@ -379,7 +380,8 @@ def run_batch(args, dev, stream):
                       "max": int(evals.max())},
             "converged": int((status == 0).sum()), "step_ms_all": times,
             "workload": "n log-uniform in [100, 2e5], m uniform in {4, 8, 16, 32}, "
-                        "heterogeneous-hardware recipe, cold start to 1e-6 relative gap"}
+                        "heterogeneous-hardware recipe, per-job cap 1^T x_i <= 1 (problem "
+                        "e-res-alloc), cold start to 1e-6 relative gap, at most 500 evaluations"}
 
 
 def main():

@@ -294,6 +294,63 @@ int64_t ra_batch_prices(const ra_batch *b);
 ra_status ra_batch_solve(ra_batch *b, const ra_solve_opts *opts, const double *lambda0,
                          double *lambda_out, ra_solve_info *infos, double *seconds);
 
+/*
+ * Learned warm start (not in the paper; the cold start it competes with is
+ * the paper's Eq. e-initialization).  A problem is summarised per resource j
+ * by RA_MLP_STATS = 13 statistics taken over a strided sample of at most
+ * 16384 rows (rows floor(k n / S), S = min(n, 16384)): the order statistics
+ * of A[:, j] at levels (2l+1)/16, l = 0..7, as logarithms; log(R_j / n); the
+ * fractions of log, power and linear (lin-cap and target) utilities; the mean
+ * of log w.  The network input of resource j (RA_MLP_IN = 26 floats) is its
+ * 13 statistics followed by their mean over the problem's resources.  A
+ * shared per-resource MLP 26 -> 256 -> 256 -> 1 with GELU maps each input row
+ * to log(lambda_j).
+ *
+ * Parameters: one FP32 vector of RA_MLP_PARAMS entries laid out as W1 (26 x
+ * 256, row-major, input-major), b1 (256), W2 (256 x 256), b2 (256), W3 (256),
+ * b3 (1).  Training minimises the mean squared error against log(lambda*)
+ * with Adam (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8).
+ */
+#define RA_MLP_STATS 13
+#define RA_MLP_IN 26
+#define RA_MLP_HIDDEN 256
+#define RA_MLP_PARAMS 72961
+
+typedef struct ra_mlp ra_mlp; /* opaque; owns parameters, Adam moments, activations */
+
+/* theta: host, RA_MLP_PARAMS floats, or NULL for zeros.  Kernels of the
+ * network run on `stream`, except inside ra_warmstart_prices (the problem's
+ * stream); the object is not safe for concurrent use. */
+ra_status ra_mlp_create(const float *theta, void *stream, ra_mlp **out);
+void ra_mlp_destroy(ra_mlp *net);
+/* Host copies of the parameters / the gradient of the last training step
+ * (RA_MLP_PARAMS floats each; synchronise).  set_params also clears Adam's
+ * moments and step count. */
+ra_status ra_mlp_get_params(ra_mlp *net, float *theta);
+ra_status ra_mlp_set_params(ra_mlp *net, const float *theta);
+ra_status ra_mlp_get_grads(ra_mlp *net, float *grad);
+/* log_lambda[r] = MLP(feats[r, 0..26)) for rows r < rows (device arrays). */
+ra_status ra_mlp_forward(ra_mlp *net, const float *feats, int32_t rows, float *log_lambda);
+/* One Adam step on L = (1/rows) sum_r (MLP(feats_r) - target_r)^2 at
+ * learning rate lr; loss (device, 1 float) receives L before the step, or
+ * NULL. */
+ra_status ra_mlp_train_step(ra_mlp *net, const float *feats, const float *target, int32_t rows,
+                            float lr, float *loss);
+
+/* Network input of every resource of a problem: feats (device) m x 26. */
+ra_status ra_warmstart_features(ra_problem *prob, float *feats);
+/* The same for every problem of a batch: (sum_p m_p) x 26, problem order. */
+ra_status ra_batch_features(ra_batch *b, float *feats);
+
+/*
+ * ra_warmstart_prices -- start prices for ra_solve: lambda_w = exp(MLP(x_j))
+ * and the cold start lambda_c of Eq. e-initialization are both evaluated,
+ * and lambda0 (device, m FP64) receives lambda_w when g(lambda_w) is finite
+ * and g(lambda_w) <= g(lambda_c), else lambda_c.  used_warm (host, or NULL
+ * to stay asynchronous) receives 1 when the network's prices were kept.
+ */
+ra_status ra_warmstart_prices(ra_problem *prob, ra_mlp *net, double *lambda0, int32_t *used_warm);
+
 /* Static strings; ra_last_error() is thread-local and valid until the next call. */
 const char *ra_status_string(ra_status s);
 const char *ra_last_error(void);

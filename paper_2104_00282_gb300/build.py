@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libra.so")
-SOURCES = ["ra_dual.cu", "ra_solve.cu", "ra_api.cu", "ra_static.cu"]
+SOURCES = ["ra_dual.cu", "ra_solve.cu", "ra_api.cu", "ra_static.cu", "ra_warm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

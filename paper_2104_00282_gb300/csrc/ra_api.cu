@@ -160,6 +160,7 @@ ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t 
     alloc(reinterpret_cast<void **>(&p->st), sizeof(ra::SolverState));
     alloc(reinterpret_cast<void **>(&p->graph_flag), sizeof(int32_t) * 8);
     alloc(reinterpret_cast<void **>(&p->tmp), sizeof(double) * (RA_MAX_M + 8));
+    alloc(reinterpret_cast<void **>(&p->warm), ra::kWarmBytes);
     if (!ok) {
         (void)cudaGetLastError();
         ra_problem_destroy(p);
@@ -193,6 +194,7 @@ void ra_problem_destroy(ra_problem *p)
     cudaFree(p->st);
     cudaFree(p->graph_flag);
     cudaFree(p->tmp);
+    cudaFree(p->warm);
     delete p;
 }
 
@@ -331,6 +333,8 @@ void ra_batch_destroy(ra_batch *b)
     cudaFree(b->info);
     cudaFree(b->secs);
     cudaFree(b->lam_tmp);
+    cudaFree(b->feat_probs);
+    cudaFree(b->feat_stats);
     for (int k = 0; k < 2; ++k) {
         cudaFree(b->lbt_pool[k]);
         cudaFree(b->lbj_pool[k]);
@@ -440,6 +444,8 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
     alloc(reinterpret_cast<void **>(&b->info), sizeof(ra_solve_info) * P);
     alloc(reinterpret_cast<void **>(&b->secs), sizeof(double) * P);
     alloc(reinterpret_cast<void **>(&b->lam_tmp), sizeof(double) * b->m_total);
+    alloc(reinterpret_cast<void **>(&b->feat_probs), sizeof(ra::FeatProblem) * P);
+    alloc(reinterpret_cast<void **>(&b->feat_stats), sizeof(float) * RA_MLP_STATS * b->m_total);
     for (int k = 0; k < 2; ++k) {
         alloc(reinterpret_cast<void **>(&b->lbt_pool[k]), sizeof(float2) * total);
         alloc(reinterpret_cast<void **>(&b->lbj_pool[k]), sizeof(uchar2) * total);
@@ -482,6 +488,12 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
         if (e == cudaSuccess)
             e = cudaMemcpy(b->chunk_ntiles[c], cnt[c].data(), sizeof(int32_t) * b->nchunks[c], cudaMemcpyHostToDevice);
     }
+    std::vector<ra::FeatProblem> fp(P);
+    for (int p = 0; p < P; ++p) {
+        fp[p] = ra::FeatProblem{A[p], kind[p], w[p], R[p], n[p], m[p], b->lam_off_h[p]};
+        if (m[p] > b->m_max) b->m_max = m[p];
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(b->feat_probs, fp.data(), sizeof(ra::FeatProblem) * P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->probs, probs.data(), sizeof(ra::BatchProblem) * P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->lam_off, b->lam_off_h, sizeof(long long) * P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->ticket, 0, sizeof(unsigned) * P);
@@ -506,5 +518,185 @@ ra_status ra_batch_solve(ra_batch *b, const ra_solve_opts *opts, const double *l
 }
 
 int64_t ra_batch_prices(const ra_batch *b) { return b ? static_cast<int64_t>(b->m_total) : -1; }
+
+
+// ---------------------------------------------------------------------------- warm start
+
+namespace {
+
+// Offsets in the problem's warm-start scratch.
+constexpr size_t kWsStats = 0;                                   // 32 x 13 floats
+constexpr size_t kWsFeats = 1792;                                // 32 x 26 floats
+constexpr size_t kWsY = kWsFeats + sizeof(float) * RA_MAX_M * RA_MLP_IN;
+constexpr size_t kWsLamW = kWsY + sizeof(float) * RA_MAX_M;
+constexpr size_t kWsLamC = kWsLamW + sizeof(double) * RA_MAX_M;
+constexpr size_t kWsUsed = kWsLamC + sizeof(double) * RA_MAX_M;
+static_assert(kWsStats + sizeof(float) * RA_MAX_M * RA_MLP_STATS <= kWsFeats, "scratch layout");
+static_assert(kWsUsed + 16 <= ra::kWarmBytes, "scratch layout");
+
+ra::FeatProblem feat_of(const ra_problem *p)
+{
+    return ra::FeatProblem{p->A, p->kind, p->w, p->R, p->n, p->m, 0};
+}
+
+}  // namespace
+
+ra_status ra_mlp_create(const float *theta, void *stream, ra_mlp **out)
+{
+    ra::g_err[0] = 0;
+    if (!out) return fail(RA_EINVAL, "out is NULL");
+    *out = nullptr;
+    ra_mlp *net = new (std::nothrow) ra_mlp();
+    if (!net) return fail(RA_ENOMEM, "host allocation failed");
+    memset(net, 0, sizeof(*net));
+    net->stream = static_cast<cudaStream_t>(stream);
+    float *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, sizeof(float) * 4 * RA_MLP_PARAMS);
+    if (e != cudaSuccess) {
+        delete net;
+        return fail(RA_ENOMEM, "parameter allocation: %s", cudaGetErrorString(e));
+    }
+    net->theta = buf;
+    net->grad = buf + RA_MLP_PARAMS;
+    net->m1 = buf + 2 * RA_MLP_PARAMS;
+    net->m2 = buf + 3 * RA_MLP_PARAMS;
+    e = cudaMemsetAsync(buf, 0, sizeof(float) * 4 * RA_MLP_PARAMS, net->stream);
+    if (e == cudaSuccess && theta)
+        e = cudaMemcpyAsync(net->theta, theta, sizeof(float) * RA_MLP_PARAMS, cudaMemcpyHostToDevice,
+                            net->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) {
+        ra_mlp_destroy(net);
+        return fail(RA_ECUDA, "parameter upload: %s", cudaGetErrorString(e));
+    }
+    *out = net;
+    return RA_OK;
+}
+
+void ra_mlp_destroy(ra_mlp *net)
+{
+    if (!net) return;
+    cudaStreamSynchronize(net->stream);
+    cudaFree(net->theta);
+    cudaFree(net->act);
+    delete net;
+}
+
+static ra_status mlp_copy(ra_mlp *net, float *host, const float *dev)
+{
+    cudaError_t e = cudaMemcpyAsync(host, dev, sizeof(float) * RA_MLP_PARAMS, cudaMemcpyDeviceToHost,
+                                    net->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "parameter copy: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_mlp_get_params(ra_mlp *net, float *theta)
+{
+    if (!net || !theta) return fail(RA_EINVAL, "NULL argument");
+    return mlp_copy(net, theta, net->theta);
+}
+
+ra_status ra_mlp_get_grads(ra_mlp *net, float *grad)
+{
+    if (!net || !grad) return fail(RA_EINVAL, "NULL argument");
+    return mlp_copy(net, grad, net->grad);
+}
+
+ra_status ra_mlp_set_params(ra_mlp *net, const float *theta)
+{
+    if (!net || !theta) return fail(RA_EINVAL, "NULL argument");
+    cudaError_t e = cudaMemcpyAsync(net->theta, theta, sizeof(float) * RA_MLP_PARAMS,
+                                    cudaMemcpyHostToDevice, net->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(net->grad, 0, sizeof(float) * 3 * RA_MLP_PARAMS, net->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "parameter upload: %s", cudaGetErrorString(e));
+    net->t = 0;
+    return RA_OK;
+}
+
+ra_status ra_mlp_forward(ra_mlp *net, const float *feats, int32_t rows, float *log_lambda)
+{
+    if (!net || !feats || !log_lambda) return fail(RA_EINVAL, "NULL argument");
+    if (rows < 1) return fail(RA_EINVAL, "rows = %d must be >= 1", rows);
+    cudaError_t e = ra::mlp_forward(net, feats, rows, log_lambda, net->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "MLP forward: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_mlp_train_step(ra_mlp *net, const float *feats, const float *target, int32_t rows,
+                            float lr, float *loss)
+{
+    if (!net || !feats || !target) return fail(RA_EINVAL, "NULL argument");
+    if (rows < 1) return fail(RA_EINVAL, "rows = %d must be >= 1", rows);
+    if (!(lr > 0.0f)) return fail(RA_EINVAL, "lr must be > 0");
+    cudaError_t e = ra::mlp_train_step(net, feats, target, rows, lr, loss, net->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "MLP training step: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_warmstart_features(ra_problem *p, float *feats)
+{
+    if (!p || !feats) return fail(RA_EINVAL, "NULL argument");
+    cudaError_t e = ra::launch_features(nullptr, feat_of(p), 1, p->m,
+                                        reinterpret_cast<float *>(p->warm + kWsStats), feats, p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "features launch: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_batch_features(ra_batch *b, float *feats)
+{
+    if (!b || !feats) return fail(RA_EINVAL, "NULL argument");
+    ra::FeatProblem none{};
+    cudaError_t e = ra::launch_features(b->feat_probs, none, b->P, b->m_max, b->feat_stats, feats,
+                                        b->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "features launch: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_warmstart_prices(ra_problem *p, ra_mlp *net, double *lambda0, int32_t *used_warm)
+{
+    if (!p || !net || !lambda0) return fail(RA_EINVAL, "NULL argument");
+    if (p->flags & RA_FP64_JOBMATH) return fail(RA_EINVAL, "the warm start uses the FP32 job math");
+    cudaStream_t s = p->stream;
+    float *stats = reinterpret_cast<float *>(p->warm + kWsStats);
+    float *feats = reinterpret_cast<float *>(p->warm + kWsFeats);
+    float *y = reinterpret_cast<float *>(p->warm + kWsY);
+    double *lam_w = reinterpret_cast<double *>(p->warm + kWsLamW);
+    double *lam_c = reinterpret_cast<double *>(p->warm + kWsLamC);
+    int32_t *used = reinterpret_cast<int32_t *>(p->warm + kWsUsed);
+    cudaError_t e = ra::launch_features(nullptr, feat_of(p), 1, p->m, stats, feats, s);
+    if (e == cudaSuccess) e = ra::mlp_forward(net, feats, p->m, y, s);
+    if (e == cudaSuccess) e = ra::launch_exp_prices(p->m, y, lam_w, s);
+    if (e == cudaSuccess) e = ra::launch_init(p, lam_c, s);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start launch: %s", cudaGetErrorString(e));
+    // g at both candidates: one dual pass each (results in the two EvalOut slots)
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        ra::DualParams dp{};
+        dp.A = p->A;
+        dp.kind = p->kind;
+        dp.w = p->w;
+        dp.param = p->param;
+        dp.R = p->R;
+        dp.n = p->n;
+        dp.m = p->m;
+        dp.lam = k == 0 ? lam_w : lam_c;
+        dp.partials = p->partials;
+        dp.ticket = p->ticket;
+        dp.status = p->status;
+        dp.out = p->ev + k;
+        e = ra::launch_dual(p, dp, s);
+    }
+    if (e == cudaSuccess) e = ra::launch_choose(p->m, lam_w, lam_c, p->ev, p->ev + 1, lambda0, used, s);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start evaluation: %s", cudaGetErrorString(e));
+    if (used_warm) {
+        e = cudaMemcpyAsync(used_warm, used, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start flag: %s", cudaGetErrorString(e));
+        return check_status_word(p);
+    }
+    return RA_OK;
+}
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include "ra.h"
 
 struct ra_batch;
+struct ra_mlp;
 
 namespace ra {
 
@@ -17,6 +18,7 @@ constexpr int kHist = 512;          // solver history length
 constexpr int kHistCols = 6;        // eval, g, best U_lb, gap, master-LP value, LP pivots
 constexpr int kPartW = RA_MAX_M + 4; // doubles per block partial: h, U(X), U_lb(prev), spare, r[m]
 constexpr int kCand = 64;           // master-LP candidates kept (two per evaluation)
+constexpr size_t kWarmBytes = 8192; // per-problem warm-start scratch
 
 // Status word bits written by kernels (never trap: a kernel that gives up
 // records why and returns).
@@ -134,6 +136,7 @@ struct ra_problem {
     ra::SolverState *st;
     int32_t *graph_flag;
     double *tmp;         // small scratch (m + 8 doubles)
+    unsigned char *warm; // warm-start scratch (kWarmBytes)
 };
 
 namespace ra {
@@ -219,6 +222,28 @@ int batch_stages(int mt);
 size_t batch_smem(int mt);
 cudaError_t batch_configure(int mt, int *blocks_per_sm);
 
+// One problem for the warm-start statistics (device copy or by value).
+struct FeatProblem {
+    const float *A;
+    const uint8_t *kind;
+    const float *w;
+    const double *R;
+    long long n;
+    int m;
+    long long row0;   // first output row (resource 0) of this problem
+};
+
+// Warm start (ra_warm.cu).
+cudaError_t launch_features(const FeatProblem *probs, const FeatProblem &one, int P, int m_max,
+                            float *stats, float *feats, cudaStream_t s);
+cudaError_t mlp_reserve(ra_mlp *net, int rows);
+cudaError_t mlp_forward(ra_mlp *net, const float *X, int rows, float *y_out, cudaStream_t s);
+cudaError_t mlp_train_step(ra_mlp *net, const float *X, const float *target, int rows, float lr,
+                           float *loss, cudaStream_t s);
+cudaError_t launch_exp_prices(int m, const float *y, double *lam, cudaStream_t s);
+cudaError_t launch_choose(int m, const double *lam_w, const double *lam_c, const EvalOut *ev_w,
+                          const EvalOut *ev_c, double *lam0, int32_t *used, cudaStream_t s);
+
 // Solver (ra_solve.cu).
 ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, double *lambda_out,
                 double *lambda_lb, ra_solve_info *info);
@@ -265,4 +290,18 @@ struct ra_batch {
     unsigned long long *t0;    // device: global timer at the start of the solve
     ra_solve_info *info;       // device, P
     double *secs;              // device, P
+    ra::FeatProblem *feat_probs; // device, P (warm-start statistics)
+    float *feat_stats;         // device, m_total x RA_MLP_STATS
+    int m_max;
+};
+
+struct ra_mlp {
+    cudaStream_t stream;
+    float *theta;      // RA_MLP_PARAMS each: parameters, last gradient, Adam moments
+    float *grad;
+    float *m1;
+    float *m2;
+    float *act;        // activations of up to cap_rows rows
+    int cap_rows;
+    int t;             // Adam step count
 };

@@ -19,6 +19,7 @@ RA_OK, RA_EINVAL, RA_ENOMEM, RA_ECUDA, RA_ENOTCONV, RA_ETIMEOUT, RA_EUNBOUNDED =
 RA_U_LOG, RA_U_POWER, RA_U_LINCAP, RA_U_TARGET = range(4)
 RA_JOB_CAP, RA_NO_JOB_CAP, RA_FP64_JOBMATH, RA_VALIDATE = 0x0, 0x1, 0x2, 0x4
 RA_MAX_M = 32
+RA_MLP_STATS, RA_MLP_IN, RA_MLP_HIDDEN, RA_MLP_PARAMS = 13, 26, 256, 72961
 
 
 class RaError(RuntimeError):
@@ -84,6 +85,23 @@ def lib():
         L.ra_batch_prices.restype = i64
         L.ra_batch_solve.argtypes = [P, ctypes.POINTER(ra_solve_opts), P, P, P, P]
         L.ra_batch_solve.restype = i32
+        L.ra_mlp_create.argtypes = [P, P, ctypes.POINTER(P)]
+        L.ra_mlp_create.restype = i32
+        L.ra_mlp_destroy.argtypes = [P]
+        L.ra_mlp_destroy.restype = None
+        for name in ("ra_mlp_get_params", "ra_mlp_set_params", "ra_mlp_get_grads"):
+            getattr(L, name).argtypes = [P, P]
+            getattr(L, name).restype = i32
+        L.ra_mlp_forward.argtypes = [P, P, i32, P]
+        L.ra_mlp_forward.restype = i32
+        L.ra_mlp_train_step.argtypes = [P, P, P, i32, ctypes.c_float, P]
+        L.ra_mlp_train_step.restype = i32
+        L.ra_warmstart_features.argtypes = [P, P]
+        L.ra_warmstart_features.restype = i32
+        L.ra_batch_features.argtypes = [P, P]
+        L.ra_batch_features.restype = i32
+        L.ra_warmstart_prices.argtypes = [P, P, P, ctypes.POINTER(i32)]
+        L.ra_warmstart_prices.restype = i32
         L.ra_status_string.argtypes = [i32]
         L.ra_status_string.restype = ctypes.c_char_p
         L.ra_last_error.argtypes = []
@@ -248,6 +266,71 @@ def ra_batch_solve(h, P, lam_out, opts=None, lam0=None, allow_notconv=True):
     return [infos[k].as_dict() for k in range(P)], secs
 
 
+def ra_mlp_create(theta=None, stream=None):
+    """theta: host numpy float32 vector of RA_MLP_PARAMS, or None (zeros)."""
+    import numpy as np
+    h = ctypes.c_void_p()
+    buf = None
+    if theta is not None:
+        buf = np.ascontiguousarray(theta, dtype=np.float32)
+        assert buf.size == RA_MLP_PARAMS
+    _check(lib().ra_mlp_create(ctypes.c_void_p(buf.ctypes.data) if buf is not None else None,
+                               _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def ra_mlp_destroy(h):
+    lib().ra_mlp_destroy(h)
+
+
+def _mlp_host(fn, h):
+    import numpy as np
+    out = np.zeros(RA_MLP_PARAMS, np.float32)
+    _check(fn(h, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def ra_mlp_get_params(h):
+    return _mlp_host(lib().ra_mlp_get_params, h)
+
+
+def ra_mlp_get_grads(h):
+    return _mlp_host(lib().ra_mlp_get_grads, h)
+
+
+def ra_mlp_set_params(h, theta):
+    import numpy as np
+    buf = np.ascontiguousarray(theta, dtype=np.float32)
+    assert buf.size == RA_MLP_PARAMS
+    _check(lib().ra_mlp_set_params(h, ctypes.c_void_p(buf.ctypes.data)))
+
+
+def ra_mlp_forward(h, feats, rows, log_lambda):
+    _check(lib().ra_mlp_forward(h, _ptr(feats, torch.float32, rows * RA_MLP_IN), rows,
+                                _ptr(log_lambda, torch.float32, rows)))
+
+
+def ra_mlp_train_step(h, feats, target, rows, lr, loss=None):
+    _check(lib().ra_mlp_train_step(h, _ptr(feats, torch.float32, rows * RA_MLP_IN),
+                                   _ptr(target, torch.float32, rows), rows, float(lr),
+                                   _ptr(loss, torch.float32, 1)))
+
+
+def ra_warmstart_features(h, feats):
+    _check(lib().ra_warmstart_features(h, _ptr(feats, torch.float32)))
+
+
+def ra_batch_features(h, feats):
+    _check(lib().ra_batch_features(h, _ptr(feats, torch.float32)))
+
+
+def ra_warmstart_prices(h, net, lam0, sync=True):
+    flag = ctypes.c_int32(-1)
+    _check(lib().ra_warmstart_prices(h, net, _ptr(lam0, torch.float64),
+                                     ctypes.byref(flag) if sync else None))
+    return int(flag.value) if sync else None
+
+
 def ra_version():
     return lib().ra_version().decode()
 
@@ -341,6 +424,19 @@ class AllocationProblem:
             lines.append(f"Converged in {int(h[-1][0]):03d} evaluations, with residual "
                          f"{(h[-1][1] - h[-1][2]) / self.n:.6g}")
         return lines
+
+    def features(self):
+        """Warm-start network input, (m, 26) FP32 on the device."""
+        f = torch.empty((self.m, RA_MLP_IN), dtype=torch.float32, device=self.A.device)
+        ra_warmstart_features(self.handle, f)
+        return f
+
+    def warm_prices(self, net):
+        """(lambda0, used_warm): the network's prices if their dual value is not
+        larger than the cold start's, else Eq. e-initialization."""
+        lam0 = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
+        used = ra_warmstart_prices(self.handle, net.handle, lam0)
+        return lam0, bool(used)
 
     def recover(self, lam=None, dense=False):
         lam = self.prices if lam is None else torch.as_tensor(lam, dtype=torch.float64,
@@ -436,6 +532,12 @@ class AllocationBatch:
         self.prices = lam
         return self.infos, self.seconds
 
+    def features(self):
+        """Warm-start network input of every problem, (sum m, 26) FP32."""
+        f = torch.empty((self.m_total, RA_MLP_IN), dtype=torch.float32, device=self.dev["A"].device)
+        ra_batch_features(self.handle, f)
+        return f
+
     def prices_of(self, k):
         o = int(self.lam_off[k])
         return self.prices[o:o + self.m[k]]
@@ -443,6 +545,48 @@ class AllocationBatch:
     def close(self):
         if getattr(self, "handle", None):
             ra_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WarmStartMLP:
+    """The warm-start network (parameters, Adam state and activations on the
+    device); training and inference run in libra's kernels."""
+
+    def __init__(self, theta=None, stream=None):
+        self.stream = stream
+        self.handle = ra_mlp_create(theta, stream)
+
+    def params(self):
+        return ra_mlp_get_params(self.handle)
+
+    def set_params(self, theta):
+        ra_mlp_set_params(self.handle, theta)
+
+    def grads(self):
+        return ra_mlp_get_grads(self.handle)
+
+    def forward(self, feats):
+        feats = feats.contiguous()
+        rows = feats.shape[0]
+        out = torch.empty(rows, dtype=torch.float32, device=feats.device)
+        ra_mlp_forward(self.handle, feats, rows, out)
+        return out
+
+    def train_step(self, feats, target, lr):
+        rows = feats.shape[0]
+        loss = torch.empty(1, dtype=torch.float32, device=feats.device)
+        ra_mlp_train_step(self.handle, feats.contiguous(), target.contiguous(), rows, lr, loss)
+        return loss
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ra_mlp_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

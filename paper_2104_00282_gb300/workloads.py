@@ -216,3 +216,18 @@ def random_small(n: int, m: int, seed: int, kinds=(0, 1, 2, 3), r_scale: float =
 def random_prices(m: int, seed: int, lo: float = 0.2, hi: float = 3.0) -> np.ndarray:
     """A seeded FP64 price vector lambda ~ U[lo, hi]^m."""
     return _rng(9, seed).uniform(lo, hi, size=m)
+
+
+MLP_SHAPES = [(26, 256), (256,), (256, 256), (256,), (256,), (1,)]   # W1 b1 W2 b2 W3 b3
+MLP_FAN_IN = [26, 26, 256, 256, 256, 256]
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network (flat FP32 vector in
+    the library's layout): every tensor ~ U[-1/sqrt(fan_in), 1/sqrt(fan_in)]."""
+    rng = _rng(10, seed)
+    parts = []
+    for shape, fan in zip(MLP_SHAPES, MLP_FAN_IN):
+        b = 1.0 / math.sqrt(fan)
+        parts.append(rng.uniform(-b, b, size=shape).astype(np.float32).ravel())
+    return np.concatenate(parts)
