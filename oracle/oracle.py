@@ -43,9 +43,9 @@ def lib():
         L.ora_max_threads.restype = i32
         L.ora_job.argtypes = [i32, P, P, i32, d, d, i32, i32, P]
         L.ora_job.restype = None
-        L.ora_dual.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32, P, P, P, i32]
+        L.ora_dual.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32, P, P, P, P, i32]
         L.ora_dual.restype = i32
-        L.ora_scaled_utility.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32, P, i32]
+        L.ora_scaled_utility.argtypes = [i64, i32, P, P, P, P, P, P, P, i32, i32, P, i32]
         L.ora_scaled_utility.restype = i32
         L.ora_init.argtypes = [i64, i32, P, P, P, P, P, i32, P, i32]
         L.ora_init.restype = i32
@@ -119,50 +119,88 @@ def jobs(prob, lam, idx=None, cap=True, method="hull", nthreads=0):
 
 # --------------------------------------------------------------------------- dual
 
-def dual(prob, lam, cap=True, method="hull", nthreads=0):
+def dual(prob, lam, cap=True, method="hull", nthreads=0, split=False):
     """(g, r, U): dual value g(lam) = lam^T R + sum_i h_i, usage r = sum_i x_i
-    and the utility U(X) of the unscaled subproblem solutions (Section 3)."""
+    and the utility U(X) of the unscaled subproblem solutions (Section 3).
+    With split, also r_lin: the part of r used by jobs with a linear utility
+    (kinds 2 and 3)."""
     A, kind, w, par, R = _arrays(prob)
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     g = np.zeros(1)
     r = np.zeros(prob.m)
     U = np.zeros(1)
+    r_lin = np.zeros(prob.m)
     rc = lib().ora_dual(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(R), _p(lam),
                         int(bool(cap)), 0 if method == "hull" else 1, _p(g), _p(r), _p(U),
-                        nthreads)
+                        _p(r_lin), nthreads)
     assert rc == 0
+    if split:
+        return float(g[0]), r, float(U[0]), r_lin
     return float(g[0]), r, float(U[0])
 
 
-def column_scale(R, r):
-    """s_j = min(1, R_j / r_j): scaling that makes X diag(s) meet r <= R (Section 5)."""
+def column_scale(R, r, cap=True):
+    """Column scaling that makes X diag(s) feasible (Section 5).  With the
+    per-job cap, s_j = min(1, R_j / r_j): the paper's scaling down of the
+    over-used columns.  Without the cap nothing bounds a job's x_i, so the
+    under-used columns are scaled up too, s_j = R_j / r_j (1 where r_j = 0):
+    X diag(s) then uses exactly R, and to first order its utility gains
+    sum_j lambda_j (R_j - r_j), the term by which g exceeds U(X)."""
     R = np.asarray(R, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64)
     s = np.ones_like(R)
-    over = r > R
-    s[over] = R[over] / r[over]
+    sel = (r > R) if cap else (r > 0)
+    s[sel] = R[sel] / r[sel]
     return s
 
 
-def scaled_utility(prob, lam, s, cap=True, method="hull", nthreads=0):
-    """U(X diag(s)) with X the subproblem solutions at lam (Section 5)."""
+def column_scales(R, r, r_lin, cap=True):
+    """(s, s_lin): column scaling with a separate factor for the jobs with a
+    linear utility.  With the per-job cap both are the paper's min(1, R/r).
+    Without it, the linear-utility jobs sit at their target t = T, where
+    more throughput adds nothing, so their columns are only scaled down,
+    s_lin = min(1, R / r_lin); the capacity left, R - s_lin r_lin, goes to
+    the other jobs, s = (R - s_lin r_lin) / (r - r_lin) (1 where those use
+    nothing)."""
+    R = np.asarray(R, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    r_lin = np.asarray(r_lin, dtype=np.float64)
+    if cap:
+        s = column_scale(R, r, True)
+        return s, s.copy()
+    s_lin = np.ones_like(R)
+    over = r_lin > R
+    s_lin[over] = R[over] / r_lin[over]
+    r_oth = r - r_lin
+    s = np.ones_like(R)
+    use = r_oth > 0
+    s[use] = np.maximum(R[use] - s_lin[use] * r_lin[use], 0.0) / r_oth[use]
+    return s, s_lin
+
+
+def scaled_utility(prob, lam, s, cap=True, method="hull", nthreads=0, s_lin=None):
+    """U(X~) with X the subproblem solutions at lam, column j of job i scaled
+    by s_lin[j] for linear-utility jobs (when given) and s[j] otherwise
+    (Section 5)."""
     A, kind, w, par, _ = _arrays(prob)
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     s = np.ascontiguousarray(s, dtype=np.float64)
+    sl = None if s_lin is None else np.ascontiguousarray(s_lin, dtype=np.float64)
     U = np.zeros(1)
     rc = lib().ora_scaled_utility(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(lam),
-                                  _p(s), int(bool(cap)), 0 if method == "hull" else 1, _p(U),
-                                  nthreads)
+                                  _p(s), _p(sl) if sl is not None else None, int(bool(cap)),
+                                  0 if method == "hull" else 1, _p(U), nthreads)
     assert rc == 0
     return float(U[0])
 
 
-def lower_bound(prob, lam, cap=True, method="hull", nthreads=0, r=None):
-    """Feasible utility U(X~) at lam by column scaling, with the scaling used."""
-    if r is None:
-        _, r, _ = dual(prob, lam, cap, method, nthreads)
-    s = column_scale(prob.R, r)
-    return scaled_utility(prob, lam, s, cap, method, nthreads), s
+def lower_bound(prob, lam, cap=True, method="hull", nthreads=0, r=None, r_lin=None):
+    """Feasible utility U(X~) at lam by column scaling (``column_scales``),
+    with the scaling used (s, and s_lin for the linear-utility jobs)."""
+    if r is None or r_lin is None:
+        _, r, _, r_lin = dual(prob, lam, cap, method, nthreads, split=True)
+    s, s_lin = column_scales(prob.R, r, r_lin, cap)
+    return scaled_utility(prob, lam, s, cap, method, nthreads, s_lin=s_lin), (s, s_lin)
 
 
 def init_prices(prob, cap=True, nthreads=0):
@@ -260,12 +298,12 @@ def solve(prob, cap=True, tol=1e-6, max_evals=400, method="hull", nthreads=0, la
 
     def evaluate(x):
         x = np.maximum(np.asarray(x, np.float64), lam_floor)
-        g, r, Ux = dual(prob, x, cap, method, nthreads)
-        lb, s = lower_bound(prob, x, cap, method, nthreads, r=r)
+        g, r, Ux, r_lin = dual(prob, x, cap, method, nthreads, split=True)
+        lb, (s, s_lin) = lower_bound(prob, x, cap, method, nthreads, r=r, r_lin=r_lin)
         st["evals"] += 1
         if master:
             cands.append((Ux, r.copy()))
-            cands.append((lb, np.minimum(r, R)))
+            cands.append((lb, s * (r - r_lin) + s_lin * r_lin))
             if len(cands) > 2 * master_window:
                 del cands[:2]
             if st["evals"] >= 2 and rel_gap(min(st["g"], g), max(st["lb"], lb)) > tol:
@@ -452,7 +490,7 @@ def repair_lower_bound(prob, lam, cap=True, rel=1e-9, nthreads=0, max_flex=20000
     r_fixed = X[fixed].sum(axis=0)
     nv = sum(len(a_) for a_ in alts)
     if nv == 0:
-        s = column_scale(R, r_fixed)
+        s = column_scale(R, r_fixed, cap)
         return (utility_of(prob, (prob.A.astype(np.float64) * X * s).sum(1)),
                 dict(n_flex=0, n_alt=0, s=s, X=X))
     # variables: theta (nv), v (m)
@@ -489,7 +527,7 @@ def repair_lower_bound(prob, lam, cap=True, rel=1e-9, nthreads=0, max_flex=20000
             col += 1
         Xr[i] = xi
     r = Xr.sum(axis=0)
-    s = column_scale(R, r)
+    s = column_scale(R, r, cap)
     Af = prob.A.astype(np.float64)
     t_rep = (Af * Xr * s[None, :]).sum(axis=1)
     return utility_of(prob, t_rep), dict(n_flex=len(flex), n_alt=nv, s=s, X=Xr)

@@ -366,11 +366,11 @@ int ora_max_threads(void) { return nthreads_of(0); }
  * so the result does not depend on the thread count. */
 int ora_dual(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
              const float *par, const double *R, const double *lam, int cap, int method,
-             double *g, double *r, double *U, int nthreads)
+             double *g, double *r, double *U, double *r_lin, int nthreads)
 {
     if (m <= 0 || m > ORA_MAXM || n < 0) return 1;
     int64_t nb = (n + ORA_BLOCK - 1) / ORA_BLOCK;
-    int W = m + 2;
+    int W = 2 * m + 2;   /* h, U, r[m], r_lin[m] (usage of linear-utility jobs) */
     double *part = (double *)calloc((size_t)(nb > 0 ? nb : 1) * W, sizeof(double));
     if (!part) return 2;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads))
@@ -385,14 +385,22 @@ int ora_dual(int64_t n, int m, const float *A, const uint8_t *kind, const float 
             pb[1] += util(kind[i], w[i], par[i], o[0]);
             if (o[3] >= 0) pb[2 + (int)o[3]] += o[5];
             if (o[4] >= 0) pb[2 + (int)o[4]] += o[6];
+            if (kind[i] >= 2) {
+                if (o[3] >= 0) pb[2 + m + (int)o[3]] += o[5];
+                if (o[4] >= 0) pb[2 + m + (int)o[4]] += o[6];
+            }
         }
     }
     double sh = 0.0, su = 0.0;
     for (int j = 0; j < m; ++j) r[j] = 0.0;
+    if (r_lin)
+        for (int j = 0; j < m; ++j) r_lin[j] = 0.0;
     for (int64_t b = 0; b < nb; ++b) {
         sh += part[b * W];
         su += part[b * W + 1];
         for (int j = 0; j < m; ++j) r[j] += part[b * W + 2 + j];
+        if (r_lin)
+            for (int j = 0; j < m; ++j) r_lin[j] += part[b * W + 2 + m + j];
     }
     double lr = 0.0;
     for (int j = 0; j < m; ++j) lr += lam[j] * R[j];
@@ -402,12 +410,14 @@ int ora_dual(int64_t n, int m, const float *A, const uint8_t *kind, const float 
     return 0;
 }
 
-/* Utility of the column-scaled allocation X~ = X diag(s) at prices lam
- * (Section 5: scale each column of X^k down so that the limit holds):
- *   U(X~) = sum_i u_i(sum_j a_ij x_ij s_j). */
+/* Utility of the column-scaled allocation X~ at prices lam (Section 5: scale
+ * each column of X^k so that the limit holds):
+ *   U(X~) = sum_i u_i(sum_j a_ij x_ij s_ij),
+ * s_ij = s_lin[j] for jobs with a linear utility (kinds 2, 3) and s[j]
+ * otherwise (s_lin = NULL: s for every job). */
 int ora_scaled_utility(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
-                       const float *par, const double *lam, const double *s, int cap,
-                       int method, double *U_lb, int nthreads)
+                       const float *par, const double *lam, const double *s,
+                       const double *s_lin, int cap, int method, double *U_lb, int nthreads)
 {
     if (m <= 0 || m > ORA_MAXM || n < 0) return 1;
     int64_t nb = (n + ORA_BLOCK - 1) / ORA_BLOCK;
@@ -420,9 +430,10 @@ int ora_scaled_utility(int64_t n, int m, const float *A, const uint8_t *kind, co
         for (int64_t i = b * ORA_BLOCK; i < i1; ++i) {
             load_row(m, A, i, a);
             solve_job(m, a, lam, kind[i], w[i], par[i], cap, method, o);
+            const double *sc = (s_lin && kind[i] >= 2) ? s_lin : s;
             double t = 0.0;
-            if (o[3] >= 0) t += a[(int)o[3]] * o[5] * s[(int)o[3]];
-            if (o[4] >= 0) t += a[(int)o[4]] * o[6] * s[(int)o[4]];
+            if (o[3] >= 0) t += a[(int)o[3]] * o[5] * sc[(int)o[3]];
+            if (o[4] >= 0) t += a[(int)o[4]] * o[6] * sc[(int)o[4]];
             part[b] += util(kind[i], w[i], par[i], t);
         }
     }

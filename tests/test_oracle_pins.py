@@ -253,7 +253,8 @@ def test_weak_duality_and_feasible_lower_bound(oracle):
     gs, lbs = [], []
     for lam in lams:
         g, r, U = oracle.dual(p, lam)
-        lb, s = oracle.lower_bound(p, lam, r=r)
+        lb, (s, s_lin) = oracle.lower_bound(p, lam, r=r)
+        assert np.array_equal(s, s_lin)                            # one scaling with the cap
         X, _ = oracle.allocation(p, lam)
         rt = (X * s[None, :]).sum(axis=0)
         assert np.all(rt <= p.R * (1 + 1e-12))                    # X~ is feasible
@@ -263,6 +264,55 @@ def test_weak_duality_and_feasible_lower_bound(oracle):
         # g - U(X) = lam^T (R - r): the definition of the Lagrangian at X
         assert g - U == pytest.approx(float(lam @ (p.R - r)), rel=1e-9, abs=1e-7)
     assert min(gs) >= max(lbs)
+
+
+def test_uncapped_two_sided_scaling_is_feasible_and_tight(oracle):
+    # without the per-job cap, X diag(R / r) uses exactly R; its utility,
+    # recomputed here from the dense allocation, is a lower bound, and near
+    # the optimum it recovers the first-order term lam^T (R - r) that the
+    # paper's scaling down of over-used columns gives away
+    p = W.random_small(3000, 4, seed=7, kinds=(0, 1))
+    rng = np.random.default_rng(1)
+    gs, lbs = [], []
+    for lam in [rng.uniform(0.3, 3.0, p.m) for _ in range(6)]:
+        g, r, U = oracle.dual(p, lam, cap=False)
+        lb, (s, _) = oracle.lower_bound(p, lam, cap=False)
+        X, _ = oracle.allocation(p, lam, cap=False)
+        Xs = X * s[None, :]
+        assert np.allclose(Xs.sum(axis=0), p.R, rtol=1e-12)
+        t = (p.A.astype(np.float64) * Xs).sum(axis=1)
+        assert lb == pytest.approx(oracle.utility_of(p, t), rel=1e-12)
+        gs.append(g)
+        lbs.append(lb)
+    assert min(gs) >= max(lbs)
+    sol = oracle.solve(p, cap=False, tol=1e-9, max_evals=2000)
+    g, r, U = oracle.dual(p, sol.lam, cap=False)
+    one = oracle.scaled_utility(p, sol.lam, oracle.column_scale(p.R, r, cap=True), cap=False)
+    two, _ = oracle.lower_bound(p, sol.lam, cap=False, r=r)
+    assert g - two <= 0.05 * (g - one)
+    assert two == pytest.approx(U + float(sol.lam @ (p.R - r)), abs=0.05 * abs(g - one))
+
+
+def test_uncapped_scaling_spares_saturated_linear_jobs(oracle):
+    # without the cap, jobs with w min(t, T) sit at t = T (or 0); their columns
+    # are only scaled down and the capacity they leave goes to the other jobs.
+    # Checked against a dense recomputation: feasibility, the bound's value,
+    # and that near the optimum it beats scaling every job alike
+    p = W.config_large(n=20_000, m=6, seed=2)
+    lin = p.kind >= 2
+    sol = oracle.solve(p, cap=False, tol=1e-8, max_evals=3000)
+    for lam in (sol.lam, sol.lam * (1 + 1e-4 * np.random.default_rng(3).standard_normal(p.m))):
+        g, r, U, r_lin = oracle.dual(p, lam, cap=False, split=True)
+        X, _ = oracle.allocation(p, lam, cap=False)
+        assert np.allclose(X[lin].sum(axis=0), r_lin, rtol=1e-12)
+        lb, (s, s_lin) = oracle.lower_bound(p, lam, cap=False)
+        Xs = np.where(lin[:, None], X * s_lin[None, :], X * s[None, :])
+        assert np.all(Xs.sum(axis=0) <= p.R * (1 + 1e-12))
+        t = (p.A.astype(np.float64) * Xs).sum(axis=1)
+        assert lb == pytest.approx(oracle.utility_of(p, t), rel=1e-12)
+        uniform = oracle.scaled_utility(p, lam, oracle.column_scale(p.R, r, cap=False), cap=False)
+        assert lb <= g                                          # weak duality
+    assert (g - lb) < 0.5 * (g - uniform)                       # tighter near the optimum
 
 
 def test_subgradient_matches_finite_differences(oracle):
