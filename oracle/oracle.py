@@ -158,23 +158,27 @@ def column_scales(R, r, r_lin, cap=True):
     """(s, s_lin): column scaling with a separate factor for the jobs with a
     linear utility.  With the per-job cap both are the paper's min(1, R/r).
     Without it, the linear-utility jobs sit at their target t = T, where
-    more throughput adds nothing, so their columns are only scaled down,
-    s_lin = min(1, R / r_lin); the capacity left, R - s_lin r_lin, goes to
-    the other jobs, s = (R - s_lin r_lin) / (r - r_lin) (1 where those use
-    nothing)."""
+    more throughput adds nothing (and below which each unit is worth at
+    least its price), so while they use less than R_j they keep their
+    allocation, s_lin = 1, and the other jobs are scaled to the capacity
+    left, s = (R - r_lin) / (r - r_lin); a column that the linear jobs alone
+    fill, or nearly alone use (other jobs below 1e-3 r, where r - r_lin
+    would lose its digits to rounding), is scaled uniformly, s = s_lin =
+    R / r."""
     R = np.asarray(R, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64)
     r_lin = np.asarray(r_lin, dtype=np.float64)
     if cap:
         s = column_scale(R, r, True)
         return s, s.copy()
-    s_lin = np.ones_like(R)
-    over = r_lin > R
-    s_lin[over] = R[over] / r_lin[over]
+    s = column_scale(R, r, False)
+    s_lin = s.copy()
     r_oth = r - r_lin
-    s = np.ones_like(R)
-    use = r_oth > 0
-    s[use] = np.maximum(R[use] - s_lin[use] * r_lin[use], 0.0) / r_oth[use]
+    room = r_lin < R
+    s_lin[room] = 1.0
+    use = room & (r_oth > 1e-3 * r)
+    s[use] = (R[use] - r_lin[use]) / r_oth[use]
+    s_lin[room & ~use] = s[room & ~use]       # (almost) only linear jobs: uniform
     return s, s_lin
 
 
