@@ -223,7 +223,7 @@ ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jst
  * device pointers; A, kind, w, param must be 16-byte aligned.  Work is
  * enqueued on `stream`.
  *
- * Scratch: one static device array of about 296 KB in this library, which
+ * Scratch: one static device array of about 546 KB in this library, which
  * every GPU that loads libra.so keeps until the process exits.  It holds the
  * per-CTA partial sums of at most 1024 CTAs; a GPU whose evaluation would use
  * more CTAs is refused with RA_EINVAL.  Any n and 1 <= m <= RA_MAX_M are
@@ -315,6 +315,10 @@ ra_status ra_batch_solve(ra_batch *b, const ra_solve_opts *opts, const double *l
 #define RA_MLP_IN 26
 #define RA_MLP_HIDDEN 256
 #define RA_MLP_PARAMS 72961
+/* The network is trained on log(lambda* + RA_MLP_PRICE_OFFSET), so that zero
+ * prices (resources left with slack) have a finite target; its prices are
+ * lambda_j = max(exp(y_j) - RA_MLP_PRICE_OFFSET, 0). */
+#define RA_MLP_PRICE_OFFSET 1e-3
 
 typedef struct ra_mlp ra_mlp; /* opaque; owns parameters, Adam moments, activations */
 
@@ -343,8 +347,9 @@ ra_status ra_warmstart_features(ra_problem *prob, float *feats);
 ra_status ra_batch_features(ra_batch *b, float *feats);
 
 /*
- * ra_warmstart_prices -- start prices for ra_solve: lambda_w = exp(MLP(x_j))
- * and the cold start lambda_c of Eq. e-initialization are both evaluated,
+ * ra_warmstart_prices -- start prices for ra_solve: lambda_w = max(exp(MLP(x_j))
+ * - RA_MLP_PRICE_OFFSET, 0) and the cold start lambda_c of Eq.
+ * e-initialization are both evaluated,
  * and lambda0 (device, m FP64) receives lambda_w when g(lambda_w) is finite
  * and g(lambda_w) <= g(lambda_c), else lambda_c.  used_warm (host, or NULL
  * to stay asynchronous) receives 1 when the network's prices were kept.

@@ -212,6 +212,7 @@ __device__ __forceinline__ int colof(int k, int rot)
 template <typename Real>
 struct JobSol {
     Real t, h;
+    Real u;           // u(t): the job's utility at the optimum
     Real xP, xQ;      // time fractions on the segment ends (P may be the origin)
     Real tP, tQ;      // throughput delivered by P and by Q
     int cP, cQ;       // columns, -1 = none
@@ -272,6 +273,7 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
         s.xQ = Real(0);
         s.tQ = Real(0);
         s.h = util<Real>(kind, w, p, Real(0));
+        s.u = s.h;
         return;
     }
     Real aQ, lQ;
@@ -330,8 +332,17 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
         }
     }
     s.t = t;
-    const Real cost = lP + alpha * (t - aP);
-    s.h = util<Real>(kind, w, p, t) - cost;
+    const Real u = util<Real>(kind, w, p, t);
+    s.u = u;
+    s.h = u - (lP + alpha * (t - aP));
+    if (!CAP && kind <= RA_U_POWER) {
+        // interior optimum t = (u')^{-1}(alpha) on [0, inf): alpha t = w for
+        // log and alpha t = p u(t) for power, so h = u(t) - alpha t is formed
+        // without the cancellation of two huge terms (t overflows FP32 for
+        // prices near zero; h is then +inf, never inf - inf).  Selects only:
+        // u is evaluated once for every kind of a warp.
+        s.h = !(alpha > Real(0)) ? Fn<Real>::inf() : kind == RA_U_LOG ? u - w : (Real(1) - p) * u;
+    }
     Real xQ, xP;
     if (CAP) {
         const Real den = aQ - aP;
@@ -413,16 +424,37 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+// Usage of the warp's linear-utility jobs per column (no-cap mode, where a
+// job uses one column, cQ): one butterfly sum per distinct column among
+// those lanes, taken in lane order; lane c adds column c's sum to acc.
+template <typename Real>
+__device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real> &s, double &acc)
+{
+    const bool on = lin && s.cQ >= 0;
+    unsigned mask = __ballot_sync(kFull, on);
+    while (mask) {
+        const int c = __shfl_sync(kFull, s.cQ, __ffs(mask) - 1);
+        const bool mine = on && s.cQ == c;
+        Real v = mine ? s.xQ : Real(0);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == c) acc += static_cast<double>(v);
+        mask &= ~__ballot_sync(kFull, mine);
+    }
+}
+
 // Block stage + grid stage: per-thread FP64 values -> per-block partials
 // (fixed warp order) -> the last CTA to finish sums the partials in block
 // order.  Returns true in that CTA only, where red[0][0 .. m+4) then holds the
-// totals (h, U(X), lagged U_lb, spare, r_0..r_{m-1}).  red is kWarps x kPartW.
-__device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc, int m,
-                            bool lane_owns_col, double *partials, unsigned *ticket,
+// totals (h, U(X), lagged U_lb, spare, r_0..r_{m-1}, then r_lin_0..r_lin_{m-1}
+// when lin is set).  red is kWarps x kPartW.
+__device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc, double rlin,
+                            int m, bool lin, bool lane_owns_col, double *partials, unsigned *ticket,
                             double (*red)[kPartW])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ int is_last;
+    const int nv = lin ? 2 * m + 4 : m + 4;
     hsum = warp_sum_d(hsum);
     uxsum = warp_sum_d(uxsum);
     lbsum = warp_sum_d(lbsum);
@@ -433,8 +465,9 @@ __device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc
         red[warp][3] = 0.0;
     }
     if (lane < m) red[warp][4 + lane] = lane_owns_col ? racc : 0.0;
+    if (lin && lane < m) red[warp][4 + m + lane] = rlin;
     __syncthreads();
-    if (tid < m + 4) {
+    if (tid < nv) {
         double v = 0.0;
         for (int w = 0; w < kWarps; ++w) v += red[w][tid];
         partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
@@ -445,7 +478,7 @@ __device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    if (tid < m + 4) {
+    if (tid < nv) {
         double v = 0.0;
         for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[static_cast<size_t>(b) * kPartW + tid]);
         red[0][tid] = v;
@@ -457,14 +490,17 @@ __device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc
 
 // Dual outputs (Section 3): g = lambda^T R + sum h_i, q = R - r.
 __device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, double racc,
-                                    int m, bool lane_owns_col, const DualParams &P,
-                                    double (*red)[kPartW])
+                                    double rlin, int m, bool lin, bool lane_owns_col,
+                                    const DualParams &P, double (*red)[kPartW])
 {
-    if (!grid_reduce(hsum, uxsum, lbsum, racc, m, lane_owns_col, P.partials, P.ticket, red)) return;
+    if (!grid_reduce(hsum, uxsum, lbsum, racc, rlin, m, lin, lane_owns_col, P.partials, P.ticket,
+                     red))
+        return;
     const int tid = threadIdx.x;
     if (tid < m) {
         P.out->r[tid] = red[0][4 + tid];
         P.out->q[tid] = P.R[tid] - red[0][4 + tid];
+        P.out->r_lin[tid] = lin ? red[0][4 + m + tid] : 0.0;
     }
     if (tid == 0) {
         double lr = 0.0;
@@ -608,6 +644,7 @@ __global__ void __launch_bounds__(kTile, 2)
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ float lam_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
+    __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
 
     if (P.skip != nullptr && *P.skip != 0) return;
@@ -633,6 +670,9 @@ __global__ void __launch_bounds__(kTile, 2)
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<float>(P.lam[tid]) : Fn<float>::inf();
         s_s[tid] = (LAG && lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
+        sl_s[tid] = (LAG && lag && tid < m)
+                        ? static_cast<float>((P.s_lin_prev ? P.s_lin_prev : P.s_prev)[tid])
+                        : 1.0f;
     }
     __syncthreads();
     float lam_r[MT], mu_r[MT];
@@ -643,7 +683,7 @@ __global__ void __launch_bounds__(kTile, 2)
         mu_r[k] = inv_price<float>(lam_s[c]);
     }
 
-    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
+    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0, rlin = 0.0;
     auto job = [&](long long i, bool valid, const float *row, int kind, float w, float p,
                    float *warp_rows) {
         // the previous evaluation's record is read first so that its latency
@@ -667,11 +707,12 @@ __global__ void __launch_bounds__(kTile, 2)
             };
             solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
             hsum += static_cast<double>(s.h);
-            uxsum += static_cast<double>(util<float>(kind, w, p, s.t));
+            uxsum += static_cast<double>(s.u);
             if (LAG && lag) {
+                const float *sc = kind >= RA_U_LINCAP ? sl_s : s_s;
                 float tt = 0.f;
-                if (jp.x != 255) tt += s_s[jp.x] * tp.x;
-                if (jp.y != 255) tt += s_s[jp.y] * tp.y;
+                if (jp.x != 255) tt += sc[jp.x] * tp.x;
+                if (jp.y != 255) tt += sc[jp.y] * tp.y;
                 lbsum += static_cast<double>(util<float>(kind, w, p, tt));
             }
             if (REC) {
@@ -680,10 +721,12 @@ __global__ void __launch_bounds__(kTile, 2)
             }
         }
         warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, s, racc);
+        if (!CAP) warp_rlin<float>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job);
-    reduce_and_finalize(hsum, uxsum, lbsum, racc, m, grouped ? (lane / MT == 0) : true, P, red);
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, grouped ? (lane / MT == 0) : true, P,
+                        red);
 }
 
 // Initial prices, Eq. e-initialization:
@@ -747,7 +790,8 @@ __global__ void __launch_bounds__(kTile, 2)
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
-    if (grid_reduce(0.0, 0.0, 0.0, racc, m, grouped ? (lane / MT == 0) : true, partials, ticket, red))
+    if (grid_reduce(0.0, 0.0, 0.0, racc, 0.0, m, false, grouped ? (lane / MT == 0) : true, partials,
+                    ticket, red))
         if (tid < m) lam1[tid] = red[0][4 + tid] / static_cast<double>(n);
 }
 
@@ -818,6 +862,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ float lam_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
+    __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
     __shared__ int is_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -859,7 +904,8 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
     cursor_first(B, cur);
     long long consumed = 0;
     float lam_r[MT], mu_r[MT];
-    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
+    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0, rlin = 0.0;
+    const int nv_lin = CAP ? 0 : 1;
     while (cur.c < B.nchunks) {
         const int p = B.chunk_prob[cur.c];
         const BatchProblem &P = B.probs[p];
@@ -877,6 +923,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
             if (tid < RA_MAX_M) {
                 lam_s[tid] = tid < m ? static_cast<float>(B.st[p].lam_trial[tid]) : Fn<float>::inf();
                 s_s[tid] = (lag && tid < m) ? static_cast<float>(B.st[p].s_lag[tid]) : 1.0f;
+                sl_s[tid] = (lag && tid < m) ? static_cast<float>(B.st[p].s_lin_lag[tid]) : 1.0f;
             }
             __syncthreads();
 #pragma unroll
@@ -885,7 +932,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 lam_r[k] = lam_s[c];
                 mu_r[k] = inv_price<float>(lam_s[c]);
             }
-            hsum = uxsum = lbsum = racc = 0.0;
+            hsum = uxsum = lbsum = racc = rlin = 0.0;
         }
         const long long t = B.chunk_tile0[cur.c] + cur.k;
         const bool full = (t + 1) * kTile <= P.n;
@@ -947,11 +994,12 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
             };
             solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, pr, sol);
             hsum += static_cast<double>(sol.h);
-            uxsum += static_cast<double>(util<float>(kind, w, pr, sol.t));
+            uxsum += static_cast<double>(sol.u);
             if (lag) {
+                const float *sc = kind >= RA_U_LINCAP ? sl_s : s_s;
                 float tt = 0.f;
-                if (jp.x != 255) tt += s_s[jp.x] * tp.x;
-                if (jp.y != 255) tt += s_s[jp.y] * tp.y;
+                if (jp.x != 255) tt += sc[jp.x] * tp.x;
+                if (jp.y != 255) tt += sc[jp.y] * tp.y;
                 lbsum += static_cast<double>(util<float>(kind, w, pr, tt));
             }
             lbt_out[i] = make_float2(sol.tP, sol.tQ);
@@ -959,6 +1007,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
         }
         if (full) warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, sol, racc);
         else warp_rsum_shfl<float>(m, lane, sol, racc);
+        if (!CAP) warp_rlin<float>(valid && kind >= RA_U_LINCAP, lane, sol, rlin);
         __syncthreads();  // stage consumed
         if (full) {
             ++consumed;
@@ -978,8 +1027,9 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 red[warp][3] = 0.0;
             }
             if (lane < m) red[warp][4 + lane] = (grouped ? (lane / MT == 0) : true) ? racc : 0.0;
+            if (nv_lin && lane < m) red[warp][4 + m + lane] = rlin;
             __syncthreads();
-            if (tid < m + 4) {
+            if (tid < (1 + nv_lin) * m + 4) {
                 double v = 0.0;
                 for (int w2 = 0; w2 < kWarps; ++w2) v += red[w2][tid];
                 B.partials[static_cast<size_t>(cur.c) * kPartW + tid] = v;
@@ -993,7 +1043,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
             __syncthreads();
             if (is_last) {
                 __threadfence();
-                if (tid < m + 4) {
+                if (tid < (1 + nv_lin) * m + 4) {
                     double v = 0.0;
                     for (int c2 = P.chunk_begin; c2 < P.chunk_end; ++c2)
                         v += __ldcg(&B.partials[static_cast<size_t>(c2) * kPartW + tid]);
@@ -1004,6 +1054,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 if (tid < m) {
                     out->r[tid] = red[0][4 + tid];
                     out->q[tid] = P.R[tid] - red[0][4 + tid];
+                    out->r_lin[tid] = nv_lin ? red[0][4 + m + tid] : 0.0;
                 }
                 if (tid == 0) {
                     double lr = 0.0;
@@ -1016,7 +1067,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 }
             }
             __syncthreads();
-            hsum = uxsum = lbsum = racc = 0.0;
+            hsum = uxsum = lbsum = racc = rlin = 0.0;
         }
         cursor_next(B, cur);
     }
@@ -1108,6 +1159,7 @@ __global__ void __launch_bounds__(kTile)
     extern __shared__ __align__(16) unsigned char smem_simple[];
     __shared__ Real lam_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
+    __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
     Real *rows = reinterpret_cast<Real *>(smem_simple);  // kTile x m
 
@@ -1129,6 +1181,9 @@ __global__ void __launch_bounds__(kTile)
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<Real>(P.lam[tid]) : Fn<Real>::inf();
         s_s[tid] = (lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
+        sl_s[tid] = (lag && tid < m)
+                        ? static_cast<float>((P.s_lin_prev ? P.s_lin_prev : P.s_prev)[tid])
+                        : 1.0f;
     }
     __syncthreads();
     Real lam_r[MT], mu_r[MT];
@@ -1137,7 +1192,7 @@ __global__ void __launch_bounds__(kTile)
         lam_r[k] = lam_s[k];
         mu_r[k] = inv_price<Real>(lam_s[k]);
     }
-    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0;
+    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0, rlin = 0.0;
     const long long stride = static_cast<long long>(gridDim.x) * kTile;
     const long long nround = (P.n + stride - 1) / stride;
     for (long long rr = 0; rr < nround; ++rr) {
@@ -1161,13 +1216,14 @@ __global__ void __launch_bounds__(kTile)
             };
             solve_job<MT, CAP, false, Real>(a, lam_r, mu_r, 0, fetch, kind, w, p, s);
             hsum += static_cast<double>(s.h);
-            uxsum += static_cast<double>(util<Real>(kind, w, p, s.t));
+            uxsum += static_cast<double>(s.u);
             if (lag) {
                 const float2 tp = lbt_prev[i];
                 const uchar2 jp = lbj_prev[i];
+                const float *sc = kind >= RA_U_LINCAP ? sl_s : s_s;
                 Real tt = Real(0);
-                if (jp.x != 255) tt += static_cast<Real>(s_s[jp.x]) * static_cast<Real>(tp.x);
-                if (jp.y != 255) tt += static_cast<Real>(s_s[jp.y]) * static_cast<Real>(tp.y);
+                if (jp.x != 255) tt += static_cast<Real>(sc[jp.x]) * static_cast<Real>(tp.x);
+                if (jp.y != 255) tt += static_cast<Real>(sc[jp.y]) * static_cast<Real>(tp.y);
                 lbsum += static_cast<double>(util<Real>(kind, w, p, tt));
             }
             if (REC) {
@@ -1176,30 +1232,35 @@ __global__ void __launch_bounds__(kTile)
             }
         }
         warp_rsum<MT, Real>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
+        if (!CAP) warp_rlin<Real>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
     }
-    reduce_and_finalize(hsum, uxsum, lbsum, racc, m, true, P, red);
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, true, P, red);
 }
 
 // ---------------------------------------------------------------------------- lower bound
 
-// U(X~) = sum_i u_i(s_P t_P + s_Q t_Q), s = min(1, R / r) from an evaluation's r
-// (Section 5, column scaling), from the compact per-job records.
+// U(X~) = sum_i u_i(s_P t_P + s_Q t_Q), s the column scaling of an evaluation's
+// r and r_lin (Section 5; see column_scales), from the compact per-job records.
 __global__ void __launch_bounds__(kTile)
     lower_bound_kernel(const uint8_t *kind, const float *w, const float *param, const float2 *lbt,
                        const uchar2 *lbj, long long n, int m, const EvalOut *src, const double *R,
-                       double *partials, unsigned *ticket, double *U_lb)
+                       int cap, double *partials, unsigned *ticket, double *U_lb)
 {
     __shared__ float s_s[RA_MAX_M];
+    __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps];
     __shared__ int is_last;
     const int tid = threadIdx.x;
     if (tid < RA_MAX_M) {
-        float s = 1.0f;
+        float s = 1.0f, sl = 1.0f;
         if (tid < m) {
-            const double r = src->r[tid];
-            s = r > R[tid] ? static_cast<float>(R[tid] / r) : 1.0f;
+            double sd, sld;
+            column_scales(R[tid], src->r[tid], src->r_lin[tid], cap, sd, sld);
+            s = static_cast<float>(sd);
+            sl = static_cast<float>(sld);
         }
         s_s[tid] = s;
+        sl_s[tid] = sl;
     }
     __syncthreads();
     double acc = 0.0;
@@ -1207,10 +1268,12 @@ __global__ void __launch_bounds__(kTile)
          i += static_cast<long long>(gridDim.x) * kTile) {
         const float2 tp = lbt[i];
         const uchar2 jp = lbj[i];
+        const int kd = kind[i];
+        const float *sc = kd >= RA_U_LINCAP ? sl_s : s_s;
         float tt = 0.f;
-        if (jp.x != 255) tt += s_s[jp.x] * tp.x;
-        if (jp.y != 255) tt += s_s[jp.y] * tp.y;
-        acc += static_cast<double>(util<float>(kind[i], w[i], param[i], tt));
+        if (jp.x != 255) tt += sc[jp.x] * tp.x;
+        if (jp.y != 255) tt += sc[jp.y] * tp.y;
+        acc += static_cast<double>(util<float>(kd, w[i], param[i], tt));
     }
     acc = warp_sum_d(acc);
     if ((tid & 31) == 0) red[tid >> 5] = acc;
@@ -1473,7 +1536,8 @@ cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uch
     long long blocks = (p->n + kTile - 1) / kTile;
     if (blocks > p->grid_aux) blocks = p->grid_aux;
     lower_bound_kernel<<<static_cast<int>(blocks), kTile, 0, s>>>(
-        p->kind, p->w, p->param, lbt, lbj, p->n, p->m, src, p->R, p->partials, p->ticket + 1, U_lb);
+        p->kind, p->w, p->param, lbt, lbj, p->n, p->m, src, p->R, !(p->flags & RA_NO_JOB_CAP),
+        p->partials, p->ticket + 1, U_lb);
     return cudaGetLastError();
 }
 

@@ -16,13 +16,42 @@ constexpr int kMaxStages = 8;
 constexpr int kMaxLbfgsMem = 16;
 constexpr int kHist = 512;          // solver history length
 constexpr int kHistCols = 6;        // eval, g, best U_lb, gap, master-LP value, LP pivots
-constexpr int kPartW = RA_MAX_M + 4; // doubles per block partial: h, U(X), U_lb(prev), spare, r[m]
+constexpr int kPartW = 2 * RA_MAX_M + 4; // doubles per block partial: h, U(X), U_lb(prev), spare, r[m], r_lin[m]
 constexpr int kCand = 64;           // master-LP candidates kept (two per evaluation)
 constexpr size_t kWarmBytes = 8192; // per-problem warm-start scratch
 
 // Status word bits written by kernels (never trap: a kernel that gives up
 // records why and returns).
 constexpr int kStatusTimeout = 1;
+
+// Column scaling of Section 5 that makes the evaluated allocation feasible,
+// for one column with usage r, of which r_lin by jobs with a linear utility.
+// With the per-job cap both factors are min(1, R / r): the over-used column
+// is scaled down.  Without the cap nothing bounds a job's x_i, so the column
+// is scaled to use exactly R: while the linear-utility jobs (at t = T, where
+// more throughput is worth nothing) use less than R they keep their
+// allocation, s_lin = 1, and the other jobs get the capacity left,
+// s = (R - r_lin) / (r - r_lin); a column that the linear jobs alone fill, or
+// nearly alone use (others below 1e-3 r, where r - r_lin would lose its
+// digits to rounding), is scaled uniformly, s = s_lin = R / r.  s stays
+// below 1e30 so that FP32 products cannot overflow.
+__host__ __device__ inline void column_scales(double R, double r, double r_lin, int cap, double &s,
+                                              double &s_lin)
+{
+    if (cap) {
+        s = r > R ? R / r : 1.0;
+        s_lin = s;
+        return;
+    }
+    const double r_oth = r - r_lin;
+    if (r_lin < R && r_oth > 1e-3 * r) {
+        s_lin = 1.0;
+        s = fmin((R - r_lin) / r_oth, 1e30);
+    } else {
+        s = r > 0.0 ? fmin(R / r, 1e30) : 1.0;
+        s_lin = s;
+    }
+}
 
 // Result slots of one dual evaluation (device, FP64).
 struct EvalOut {
@@ -32,6 +61,7 @@ struct EvalOut {
     double sumh;     // sum_i h_i
     double q[RA_MAX_M];
     double r[RA_MAX_M];
+    double r_lin[RA_MAX_M];  // part of r used by linear-utility jobs (kinds 2, 3; no-cap mode)
 };
 
 // Projected L-BFGS state of one solve, entirely in device memory.
@@ -51,7 +81,7 @@ struct SolverState {
     int32_t max_evals;
     int32_t update;       // 0 L-BFGS, 1 subgradient
     int32_t hist_len;
-    int32_t pad_;
+    int32_t cap;          // per-job cap 1^T x_i <= 1 (selects the column scaling)
     double tol;
     double lam_floor;
     double g_cur;
@@ -99,6 +129,8 @@ struct SolverState {
     double lam_best[RA_MAX_M];
     double lam_lb[RA_MAX_M];      // prices whose scaled allocation gave U_best
     double s_lag[RA_MAX_M];       // column scaling of the previous evaluation (lower bound)
+    double s_lin_lag[RA_MAX_M];   // the same for its linear-utility jobs
+    double r_lin_prev[RA_MAX_M];  // r_lin of the previous evaluation
     double R[RA_MAX_M];
     double S[kMaxLbfgsMem][RA_MAX_M];
     double Y[kMaxLbfgsMem][RA_MAX_M];
@@ -154,6 +186,7 @@ struct DualParams {
     const float2 *lbt_prev;
     const uchar2 *lbj_prev;
     const double *s_prev;
+    const double *s_lin_prev; // scaling of the linear-utility jobs (NULL: s_prev)
     // compact record of this evaluation (NULL = not written)
     float2 *lbt_out;
     uchar2 *lbj_out;

@@ -82,6 +82,7 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
         st->max_evals = max_evals;
         st->update = update;
         st->hist_len = 0;
+        st->cap = cap;
         st->tol = tol;
         st->lam_floor = fl;
         st->g_best = __longlong_as_double(0x7ff0000000000000ll);
@@ -276,7 +277,9 @@ __global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, con
             st->cand_lam[s_slotU][tid] = st->lam_trial[tid];
         }
         if (s_slotS >= 0) {
-            st->cand_r[s_slotS][tid] = fmin(st->r_prev[tid], st->R[tid]);
+            // usage of the scaled allocation
+            st->cand_r[s_slotS][tid] = st->s_lag[tid] * (st->r_prev[tid] - st->r_lin_prev[tid]) +
+                                       st->s_lin_lag[tid] * st->r_lin_prev[tid];
             st->cand_lam[s_slotS][tid] = st->lam_prev_eval[tid];
         }
         Rr[tid] = st->R[tid];
@@ -684,6 +687,7 @@ __global__ void __launch_bounds__(32)
     if (active) {
         st->lam_prev_eval[j] = lam_t;
         st->r_prev[j] = r_t;
+        st->r_lin_prev[j] = ev->r_lin[j];
     }
     double g_best = st->g_best;
     const bool improved = g_t < g_best;
@@ -695,7 +699,12 @@ __global__ void __launch_bounds__(32)
         }
     }
     // column scaling of this evaluation, consumed by the next pass
-    if (active) st->s_lag[j] = r_t > st->R[j] ? st->R[j] / r_t : 1.0;
+    if (active) {
+        double sc, scl;
+        column_scales(st->R[j], r_t, ev->r_lin[j], st->cap, sc, scl);
+        st->s_lag[j] = sc;
+        st->s_lin_lag[j] = scl;
+    }
     const double den = fmax(fmax(fabs(U_best), fabs(g_best)), 1.0);
     const bool finite = isfinite(U_best) && isfinite(g_best);
     const double gap = finite ? (g_best - U_best) / den : __longlong_as_double(0x7ff0000000000000ll);
@@ -871,6 +880,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     dp.m = p->m;
     dp.lam = st->lam_trial;
     dp.s_prev = st->s_lag;
+    dp.s_lin_prev = st->s_lin_lag;
     dp.lbt_prev = p->lbt[0];  // non-NULL selects the lagged instantiation
     dp.lbj_prev = p->lbj[0];
     dp.lbt_out = p->lbt[1];

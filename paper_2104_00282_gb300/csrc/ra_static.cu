@@ -16,7 +16,7 @@ constexpr size_t kPartialBytes = sizeof(double) * ra::kPartW * kStaticMaxCtas;
 constexpr size_t kOutOffset = kPartialBytes;
 constexpr size_t kTicketOffset = kOutOffset + ((sizeof(ra::EvalOut) + 255) / 256) * 256;
 constexpr size_t kStatusOffset = kTicketOffset + 256;
-constexpr size_t kScratchBytes = kStatusOffset + 256;  // about 296 KB
+constexpr size_t kScratchBytes = kStatusOffset + 256;  // about 546 KB
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 

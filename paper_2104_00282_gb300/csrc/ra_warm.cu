@@ -311,7 +311,7 @@ __global__ void adam_kernel(int np, float *theta, const float *grad, float *m1, 
 __global__ void exp_prices_kernel(int m, const float *y, double *lam)
 {
     const int j = threadIdx.x;
-    if (j < m) lam[j] = exp(static_cast<double>(y[j]));
+    if (j < m) lam[j] = fmax(exp(static_cast<double>(y[j])) - RA_MLP_PRICE_OFFSET, 0.0);
 }
 
 // Start prices: the network's when their dual value is finite and not larger

@@ -20,6 +20,7 @@ RA_U_LOG, RA_U_POWER, RA_U_LINCAP, RA_U_TARGET = range(4)
 RA_JOB_CAP, RA_NO_JOB_CAP, RA_FP64_JOBMATH, RA_VALIDATE = 0x0, 0x1, 0x2, 0x4
 RA_MAX_M = 32
 RA_MLP_STATS, RA_MLP_IN, RA_MLP_HIDDEN, RA_MLP_PARAMS = 13, 26, 256, 72961
+RA_MLP_PRICE_OFFSET = 1e-3
 
 
 class RaError(RuntimeError):
@@ -515,6 +516,27 @@ class AllocationBatch:
         self.m_total = ra_batch_prices(self.handle)
         self.lam_off = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
         self.prices = None
+
+    @classmethod
+    def from_tensors(cls, tensors, job_cap=True, stream=None):
+        """Batch over device tensors (A, kind, w, param, R) per problem, used in
+        place (they must stay alive with the batch; each is kept referenced)."""
+        import numpy as np
+        self = cls.__new__(cls)
+        self.P = len(tensors)
+        self.n = [int(t[0].shape[0]) for t in tensors]
+        self.m = [int(t[0].shape[1]) for t in tensors]
+        self.tensors = [tuple(x.contiguous() for x in t) for t in tensors]
+        self.dev = {"A": self.tensors[0][0]}
+        self.flags = 0 if job_cap else RA_NO_JOB_CAP
+        self.stream = stream
+        cols = list(zip(*self.tensors))
+        ptrs = [[x.data_ptr() for x in col] for col in cols]
+        self.handle = ra_batch_create(self.n, self.m, *ptrs, self.flags, stream)
+        self.m_total = ra_batch_prices(self.handle)
+        self.lam_off = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
+        self.prices = None
+        return self
 
     def solve(self, tol=1e-6, max_evals=500, lam0=None, use_graph=True, master_lb=True,
               lbfgs_mem=10):

@@ -19,7 +19,8 @@ A problem is (Section 2.4, problem (e-res-alloc)):
 * ``R``     -- m FP64 resource limits.
 
 Every generator takes an explicit seed; the same (recipe, sizes, seed)
-always yields bit-identical arrays on any machine (numpy PCG64 streams).
+always yields bit-identical arrays on any machine (numpy PCG64 streams);
+``hetero_device`` alone draws on the GPU with torch's seeded generator.
 """
 from __future__ import annotations
 
@@ -231,3 +232,35 @@ def mlp_init(seed: int = 0) -> np.ndarray:
         b = 1.0 / math.sqrt(fan)
         parts.append(rng.uniform(-b, b, size=shape).astype(np.float32).ravel())
     return np.concatenate(parts)
+
+
+def device_seed(recipe: int, seed: int, idx: int = 0) -> int:
+    """63-bit seed of a torch generator for (recipe, seed, idx)."""
+    state = np.random.SeedSequence([recipe, idx, seed]).generate_state(2, np.uint32)
+    return int((int(state[0]) << 31) ^ int(state[1]))
+
+
+def hetero_device(n: int, m: int, seed: int, idx: int, device, recipe: int = 50):
+    """The heterogeneous-hardware recipe of ``config_hetero`` drawn directly on
+    a CUDA device with a seeded torch generator (for corpora too large to
+    generate on the host; reproducible for a given torch version and GPU):
+    A_ij = s_j exp(0.5 z), s_j ~ U[0.5, 4]; 50 % log and 50 % power utilities
+    (p ~ U[0.2, 0.8]); w ~ U[0.5, 2]; R_j ~ U[0.1, 0.4] n.  Returns device
+    tensors (A, kind, w, param, R)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(device_seed(recipe, seed, idx))
+    s = 0.5 + 3.5 * torch.rand(m, generator=g, device=device)
+    A = torch.randn(n, m, generator=g, device=device).mul_(0.5).exp_().mul_(s)
+    kind = (torch.rand(n, generator=g, device=device) >= 0.5).to(torch.uint8)
+    w = 0.5 + 1.5 * torch.rand(n, generator=g, device=device)
+    p = 0.2 + 0.6 * torch.rand(n, generator=g, device=device)
+    param = torch.where(kind == U_POWER, p, torch.zeros_like(p))
+    R = (0.1 + 0.3 * torch.rand(m, generator=g, device=device, dtype=torch.float64)) * n
+    return A.contiguous(), kind, w.contiguous(), param.contiguous(), R
+
+
+def warmstart_sizes(P: int, seed: int = 0, n_lo: int = 10_000, n_hi: int = 1_000_000) -> np.ndarray:
+    """n of the P problems of a warm-start corpus: log-uniform in [n_lo, n_hi]."""
+    rng = _rng(11, seed)
+    return np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=P))).astype(np.int64)

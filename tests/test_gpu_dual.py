@@ -159,11 +159,15 @@ def compare_eval(ra, O, prob, lam, cap=True, fp64=False, check_lb=True):
     mag = float(np.abs(lam * prob.R).sum() + np.abs(ora[:, 1]).sum())
     assert abs(g - g_ora) <= (1e-11 if fp64 else 2e-6) * mag, (g, g_ora)
     if check_lb:
-        s = np.where(r_gpu > prob.R, prob.R / np.maximum(r_gpu, 1e-300), 1.0)
-        tt = (A * X_mix * s[None, :]).sum(1)
+        r_lin = X_mix[kind >= 2].sum(0)
+        s, s_lin = O.column_scales(prob.R, r_gpu, r_lin, cap)
+        tt = (A * X_mix * np.where((kind >= 2)[:, None], s_lin[None, :], s[None, :])).sum(1)
         uu = _u(kind, w, par, tt)
         U_exp = float(uu.sum())
-        assert abs(U - U_exp) <= (2e-7 if fp64 else 3e-6) * (np.abs(uu).sum() + 1.0), (U, U_exp)
+        if np.isinf(U_exp):      # a job left with no throughput: both -inf
+            assert U == U_exp, (U, U_exp)
+        else:
+            assert abs(U - U_exp) <= (2e-7 if fp64 else 3e-6) * (np.abs(uu).sum() + 1.0), (U, U_exp)
     return dict(n_amb=int(amb.sum()), g=g)
 
 

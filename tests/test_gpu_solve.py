@@ -51,7 +51,9 @@ def certify(O, prob, P, cap=True):
             continue
         X, _ = O.allocation(prob, l, cap=cap)
         if sc:
-            X *= O.column_scale(prob.R, X.sum(0))[None, :]
+            Xs = X.sum(0)
+            s, s_lin = O.column_scales(prob.R, Xs, X[prob.kind >= 2].sum(0), cap)
+            X *= np.where((prob.kind >= 2)[:, None], s_lin[None, :], s[None, :])
         Xbar += th * X
     usage = Xbar.sum(0)
     assert np.all(usage <= prob.R * (1 + 3e-6) + 1e-9), (usage, prob.R)
