@@ -362,18 +362,40 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
     }
 }
 
-template <int MT, typename Real>
+// Per-thread running sums of the FP32 path: compensated FP32 (Kahan), error
+// about 2^-23 of the sum of magnitudes however many terms, so the per-job
+// adds stay off the FP64 pipe (a small fraction of the FP32 rate on this
+// GPU); converted to FP64 once, before the block and grid stages.  An
+// infinite term leaves the sum infinite (the compensation is dropped).
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = isfinite(t) ? (t - s) - y : 0.0f;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const
+    {
+        return static_cast<double>(s) - static_cast<double>(c);
+    }
+};
+__device__ __forceinline__ void acc_add(double &a, double x) { a += x; }
+__device__ __forceinline__ void acc_add(KahanF &a, float x) { a.add(x); }
+
+template <int MT, typename Real, typename Acc>
 __device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int lane, bool grouped,
-                                            double &racc);
+                                            Acc &racc);
 
 // Warp-cooperative r accumulation: each lane's `row` (m entries of shared
 // memory that the lane alone owns) becomes its dense x_i; the 32 x m block is
 // then summed column-wise in a fixed order.  `racc` of lane c (< m) gains the
 // column-c sum.  `grouped` selects the lane-split column sum used when
 // m == MT is a power of two >= 4.
-template <int MT, typename Real>
+template <int MT, typename Real, typename Acc>
 __device__ __forceinline__ void warp_rsum(Real *warp_rows, int m, int lane, bool grouped,
-                                          int rot, const JobSol<Real> &s, double &racc)
+                                          int rot, const JobSol<Real> &s, Acc &racc)
 {
     Real *row = warp_rows + lane * m;
     if (grouped && sizeof(Real) == 4) {
@@ -389,14 +411,14 @@ __device__ __forceinline__ void warp_rsum(Real *warp_rows, int m, int lane, bool
     if (s.cP >= 0) row[s.cP] = s.xP;
     if (s.cQ >= 0) row[s.cQ] = s.xQ;
     __syncwarp();
-    warp_colsum<MT, Real>(warp_rows, m, lane, grouped, racc);
+    warp_colsum<MT, Real, Acc>(warp_rows, m, lane, grouped, racc);
 }
 
 // Column sums of a warp's 32 x m block of shared memory, in a fixed order with
 // four independent partial sums; lane c (< m) adds column c's total to racc.
-template <int MT, typename Real>
+template <int MT, typename Real, typename Acc>
 __device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int lane, bool grouped,
-                                            double &racc)
+                                            Acc &racc)
 {
     if (grouped) {
         constexpr int G = 32 / MT;
@@ -407,12 +429,12 @@ __device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int la
         Real t = (cs[0] + cs[1]) + (cs[2] + cs[3]);
 #pragma unroll
         for (int off = MT; off < 32; off <<= 1) t += __shfl_xor_sync(kFull, t, off);
-        if (g == 0) racc += static_cast<double>(t);
+        if (g == 0) acc_add(racc, t);
     } else if (lane < m) {
         Real cs[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll 8
         for (int r = 0; r < 32; ++r) cs[r & 3] += warp_rows[r * m + lane];
-        racc += static_cast<double>((cs[0] + cs[1]) + (cs[2] + cs[3]));
+        acc_add(racc, (cs[0] + cs[1]) + (cs[2] + cs[3]));
     }
     __syncwarp();
 }
@@ -427,8 +449,8 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // Usage of the warp's linear-utility jobs per column (no-cap mode, where a
 // job uses one column, cQ): one butterfly sum per distinct column among
 // those lanes, taken in lane order; lane c adds column c's sum to acc.
-template <typename Real>
-__device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real> &s, double &acc)
+template <typename Real, typename Acc>
+__device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real> &s, Acc &acc)
 {
     const bool on = lin && s.cQ >= 0;
     unsigned mask = __ballot_sync(kFull, on);
@@ -438,9 +460,33 @@ __device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real>
         Real v = mine ? s.xQ : Real(0);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-        if (lane == c) acc += static_cast<double>(v);
+        if (lane == c) acc_add(acc, v);
         mask &= ~__ballot_sync(kFull, mine);
     }
+}
+
+// The same through shared memory: each linear lane posts (column, x) to the
+// warp's scratch (64 floats the warp owns), then lane c adds up the entries
+// for column c in lane order with four independent chains -- no chain of
+// dependent shuffles.  Warps without a linear job skip it.
+template <typename Acc>
+__device__ __forceinline__ void warp_rlin_smem(float *scratch, int m, bool lin, int lane,
+                                               const JobSol<float> &s, Acc &acc)
+{
+    const bool on = lin && s.cQ >= 0;
+    if (__ballot_sync(kFull, on) == 0) return;
+    float2 *post = reinterpret_cast<float2 *>(scratch);
+    __syncwarp();
+    post[lane] = make_float2(__int_as_float(on ? s.cQ : -1), on ? s.xQ : 0.0f);
+    __syncwarp();
+    float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const float2 e = post[r];
+        if (__float_as_int(e.x) == lane) cs[r & 3] += e.y;
+    }
+    if (lane < m) acc_add(acc, (cs[0] + cs[1]) + (cs[2] + cs[3]));
+    __syncwarp();
 }
 
 // Block stage + grid stage: per-thread FP64 values -> per-block partials
@@ -683,7 +729,7 @@ __global__ void __launch_bounds__(kTile, 2)
         mu_r[k] = inv_price<float>(lam_s[c]);
     }
 
-    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0, rlin = 0.0;
+    KahanF hsum, uxsum, lbsum, racc, rlin;
     auto job = [&](long long i, bool valid, const float *row, int kind, float w, float p,
                    float *warp_rows) {
         // the previous evaluation's record is read first so that its latency
@@ -706,27 +752,30 @@ __global__ void __launch_bounds__(kTile, 2)
                 lv = lam_s[c];
             };
             solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
-            hsum += static_cast<double>(s.h);
-            uxsum += static_cast<double>(s.u);
+            hsum.add(s.h);
+            uxsum.add(s.u);
             if (LAG && lag) {
                 const float *sc = kind >= RA_U_LINCAP ? sl_s : s_s;
                 float tt = 0.f;
                 if (jp.x != 255) tt += sc[jp.x] * tp.x;
                 if (jp.y != 255) tt += sc[jp.y] * tp.y;
-                lbsum += static_cast<double>(util<float>(kind, w, p, tt));
+                lbsum.add(util<float>(kind, w, p, tt));
             }
             if (REC) {
                 lbt_out[i] = make_float2(s.tP, s.tQ);
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
             }
         }
-        warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, s, racc);
-        if (!CAP) warp_rlin<float>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
+        warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, s, racc);
+        if (!CAP && REC) {  // 64 floats of the warp's rows when m >= 2, else shuffles
+            if (m >= 2) warp_rlin_smem<KahanF>(warp_rows, m, valid && kind >= RA_U_LINCAP, lane, s, rlin);
+            else warp_rlin<float, KahanF>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
+        }
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job);
-    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, grouped ? (lane / MT == 0) : true, P,
-                        red);
+    reduce_and_finalize(hsum.value(), uxsum.value(), lbsum.value(), racc.value(), rlin.value(), m,
+                        !CAP && REC, grouped ? (lane / MT == 0) : true, P, red);
 }
 
 // Initial prices, Eq. e-initialization:
@@ -758,7 +807,7 @@ __global__ void __launch_bounds__(kTile, 2)
     float x0_r[MT];
 #pragma unroll
     for (int k = 0; k < MT; ++k) x0_r[k] = x0_s[colof<MT>(k, rot)];
-    double racc = 0.0;
+    KahanF racc;
     auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
                    float *warp_rows) {
         float a[MT];
@@ -786,11 +835,11 @@ __global__ void __launch_bounds__(kTile, 2)
                 if (k < m) own[colof<MT>(k, rot)] = d * a[k];
         }
         __syncwarp();
-        warp_colsum<MT, float>(warp_rows, m, lane, grouped, racc);
+        warp_colsum<MT, float, KahanF>(warp_rows, m, lane, grouped, racc);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
-    if (grid_reduce(0.0, 0.0, 0.0, racc, 0.0, m, false, grouped ? (lane / MT == 0) : true, partials,
+    if (grid_reduce(0.0, 0.0, 0.0, racc.value(), 0.0, m, false, grouped ? (lane / MT == 0) : true, partials,
                     ticket, red))
         if (tid < m) lam1[tid] = red[0][4 + tid] / static_cast<double>(n);
 }
@@ -799,14 +848,14 @@ __global__ void __launch_bounds__(kTile, 2)
 
 // Column sums of a warp's x block without shared memory: column c is summed
 // by a butterfly over the lanes' (at most two) nonzeros and lane c adds it.
-template <typename Real>
-__device__ __forceinline__ void warp_rsum_shfl(int m, int lane, const JobSol<Real> &s, double &racc)
+template <typename Real, typename Acc>
+__device__ __forceinline__ void warp_rsum_shfl(int m, int lane, const JobSol<Real> &s, Acc &racc)
 {
     for (int c = 0; c < m; ++c) {
         float v = (s.cP == c ? static_cast<float>(s.xP) : 0.f) + (s.cQ == c ? static_cast<float>(s.xQ) : 0.f);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-        if (lane == c) racc += static_cast<double>(v);
+        if (lane == c) acc_add(racc, v);
     }
 }
 
@@ -904,7 +953,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
     cursor_first(B, cur);
     long long consumed = 0;
     float lam_r[MT], mu_r[MT];
-    double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0, rlin = 0.0;
+    KahanF hsum, uxsum, lbsum, racc, rlin;
     const int nv_lin = CAP ? 0 : 1;
     while (cur.c < B.nchunks) {
         const int p = B.chunk_prob[cur.c];
@@ -932,7 +981,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 lam_r[k] = lam_s[c];
                 mu_r[k] = inv_price<float>(lam_s[c]);
             }
-            hsum = uxsum = lbsum = racc = rlin = 0.0;
+            hsum = uxsum = lbsum = racc = rlin = KahanF{};
         }
         const long long t = B.chunk_tile0[cur.c] + cur.k;
         const bool full = (t + 1) * kTile <= P.n;
@@ -993,21 +1042,25 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 lv = lam_s[c];
             };
             solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, pr, sol);
-            hsum += static_cast<double>(sol.h);
-            uxsum += static_cast<double>(sol.u);
+            hsum.add(sol.h);
+            uxsum.add(sol.u);
             if (lag) {
                 const float *sc = kind >= RA_U_LINCAP ? sl_s : s_s;
                 float tt = 0.f;
                 if (jp.x != 255) tt += sc[jp.x] * tp.x;
                 if (jp.y != 255) tt += sc[jp.y] * tp.y;
-                lbsum += static_cast<double>(util<float>(kind, w, pr, tt));
+                lbsum.add(util<float>(kind, w, pr, tt));
             }
             lbt_out[i] = make_float2(sol.tP, sol.tQ);
             lbj_out[i] = make_uchar2(sol.cP >= 0 ? sol.cP : 255, sol.cQ >= 0 ? sol.cQ : 255);
         }
-        if (full) warp_rsum<MT, float>(warp_rows, m, lane, grouped, rot, sol, racc);
-        else warp_rsum_shfl<float>(m, lane, sol, racc);
-        if (!CAP) warp_rlin<float>(valid && kind >= RA_U_LINCAP, lane, sol, rlin);
+        if (full) warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, sol, racc);
+        else warp_rsum_shfl<float, KahanF>(m, lane, sol, racc);
+        if (!CAP) {
+            if (full && m >= 2)
+                warp_rlin_smem<KahanF>(warp_rows, m, valid && kind >= RA_U_LINCAP, lane, sol, rlin);
+            else warp_rlin<float, KahanF>(valid && kind >= RA_U_LINCAP, lane, sol, rlin);
+        }
         __syncthreads();  // stage consumed
         if (full) {
             ++consumed;
@@ -1019,15 +1072,16 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
         // chunk end: block sums -> this chunk's partial slot -> per-problem ticket
         const bool chunk_end = cur.k + 1 >= B.chunk_ntiles[cur.c];
         if (chunk_end) {
-            double h = warp_sum_d(hsum), ux = warp_sum_d(uxsum), lb = warp_sum_d(lbsum);
+            double h = warp_sum_d(hsum.value()), ux = warp_sum_d(uxsum.value()),
+                   lb = warp_sum_d(lbsum.value());
             if (lane == 0) {
                 red[warp][0] = h;
                 red[warp][1] = ux;
                 red[warp][2] = lb;
                 red[warp][3] = 0.0;
             }
-            if (lane < m) red[warp][4 + lane] = (grouped ? (lane / MT == 0) : true) ? racc : 0.0;
-            if (nv_lin && lane < m) red[warp][4 + m + lane] = rlin;
+            if (lane < m) red[warp][4 + lane] = (grouped ? (lane / MT == 0) : true) ? racc.value() : 0.0;
+            if (nv_lin && lane < m) red[warp][4 + m + lane] = rlin.value();
             __syncthreads();
             if (tid < (1 + nv_lin) * m + 4) {
                 double v = 0.0;
@@ -1067,7 +1121,7 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
                 }
             }
             __syncthreads();
-            hsum = uxsum = lbsum = racc = rlin = 0.0;
+            hsum = uxsum = lbsum = racc = rlin = KahanF{};
         }
         cursor_next(B, cur);
     }
@@ -1097,7 +1151,7 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
                 x0_s[j] = j < m ? static_cast<float>(P.R[j] / (static_cast<double>(P.n) * div)) : 0.0f;
         }
         __syncthreads();
-        double racc = 0.0;
+        KahanF racc;
         for (int k = 0; k < B.chunk_ntiles[c]; ++k) {
             const long long i = static_cast<long long>(B.chunk_tile0[c] + k) * kTile + tid;
             const bool valid = i < P.n;
@@ -1122,9 +1176,9 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
             for (int j = 0; j < MT; ++j)
                 if (j < m) own[j] = d * a[j];
             __syncwarp();
-            warp_colsum<MT, float>(rows + warp * 32 * m, m, lane, false, racc);
+            warp_colsum<MT, float, KahanF>(rows + warp * 32 * m, m, lane, false, racc);
         }
-        if (lane < m) red[warp][4 + lane] = racc;
+        if (lane < m) red[warp][4 + lane] = racc.value();
         __syncthreads();
         if (tid < m) {
             double v = 0.0;
@@ -1231,8 +1285,8 @@ __global__ void __launch_bounds__(kTile)
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
             }
         }
-        warp_rsum<MT, Real>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
-        if (!CAP) warp_rlin<Real>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
+        warp_rsum<MT, Real, double>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
+        if (!CAP) warp_rlin<Real, double>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
     }
     reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, true, P, red);
 }
@@ -1263,7 +1317,7 @@ __global__ void __launch_bounds__(kTile)
         sl_s[tid] = sl;
     }
     __syncthreads();
-    double acc = 0.0;
+    KahanF acc;
     for (long long i = static_cast<long long>(blockIdx.x) * kTile + tid; i < n;
          i += static_cast<long long>(gridDim.x) * kTile) {
         const float2 tp = lbt[i];
@@ -1273,10 +1327,10 @@ __global__ void __launch_bounds__(kTile)
         float tt = 0.f;
         if (jp.x != 255) tt += sc[jp.x] * tp.x;
         if (jp.y != 255) tt += sc[jp.y] * tp.y;
-        acc += static_cast<double>(util<float>(kd, w[i], param[i], tt));
+        acc.add(util<float>(kd, w[i], param[i], tt));
     }
-    acc = warp_sum_d(acc);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    const double accd = warp_sum_d(acc.value());
+    if ((tid & 31) == 0) red[tid >> 5] = accd;
     __syncthreads();
     if (tid == 0) {
         double v = 0.0;
