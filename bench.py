@@ -298,6 +298,7 @@ def run_gpu(args):
              "rel_gap": o_info["rel_gap"], "status": o_info["status"]}
 
     batch = run_batch(args, dev, stream) if args.batch > 0 else None
+    warm = run_warm(args) if args.warm > 0 else None
 
     if rank != 0:
         return
@@ -336,8 +337,30 @@ def run_gpu(args):
         "clocks": clk.summary(),
         ("no_job_cap" if cap else "with_job_cap"): other,
         "batched": batch,
+        "warm_start": warm,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_warm(args):
+    """Learned warm start (the committed network, trained by
+    paper_2104_00282_gb300.warmstart on 20000 solved problems): cold and warm
+    ra_solve of held-out problems of the same recipe (n log-uniform in
+    [1e4, 1e6], m = 16, no per-job cap), median device time and evaluations
+    to a 1e-6 relative gap; the warm time includes the statistics, the
+    network and both start-point evaluations."""
+    import os
+    from paper_2104_00282_gb300 import warmstart as WS
+    if not os.path.exists(WS.WEIGHTS):
+        return {"unavailable": "no trained network in the package"}
+    net = WS.load()
+    rec = WS.evaluate(net, P=args.warm, log=None)
+    net.close()
+    out = WS.summarize(rec)
+    out["held_out_seed"] = WS.EVAL_SEED
+    out["note"] = ("medians over all held-out problems; a solve that stops at the evaluation "
+                   "limit counts with its time")
+    return out
 
 
 def run_batch(args, dev, stream):
@@ -398,6 +421,8 @@ def main():
                     help="headline with the paper's per-job cap 1^T x_i <= 1 (default: X >= 0 only)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven solver loop (same kernels; lets ncu see every launch)")
+    ap.add_argument("--warm", type=int, default=200,
+                    help="held-out problems in the warm-start comparison (0 = skip)")
     ap.add_argument("--batch", type=int, default=4096,
                     help="problems in the batched solve reported beside the headline (0 = skip)")
     args = ap.parse_args()
