@@ -104,7 +104,7 @@ struct SolverState {
     int32_t master_ok;      // the best lower bound came from the master LP
     double U_master;        // value of the last master LP (-inf if none)
     int32_t lp_iters;       // pivots of the last master LP
-    int32_t pad4_;
+    int32_t lb_stall;       // evaluations since the scaled bound last closed 10 % of the gap
     int32_t mu_ok;          // mu_lp holds the LP's resource duals
     int32_t pad3_;
     double mu_lp[RA_MAX_M]; // minimiser of the cutting-plane model of g (LP duals)

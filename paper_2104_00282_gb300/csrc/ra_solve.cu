@@ -94,6 +94,7 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
         st->sg_pending = 0;
         st->cand_count = 0;
         st->cand_head = 0;
+        st->lb_stall = 0;
         st->use_master = use_master;
         st->master_ok = 0;
         st->theta_n = 0;
@@ -262,10 +263,10 @@ __global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, con
         }
         s_slotU = su;
         s_slotS = ss;
-        // the bound matters most near convergence: while the gap is above
-        // 1e-2 the LP runs on every fourth evaluation only
+        // the LP runs when the column-scaled bound has stopped closing the
+        // gap near convergence, and on every sixteenth evaluation otherwise
         s_run = st->use_master && count >= 2 && !(st->gap <= st->tol) &&
-                (st->gap < 1e-2 || (st->evals & 3) == 0);
+                ((st->gap < 1e-2 && st->lb_stall >= 2) || (st->evals & 15) == 0);
         st->U_master = -inf;
         st->mu_ok = 0;
         st->lp_iters = 0;
@@ -643,6 +644,7 @@ __global__ void __launch_bounds__(32)
     // lower bounds: the lagged column-scaled bound of the previous evaluation,
     // and U(X) itself whenever X(lambda_t) already meets r <= R
     double U_best = st->U_best;
+    const double U_prev = U_best;
     const double lam_pe = active ? st->lam_prev_eval[j] : 0.0;
     // certificate of the best bound: one allocation with weight 1, or the
     // master LP's mixture (copied, since the candidate ring moves on)
@@ -656,6 +658,9 @@ __global__ void __launch_bounds__(32)
         U_best = ev->Ux;
         cert = 2;
     }
+    // progress of the bounds this evaluation made without the master LP
+    const double own = cert ? U_best : U_prev;
+    const bool own_gain = isfinite(U_prev) ? (own - U_prev > 0.1 * (st->g_best - U_prev)) : cert != 0;
     if (st->use_master && st->U_master > U_best) {
         U_best = st->U_master;
         cert = 3;
@@ -711,6 +716,7 @@ __global__ void __launch_bounds__(32)
     __syncwarp();
     if (j == 0) {
         st->evals = evals;
+        st->lb_stall = own_gain ? 0 : st->lb_stall + 1;
         st->g_best = g_best;
         st->U_best = U_best;
         st->gap = gap;
