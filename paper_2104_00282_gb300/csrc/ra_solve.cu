@@ -214,7 +214,7 @@ struct LpShared {
     double CU[kCand];                                  // candidate utility, staged
 };
 
-__global__ void __launch_bounds__(kLpThreads) master_kernel(SolverState *st, const EvalOut *ev)
+__device__ void master_body(SolverState *st, const EvalOut *ev)
 {
     extern __shared__ __align__(16) unsigned char lp_dyn[];
     LpShared &S = *reinterpret_cast<LpShared *>(lp_dyn);
@@ -619,10 +619,9 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
 }
 
 // One update after the evaluation of st->lam_trial (results in *ev).
-__global__ void __launch_bounds__(32)
-    solver_update_kernel(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
-                         const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
-                         int32_t *done_host_flag)
+__device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
+                            const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
+                            int32_t *done_host_flag)
 {
     const int j = threadIdx.x;
     st += blockIdx.x;  // block b: problem b of a batch (one block for a single solve)
@@ -806,6 +805,20 @@ __global__ void batch_finish_kernel(const SolverState *st, const BatchProblem *p
     }
 }
 
+// One solver step after an evaluation: the master LP (all threads of the
+// CTA, when it runs), then the bookkeeping and price update (warp 0).  Block
+// b serves problem b of a batch.
+__global__ void __launch_bounds__(kLpThreads)
+    step_kernel(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
+                const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
+                int32_t *done_host_flag)
+{
+    master_body(st, ev);
+    __syncthreads();
+    if (threadIdx.x < 32)
+        update_body(st, ev, pingpong, lag_on, kstatus, cond, use_cond, done_host_flag);
+}
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -873,7 +886,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
-    if ((e = cudaFuncSetAttribute(master_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
         return fail(RA_ECUDA, "master kernel attribute: %s", cudaGetErrorString(e));
     DualParams dp{};
@@ -923,8 +936,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 cudaError_t e1 = launch_dual(p, dp, s);
-                master_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev);
-                solver_update_kernel<<<1, 32, 0, s>>>(st, p->ev, pingpong, lag_on, p->status, cond,
+                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, cond,
                                                       1, nullptr);
                 cudaError_t e2 = cudaGetLastError();
                 cudaError_t e3 = cudaStreamEndCapture(s, &body);
@@ -948,8 +960,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             for (int k = 0; k < 8; ++k) {
                 if ((e = launch_dual(p, dp, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
-                master_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev);
-                solver_update_kernel<<<1, 32, 0, s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
+                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
                                                       done_flag);
             }
             if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
@@ -1058,7 +1069,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
                                         cap, opts.master_lb, b->pingpong, b->lag_on);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "batched setup launch: %s", cudaGetErrorString(e));
-    if ((e = cudaFuncSetAttribute(master_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
         return fail(RA_ECUDA, "master kernel attribute: %s", cudaGetErrorString(e));
 
@@ -1068,8 +1079,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
             cudaError_t e1 = launch_batch_dual(4 << c, args[c], b->grid[c], batch_smem(4 << c), s);
             if (e1 != cudaSuccess) return e1;
         }
-        master_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev);
-        solver_update_kernel<<<P, 32, 0, s>>>(b->st, b->ev, b->pingpong, b->lag_on, b->status, cond,
+        step_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, b->status, cond,
                                               0, nullptr);
         batch_any_active_kernel<<<1, 1024, 0, s>>>(b->st, P, cond, use_cond, b->active);
         return cudaGetLastError();

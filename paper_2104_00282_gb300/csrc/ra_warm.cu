@@ -37,25 +37,39 @@ __device__ __forceinline__ long long sample_row(long long k, long long n, int S)
     return k * n / S;
 }
 
+// Order-preserving map of a float to an unsigned key (NaN excluded).
+__device__ __forceinline__ unsigned fkey(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float fkey_inv(unsigned k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 // Statistics of resource blockIdx.x of problem blockIdx.y: the 8 quantiles of
-// A[:, j] over the sample (order statistics at levels (2l+1)/16, exact by a
-// bitonic sort in shared memory), log(R_j / n), the fractions of log, power
-// and linear utilities and the mean of log w over the sample.
+// A[:, j] over the sample (order statistics of rank floor((2l+1) S / 16),
+// selected exactly by a radix select over the float's order-preserving key,
+// 8 bits a pass, all 8 ranks at once: integer bin counts, so the selection
+// does not depend on thread timing), log(R_j / n), the fractions of log,
+// power and linear utilities and the mean of log w over the sample.
 __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, FeatProblem one,
                                                      float *stats)
 {
-    extern __shared__ float key[];   // kSampleMax floats
+    extern __shared__ unsigned key[];   // kSampleMax keys
     __shared__ double red[32][3];
+    __shared__ unsigned hist[kQuant][256];
+    __shared__ unsigned pref[kQuant];   // key bits fixed so far
+    __shared__ unsigned rank[kQuant];   // rank within the keys matching pref
     const FeatProblem P = probs ? probs[blockIdx.y] : one;
     const int j = blockIdx.x;
     if (j >= P.m) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = P.n;
     const int S = n < kSampleMax ? static_cast<int>(n) : kSampleMax;
-    int Sp = 1;
-    while (Sp < S) Sp <<= 1;
-    for (int k = tid; k < Sp; k += blockDim.x)
-        key[k] = k < S ? P.A[sample_row(k, n, S) * P.m + j] : __int_as_float(0x7f800000);
+    for (int k = tid; k < S; k += blockDim.x) key[k] = fkey(P.A[sample_row(k, n, S) * P.m + j]);
     double c_log = 0.0, c_pow = 0.0, s_lw = 0.0;
     for (int k = tid; k < S; k += blockDim.x) {
         const long long row = sample_row(k, n, S);
@@ -75,25 +89,57 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
         red[warp][1] = c_pow;
         red[warp][2] = s_lw;
     }
-    __syncthreads();
-    // ascending bitonic sort of key[0 .. Sp)
-    for (int size = 2; size <= Sp; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < (Sp >> 1); t += blockDim.x) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const float a = key[lo], b = key[hi];
-                if ((a > b) == up) {
-                    key[lo] = b;
-                    key[hi] = a;
-                }
+    if (tid < kQuant) {
+        pref[tid] = 0u;
+        rank[tid] = static_cast<unsigned>(((2 * tid + 1) * S) / 16);
+    }
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        for (int e = tid; e < kQuant * 256; e += blockDim.x) (&hist[0][0])[e] = 0u;
+        __syncthreads();
+        for (int k = tid; k < S; k += blockDim.x) {
+            const unsigned kv = key[k];
+            const unsigned bin = (kv >> shift) & 255u;
+            if (pass == 0) {
+                atomicAdd(&hist[0][bin], 1u);   // the same histogram serves every rank
+            } else {
+#pragma unroll
+                for (int l = 0; l < kQuant; ++l)
+                    if (((kv ^ pref[l]) >> (shift + 8)) == 0u) atomicAdd(&hist[l][bin], 1u);
             }
-            __syncthreads();
         }
+        __syncthreads();
+        if (warp < kQuant) {   // warp l finds the bin holding its rank
+            const unsigned *h = hist[pass == 0 ? 0 : warp];
+            unsigned c[8], tot = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = h[lane * 8 + q];
+                tot += c[q];
+            }
+            unsigned incl = tot;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const unsigned excl = incl - tot;
+            const unsigned r = rank[warp];
+            const bool mine = r >= excl && r < incl;
+            const unsigned owner = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+                unsigned before = excl;
+                int q = 0;
+                while (q < 7 && r >= before + c[q]) before += c[q++];
+                pref[warp] |= static_cast<unsigned>(lane * 8 + q) << shift;
+                rank[warp] = r - before;
+            }
+            (void)owner;
+        }
+        __syncthreads();
     }
     float *out = stats + (P.row0 + j) * kFeatRes;
-    if (tid < kQuant) out[tid] = logf(fmaxf(key[((2 * tid + 1) * S) / 16], 1e-30f));
+    if (tid < kQuant) out[tid] = logf(fmaxf(fkey_inv(pref[tid]), 1e-30f));
     if (tid == kQuant) out[8] = static_cast<float>(log(fmax(P.R[j] / static_cast<double>(n), 1e-30)));
     if (tid == kQuant + 1) {
         double cl = 0.0, cp = 0.0, sl = 0.0;
@@ -214,6 +260,25 @@ __global__ void __launch_bounds__(256)
             }
         }
     }
+}
+
+// Few-row layer (inference on one problem's resources): CTA r computes row r,
+// thread c output column c, z = sum_k x_rk W_kc in order k = 0..K-1 with the
+// same fused multiply-adds as gemm_kernel, so both give identical bits; then
+// z + bias -> Z and GELU -> H.  Needs N == blockDim.x.
+__global__ void __launch_bounds__(256)
+    rows_bias_gelu_kernel(int K, int N, const float *X, const float *W, const float *bias, float *Z,
+                          float *H)
+{
+    extern __shared__ float xr[];
+    const int r = blockIdx.x, c = threadIdx.x;
+    for (int k = c; k < K; k += blockDim.x) xr[k] = X[static_cast<long long>(r) * K + k];
+    __syncthreads();
+    float acc = 0.0f;
+    for (int k = 0; k < K; ++k) acc = fmaf(xr[k], W[static_cast<long long>(k) * N + c], acc);
+    const float z = acc + bias[c];
+    Z[static_cast<long long>(r) * N + c] = z;
+    H[static_cast<long long>(r) * N + c] = gelu(z);
 }
 
 // y_r = h2_r . W3 + b3, one warp per row, lanes in a fixed butterfly.
@@ -384,12 +449,18 @@ cudaError_t mlp_forward(ra_mlp *net, const float *X, int rows, float *y_out, cud
     float *z1, *h1, *z2, *h2, *dz2, *dz1, *y, *dy;
     mlp_buffers(net, rows, &z1, &h1, &z2, &h2, &dz2, &dz1, &y, &dy);
     const float *th = net->theta;
-    if ((e = gemm<kEpiBiasGelu>(s, rows, kHid, kFeatIn, X, kFeatIn, 1, th + oW1, kHid, 1, nullptr,
-                                kHid, th + ob1, z1, h1)) != cudaSuccess)
-        return e;
-    if ((e = gemm<kEpiBiasGelu>(s, rows, kHid, kHid, h1, kHid, 1, th + oW2, kHid, 1, nullptr, kHid,
-                                th + ob2, z2, h2)) != cudaSuccess)
-        return e;
+    if (rows <= 64) {   // one problem's resources: one CTA per row
+        rows_bias_gelu_kernel<<<rows, kHid, kFeatIn * 4, s>>>(kFeatIn, kHid, X, th + oW1, th + ob1, z1, h1);
+        rows_bias_gelu_kernel<<<rows, kHid, kHid * 4, s>>>(kHid, kHid, h1, th + oW2, th + ob2, z2, h2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        if ((e = gemm<kEpiBiasGelu>(s, rows, kHid, kFeatIn, X, kFeatIn, 1, th + oW1, kHid, 1, nullptr,
+                                    kHid, th + ob1, z1, h1)) != cudaSuccess)
+            return e;
+        if ((e = gemm<kEpiBiasGelu>(s, rows, kHid, kHid, h1, kHid, 1, th + oW2, kHid, 1, nullptr, kHid,
+                                    th + ob2, z2, h2)) != cudaSuccess)
+            return e;
+    }
     head_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(rows, h2, th, y_out ? y_out : y);
     return cudaGetLastError();
 }
