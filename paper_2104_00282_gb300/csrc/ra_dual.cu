@@ -362,6 +362,86 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
     }
 }
 
+// Algorithm 1 without the per-job cap, FP32, for a job whose m efficiencies
+// are at `row` (shared or global memory; 16-byte aligned when grouped).  The
+// cheapest effective price is found while streaming the row in 16-byte
+// chunks (rotated by `rot` as in load_row) against the inverse prices in
+// shared memory, so no per-job register array is held -- the register
+// footprint that lets a third CTA share the SM.  Chains, tie rules and the
+// closed forms are those of solve_job<MT, false, false, float>.
+template <int MT>
+__device__ __forceinline__ void solve_job_nc(const float *row, const float *mu_s, const float *lam_s,
+                                             int m, bool grouped, int rot, int kind, float w,
+                                             float p, JobSol<float> &s)
+{
+    constexpr int C = MT / 4;
+    float bv[4] = {0.f, 0.f, 0.f, 0.f};
+    int bc[4] = {-1, -1, -1, -1};    // column of each chain's best
+    if (grouped) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int q = (c + rot) & (C - 1);
+            const float4 av = reinterpret_cast<const float4 *>(row)[q];
+            const float4 mv = reinterpret_cast<const float4 *>(mu_s)[q];
+            const float v0 = av.x * mv.x, v1 = av.y * mv.y, v2 = av.z * mv.z, v3 = av.w * mv.w;
+            if (v0 > bv[0]) { bv[0] = v0; bc[0] = 4 * q; }
+            if (v1 > bv[1]) { bv[1] = v1; bc[1] = 4 * q + 1; }
+            if (v2 > bv[2]) { bv[2] = v2; bc[2] = 4 * q + 2; }
+            if (v3 > bv[3]) { bv[3] = v3; bc[3] = 4 * q + 3; }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            if (k < m) {
+                const float v = row[k] * mu_s[k];
+                if (v > bv[k & 3]) {
+                    bv[k & 3] = v;
+                    bc[k & 3] = k;
+                }
+            }
+        }
+    }
+    float vb = bv[0];
+    int cb = bc[0];
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+        const bool take = bv[c] > vb || (bv[c] == vb && bc[c] >= 0 && (cb < 0 || bc[c] < cb));
+        if (take) {
+            vb = bv[c];
+            cb = bc[c];
+        }
+    }
+    s.best = vb;
+    s.second = 0.f;
+    s.cP = -1;
+    s.xP = 0.f;
+    s.tP = 0.f;
+    if (cb < 0) {  // no usable resource
+        s.jstar = -1;
+        s.cQ = -1;
+        s.t = 0.f;
+        s.xQ = 0.f;
+        s.tQ = 0.f;
+        s.h = util<float>(kind, w, p, 0.f);
+        s.u = s.h;
+        return;
+    }
+    const float aQ = row[cb], lQ = lam_s[cb];
+    s.jstar = cb;
+    const float alpha = lQ / aQ;
+    const float t = topt<float>(kind, w, p, alpha, 0.f, Fn<float>::inf());
+    s.t = t;
+    const float u = util<float>(kind, w, p, t);
+    s.u = u;
+    s.h = u - alpha * t;
+    if (kind <= RA_U_POWER)   // interior optimum: see solve_job
+        s.h = !(alpha > 0.f) ? Fn<float>::inf() : kind == RA_U_LOG ? u - w : (1.f - p) * u;
+    const float xQ = t / aQ;
+    s.cQ = xQ > 0.f ? cb : -1;
+    s.xQ = xQ > 0.f ? xQ : 0.f;
+    s.tQ = s.xQ * aQ;
+}
+
 // Per-thread running sums of the FP32 path: compensated FP32 (Kahan), error
 // about 2^-23 of the sum of magnitudes however many terms, so the per-job
 // adds stay off the FP64 pipe (a small fraction of the FP32 rate on this
@@ -570,9 +650,9 @@ struct StageLayout {
 // in through a ring of `stages` shared-memory buffers filled by 1-D bulk TMA
 // copies (one elected thread issues A's rows, w, param and kind of a tile and
 // arms the stage's mbarrier with the byte count); the ragged tail (n mod 256
-// jobs) is handled by one CTA from global memory.  For every job the callee
-// receives job(i, valid, row, kind, w, p, warp_rows): row points at the job's
-// m efficiencies in shared memory (nullptr in the tail), warp_rows at the 32 x
+// jobs) is handled by one CTA, its rows staged in the idle stage 0.  For every
+// job the callee receives job(i, valid, row, kind, w, p, warp_rows): row points
+// at the job's m efficiencies in shared memory, warp_rows at the 32 x
 // m block of rows the calling warp owns (tile rows or idle stage-0 space),
 // which the callee may overwrite once it has read its own row.  All 256
 // threads call job for every tile, valid or not, so warp collectives work.
@@ -641,7 +721,10 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
         const long long i = tail0 + tid;
         const bool valid = i < n;
         float *scratch = reinterpret_cast<float *>(smem);  // stage 0 is idle now
-        job(i, valid, nullptr, valid ? static_cast<int>(Kind[i]) : RA_U_LINCAP,
+        float *own = scratch + tid * m;                     // the tail's rows, staged like a tile
+        for (int k = 0; k < m; ++k) own[k] = valid ? A[i * m + k] : 0.0f;
+        __syncthreads();
+        job(i, valid, own, valid ? static_cast<int>(Kind[i]) : RA_U_LINCAP,
             valid ? W[i] : 1.0f, valid ? Par[i] : 0.0f, scratch + warp * 32 * m);
     }
     return true;
@@ -683,12 +766,13 @@ __device__ __forceinline__ unsigned char *align128(unsigned char *p)
 
 // Main streaming kernel, FP32 per-job arithmetic (Sections 3 and 4).
 template <int MT, bool CAP, bool LAG, bool REC>
-__global__ void __launch_bounds__(kTile, 2)
+__global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     dual_tma_kernel(DualParams P, int stages, long long num_full)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
-    __shared__ float lam_s[RA_MAX_M];
+    __shared__ __align__(16) float lam_s[RA_MAX_M];
+    __shared__ __align__(16) float mu_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
     __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
@@ -715,6 +799,7 @@ __global__ void __launch_bounds__(kTile, 2)
 
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<float>(P.lam[tid]) : Fn<float>::inf();
+        mu_s[tid] = inv_price<float>(lam_s[tid]);
         s_s[tid] = (LAG && lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
         sl_s[tid] = (LAG && lag && tid < m)
                         ? static_cast<float>((P.s_lin_prev ? P.s_lin_prev : P.s_prev)[tid])
@@ -740,18 +825,22 @@ __global__ void __launch_bounds__(kTile, 2)
             tp = lbt_prev[i];
             jp = lbj_prev[i];
         }
-        float a[MT];
-        load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
         JobSol<float> s;
         s.cP = s.cQ = -1;
         s.xP = s.xQ = 0.f;
         if (valid) {
-            auto fetch = [&](int k, float &av, float &lv) {
-                const int c = colof<MT>(k, rot);
-                av = row != nullptr ? row[c] : __ldg(&P.A[i * m + c]);
-                lv = lam_s[c];
-            };
-            solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
+            if constexpr (CAP) {
+                float a[MT];
+                load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
+                auto fetch = [&](int k, float &av, float &lv) {
+                    const int c = colof<MT>(k, rot);
+                    av = row[c];
+                    lv = lam_s[c];
+                };
+                solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
+            } else {
+                solve_job_nc<MT>(row, mu_s, lam_s, m, grouped, rot, kind, w, p, s);
+            }
             hsum.add(s.h);
             uxsum.add(s.u);
             if (LAG && lag) {
@@ -1452,11 +1541,13 @@ __global__ void records_kernel(const float2 *lbt, const uchar2 *lbj, long long n
 
 // ---------------------------------------------------------------------------- dispatch
 
+// Ring stages for a shared-memory budget per CTA: 106 KB lets two CTAs share
+// an SM (the capped kernels, 128 registers), 70 KB three (the uncapped ones).
 template <int MT>
-int mt_stages(int m)
+int mt_stages(int m, size_t budget = 106 * 1024)
 {
     const size_t sb = StageLayout<MT>::bytes(m);
-    int s = static_cast<int>((106 * 1024) / sb);  // two CTAs per SM fit in 228 KB
+    int s = static_cast<int>(budget / sb);
     if (s > kMaxStages) s = kMaxStages;
     if (s < 2) s = 2;
     return s;
@@ -1531,11 +1622,13 @@ cudaError_t configure_dual(ra_problem *p)
 {
     const int m = p->m;
     p->mt = m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
+    const bool cap = !(p->flags & RA_NO_JOB_CAP);
+    const size_t budget = cap ? 106 * 1024 : 70 * 1024;
     switch (p->mt) {
-    case 4: p->stages = mt_stages<4>(m); break;
-    case 8: p->stages = mt_stages<8>(m); break;
-    case 16: p->stages = mt_stages<16>(m); break;
-    default: p->stages = mt_stages<32>(m); break;
+    case 4: p->stages = mt_stages<4>(m, budget); break;
+    case 8: p->stages = mt_stages<8>(m, budget); break;
+    case 16: p->stages = mt_stages<16>(m, budget); break;
+    default: p->stages = mt_stages<32>(m, budget); break;
     }
     const size_t sb = StageLayout<4>::bytes(m);  // layout does not depend on MT
     p->smem_dual = p->stages * sb + 128;
@@ -1560,10 +1653,14 @@ cudaError_t configure_dual(ra_problem *p)
     int per_sm = 1;
     const void *fn = nullptr;
     switch (p->mt) {
-    case 4: fn = reinterpret_cast<const void *>(dual_tma_kernel<4, true, true, true>); break;
-    case 8: fn = reinterpret_cast<const void *>(dual_tma_kernel<8, true, true, true>); break;
-    case 16: fn = reinterpret_cast<const void *>(dual_tma_kernel<16, true, true, true>); break;
-    default: fn = reinterpret_cast<const void *>(dual_tma_kernel<32, true, true, true>); break;
+    case 4: fn = cap ? reinterpret_cast<const void *>(dual_tma_kernel<4, true, true, true>)
+                     : reinterpret_cast<const void *>(dual_tma_kernel<4, false, true, true>); break;
+    case 8: fn = cap ? reinterpret_cast<const void *>(dual_tma_kernel<8, true, true, true>)
+                     : reinterpret_cast<const void *>(dual_tma_kernel<8, false, true, true>); break;
+    case 16: fn = cap ? reinterpret_cast<const void *>(dual_tma_kernel<16, true, true, true>)
+                      : reinterpret_cast<const void *>(dual_tma_kernel<16, false, true, true>); break;
+    default: fn = cap ? reinterpret_cast<const void *>(dual_tma_kernel<32, true, true, true>)
+                      : reinterpret_cast<const void *>(dual_tma_kernel<32, false, true, true>); break;
     }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, p->smem_dual);
     if (e != cudaSuccess) return e;
