@@ -66,29 +66,35 @@ def price_err(lam, ref):
     return float(np.max(np.abs(lam - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
 
-@pytest.mark.parametrize("make,tol,fp64,prices", [
-    (lambda: W.config_hetero(n=200_000, m=8, seed=3), 1e-6, False, True),
-    (lambda: W.config_large(n=200_000, m=32, seed=3), 1e-6, False, True),
-    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.1), 1e-6, False, True),
-    (lambda: W.config_plain_small(), 1e-9, True, False),
-    (lambda: W.paper_medium(n=200_000, utility="target", seed=1), 1e-6, False, False),
-    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.25), 1e-6, False, False),
+@pytest.mark.parametrize("make,tol,fp64,prices,cap", [
+    (lambda: W.config_hetero(n=200_000, m=8, seed=3), 1e-6, False, True, True),
+    (lambda: W.config_large(n=200_000, m=32, seed=3), 1e-6, False, True, True),
+    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.1), 1e-6, False, True, True),
+    (lambda: W.config_plain_small(), 1e-9, True, False, True),
+    (lambda: W.paper_medium(n=200_000, utility="target", seed=1), 1e-6, False, False, True),
+    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.25), 1e-6, False, False, True),
+    # without the cap: log, power and linear-with-cap jobs (the split column
+    # scaling of the lower bound), FP32 and FP64 job math
+    (lambda: W.config_large(n=150_000, m=32, seed=4), 1e-6, False, False, False),
+    (lambda: W.config_large(n=200_000, m=8, seed=5), 1e-6, True, False, False),
+    (lambda: W.config_hetero(n=150_000, m=16, seed=6), 1e-6, False, False, False),
 ], ids=["hetero-200k-m8", "large-200k-m32", "mixed-100k-m5", "plain-small-fp64",
-        "paper-medium-target", "degenerate-100k-m5"])
-def test_solve_matches_oracle(ra, oracle, make, tol, fp64, prices):
+        "paper-medium-target", "degenerate-100k-m5", "large-150k-m32-nocap",
+        "large-200k-m8-nocap-fp64", "hetero-150k-m16-nocap"])
+def test_solve_matches_oracle(ra, oracle, make, tol, fp64, prices, cap):
     prob = make()
-    P = ra.AllocationProblem.from_numpy(prob, "cuda", fp64_jobmath=fp64)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", fp64_jobmath=fp64, job_cap=cap)
     info = P.solve(tol=tol, max_evals=800)
     assert info["status"] == ra.RA_OK, info
     assert info["rel_gap"] <= tol
-    ref = oracle.solve(prob, tol=min(tol, 1e-8) * 0.1, max_evals=2000)
+    ref = oracle.solve(prob, cap=cap, tol=min(tol, 1e-8) * 0.1, max_evals=2000)
     # the GPU's bounds bracket the oracle's optimum
     slack = 3e-6 if not fp64 else 1e-11
     scale = max(abs(ref.g), 1.0)
     assert info["g"] >= ref.U_lb - slack * scale
     assert info["U_lb"] <= ref.g + slack * scale
     # the oracle certifies the GPU's prices in FP64
-    g, lb, gap = certify(oracle, prob, P)
+    g, lb, gap = certify(oracle, prob, P, cap)
     assert gap <= tol + (3e-6 if not fp64 else 1e-12), (g, lb, gap)
     assert lb >= info["U_lb"] - (3e-6 if not fp64 else 1e-11) * scale   # Jensen, in FP64
     # prices: the dual optimum need not be unique (jobs sitting at kinks make g
