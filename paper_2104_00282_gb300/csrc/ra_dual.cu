@@ -362,15 +362,17 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
     }
 }
 
-// Algorithm 1 without the per-job cap, FP32, for a job whose m efficiencies
-// are at `row` (shared or global memory; 16-byte aligned when grouped).  The
-// cheapest effective price is found while streaming the row in 16-byte
-// chunks (rotated by `rot` as in load_row) against the inverse prices in
-// shared memory, so no per-job register array is held -- the register
-// footprint that lets a third CTA share the SM.  Chains, tie rules and the
-// closed forms are those of solve_job<MT, false, false, float>.
-template <int MT>
-__device__ __forceinline__ void solve_job_nc(const float *row, const float *mu_s, const float *lam_s,
+// Algorithm 1 in FP32 for a job whose m efficiencies are at `row` (shared or
+// global memory; 16-byte aligned when grouped), prices and inverse prices in
+// shared memory.  The cheapest effective price is found while streaming the
+// row in 16-byte chunks (rotated by `rot` as in load_row) against the
+// inverse prices; with the cap, each hull step streams the row and the prices
+// again.  No per-job register array is held -- the register footprint that
+// lets a third CTA share the SM.  Chains, their order, tie rules and the
+// closed forms are those of solve_job<MT, CAP, false, float>, so both give
+// the same bits.
+template <int MT, bool CAP>
+__device__ __forceinline__ void solve_job_sm(const float *row, const float *mu_s, const float *lam_s,
                                              int m, bool grouped, int rot, int kind, float w,
                                              float p, JobSol<float> &s)
 {
@@ -426,20 +428,96 @@ __device__ __forceinline__ void solve_job_nc(const float *row, const float *mu_s
         s.u = s.h;
         return;
     }
-    const float aQ = row[cb], lQ = lam_s[cb];
     s.jstar = cb;
-    const float alpha = lQ / aQ;
-    const float t = topt<float>(kind, w, p, alpha, 0.f, Fn<float>::inf());
+    int cQ = cb, cP = -1;
+    float aQ = row[cb], lQ = lam_s[cb];
+    float aP = 0.f, lP = 0.f;
+    float alpha = lQ / aQ;
+    float t;
+    if (!CAP) {
+        t = topt<float>(kind, w, p, alpha, 0.f, Fn<float>::inf());
+    } else {
+        // A3: walk the lower hull until the segment holds the optimum
+        for (int step = 0; step < MT; ++step) {
+            t = topt<float>(kind, w, p, alpha, aP, aQ);
+            if (t < aQ) break;
+            // next vertex: minimum slope (lam_k - lQ)/(a_k - aQ) over a_k > aQ,
+            // compared division-free, in four independent chains
+            float cdl[4] = {1.f, 1.f, 1.f, 1.f};
+            float cda[4] = {0.f, 0.f, 0.f, 0.f};
+            int ckn[4] = {-1, -1, -1, -1};
+            auto consider = [&](int ch, float ak, float lk, int col) {
+                const float da = ak - aQ, dl = lk - lQ;
+                if (da > 0.f && dl * cda[ch] < cdl[ch] * da) {
+                    cdl[ch] = dl;
+                    cda[ch] = da;
+                    ckn[ch] = col;
+                }
+            };
+            if (grouped) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int q = (c + rot) & (C - 1);
+                    const float4 av = reinterpret_cast<const float4 *>(row)[q];
+                    const float4 lv = reinterpret_cast<const float4 *>(lam_s)[q];
+                    consider(0, av.x, lv.x, 4 * q);
+                    consider(1, av.y, lv.y, 4 * q + 1);
+                    consider(2, av.z, lv.z, 4 * q + 2);
+                    consider(3, av.w, lv.w, 4 * q + 3);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < MT; ++k)
+                    if (k < m) consider(k & 3, row[k], lam_s[k], k);
+            }
+            float bdl = cdl[0], bda = cda[0];
+            int kn = ckn[0];
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                if (ckn[c] < 0) continue;
+                const float lhs = cdl[c] * bda, rhs = bdl * cda[c];
+                if (kn < 0 || lhs < rhs || (lhs == rhs && ckn[c] < kn)) {
+                    bdl = cdl[c];
+                    bda = cda[c];
+                    kn = ckn[c];
+                }
+            }
+            if (kn < 0) {  // aQ = max_j a_j: right end of the domain
+                t = aQ;
+                break;
+            }
+            cP = cQ;
+            aP = aQ;
+            lP = lQ;
+            cQ = kn;
+            aQ = row[kn];
+            lQ = lam_s[kn];
+            alpha = bdl / bda;
+        }
+    }
     s.t = t;
     const float u = util<float>(kind, w, p, t);
     s.u = u;
-    s.h = u - alpha * t;
-    if (kind <= RA_U_POWER)   // interior optimum: see solve_job
+    s.h = u - (lP + alpha * (t - aP));
+    if (!CAP && kind <= RA_U_POWER)   // interior optimum: see solve_job
         s.h = !(alpha > 0.f) ? Fn<float>::inf() : kind == RA_U_LOG ? u - w : (1.f - p) * u;
-    const float xQ = t / aQ;
-    s.cQ = xQ > 0.f ? cb : -1;
+    float xQ, xP;
+    if (CAP) {
+        const float den = aQ - aP;
+        xQ = (t - aP) / den;
+        xP = (cP >= 0) ? (aQ - t) / den : 0.f;
+    } else {
+        xQ = t / aQ;
+        xP = 0.f;
+    }
+    s.cQ = xQ > 0.f ? cQ : -1;
     s.xQ = xQ > 0.f ? xQ : 0.f;
     s.tQ = s.xQ * aQ;
+    if (cP >= 0 && xP > 0.f) {
+        s.cP = cP;
+        s.xP = xP;
+        s.tP = xP * aP;
+    }
 }
 
 // Per-thread running sums of the FP32 path: compensated FP32 (Kahan), error
@@ -806,13 +884,6 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                         : 1.0f;
     }
     __syncthreads();
-    float lam_r[MT], mu_r[MT];
-#pragma unroll
-    for (int k = 0; k < MT; ++k) {
-        const int c = colof<MT>(k, rot);
-        lam_r[k] = lam_s[c];
-        mu_r[k] = inv_price<float>(lam_s[c]);
-    }
 
     KahanF hsum, uxsum, lbsum, racc, rlin;
     auto job = [&](long long i, bool valid, const float *row, int kind, float w, float p,
@@ -829,18 +900,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         s.cP = s.cQ = -1;
         s.xP = s.xQ = 0.f;
         if (valid) {
-            if constexpr (CAP) {
-                float a[MT];
-                load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
-                auto fetch = [&](int k, float &av, float &lv) {
-                    const int c = colof<MT>(k, rot);
-                    av = row[c];
-                    lv = lam_s[c];
-                };
-                solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, p, s);
-            } else {
-                solve_job_nc<MT>(row, mu_s, lam_s, m, grouped, rot, kind, w, p, s);
-            }
+            solve_job_sm<MT, CAP>(row, mu_s, lam_s, m, grouped, rot, kind, w, p, s);
             hsum.add(s.h);
             uxsum.add(s.u);
             if (LAG && lag) {
@@ -1623,7 +1683,7 @@ cudaError_t configure_dual(ra_problem *p)
     const int m = p->m;
     p->mt = m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
     const bool cap = !(p->flags & RA_NO_JOB_CAP);
-    const size_t budget = cap ? 106 * 1024 : 70 * 1024;
+    const size_t budget = cap ? 106 * 1024 : 70 * 1024;   // two / three CTAs per SM
     switch (p->mt) {
     case 4: p->stages = mt_stages<4>(m, budget); break;
     case 8: p->stages = mt_stages<8>(m, budget); break;
