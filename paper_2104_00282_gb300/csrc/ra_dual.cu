@@ -597,6 +597,66 @@ __device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int la
     __syncwarp();
 }
 
+// warp_rsum that also sums the linear-utility jobs' part of each column
+// (lanes flagged by `lin`): the same fixed-order column sums, with a second
+// set of partial sums fed from the rows whose bit is set in the warp's lane
+// mask -- no extra shared-memory traffic.  r is bitwise what warp_rsum gives.
+template <int MT, typename Acc>
+__device__ __forceinline__ void warp_rsum_lin(float *warp_rows, int m, int lane, bool grouped,
+                                              int rot, const JobSol<float> &s, bool lin, Acc &racc,
+                                              Acc &rlin)
+{
+    float *row = warp_rows + lane * m;
+    if (grouped) {
+        constexpr int C = MT / 4;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int q = (c + rot) & (C - 1);
+            reinterpret_cast<float4 *>(row)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        for (int j = 0; j < m; ++j) row[j] = 0.f;
+    }
+    if (s.cP >= 0) row[s.cP] = s.xP;
+    if (s.cQ >= 0) row[s.cQ] = s.xQ;
+    const unsigned lm = __ballot_sync(kFull, lin);
+    __syncwarp();
+    if (grouped) {
+        constexpr int G = 32 / MT;
+        const int c = lane % MT, g = lane / MT;
+        float cs[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            const int r = g + k * G;
+            const float v = warp_rows[r * MT + c];
+            cs[k & 3] += v;
+            cl[k & 3] += ((lm >> r) & 1u) ? v : 0.f;
+        }
+        float t = (cs[0] + cs[1]) + (cs[2] + cs[3]);
+        float tl = (cl[0] + cl[1]) + (cl[2] + cl[3]);
+#pragma unroll
+        for (int off = MT; off < 32; off <<= 1) {
+            t += __shfl_xor_sync(kFull, t, off);
+            tl += __shfl_xor_sync(kFull, tl, off);
+        }
+        if (g == 0) {
+            acc_add(racc, t);
+            acc_add(rlin, tl);
+        }
+    } else if (lane < m) {
+        float cs[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const float v = warp_rows[r * m + lane];
+            cs[r & 3] += v;
+            cl[r & 3] += ((lm >> r) & 1u) ? v : 0.f;
+        }
+        acc_add(racc, (cs[0] + cs[1]) + (cs[2] + cs[3]));
+        acc_add(rlin, (cl[0] + cl[1]) + (cl[2] + cl[3]));
+    }
+    __syncwarp();
+}
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
@@ -621,30 +681,6 @@ __device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real>
         if (lane == c) acc_add(acc, v);
         mask &= ~__ballot_sync(kFull, mine);
     }
-}
-
-// The same through shared memory: each linear lane posts (column, x) to the
-// warp's scratch (64 floats the warp owns), then lane c adds up the entries
-// for column c in lane order with four independent chains -- no chain of
-// dependent shuffles.  Warps without a linear job skip it.
-template <typename Acc>
-__device__ __forceinline__ void warp_rlin_smem(float *scratch, int m, bool lin, int lane,
-                                               const JobSol<float> &s, Acc &acc)
-{
-    const bool on = lin && s.cQ >= 0;
-    if (__ballot_sync(kFull, on) == 0) return;
-    float2 *post = reinterpret_cast<float2 *>(scratch);
-    __syncwarp();
-    post[lane] = make_float2(__int_as_float(on ? s.cQ : -1), on ? s.xQ : 0.0f);
-    __syncwarp();
-    float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        const float2 e = post[r];
-        if (__float_as_int(e.x) == lane) cs[r & 3] += e.y;
-    }
-    if (lane < m) acc_add(acc, (cs[0] + cs[1]) + (cs[2] + cs[3]));
-    __syncwarp();
 }
 
 // Block stage + grid stage: per-thread FP64 values -> per-block partials
@@ -915,11 +951,11 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
             }
         }
-        warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, s, racc);
-        if (!CAP && REC) {  // 64 floats of the warp's rows when m >= 2, else shuffles
-            if (m >= 2) warp_rlin_smem<KahanF>(warp_rows, m, valid && kind >= RA_U_LINCAP, lane, s, rlin);
-            else warp_rlin<float, KahanF>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
-        }
+        if (!CAP && REC)
+            warp_rsum_lin<MT, KahanF>(warp_rows, m, lane, grouped, rot, s,
+                                      valid && kind >= RA_U_LINCAP, racc, rlin);
+        else
+            warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, s, racc);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job);
@@ -1203,12 +1239,15 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
             lbt_out[i] = make_float2(sol.tP, sol.tQ);
             lbj_out[i] = make_uchar2(sol.cP >= 0 ? sol.cP : 255, sol.cQ >= 0 ? sol.cQ : 255);
         }
-        if (full) warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, sol, racc);
-        else warp_rsum_shfl<float, KahanF>(m, lane, sol, racc);
-        if (!CAP) {
-            if (full && m >= 2)
-                warp_rlin_smem<KahanF>(warp_rows, m, valid && kind >= RA_U_LINCAP, lane, sol, rlin);
-            else warp_rlin<float, KahanF>(valid && kind >= RA_U_LINCAP, lane, sol, rlin);
+        if (full) {
+            if (!CAP)
+                warp_rsum_lin<MT, KahanF>(warp_rows, m, lane, grouped, rot, sol,
+                                          valid && kind >= RA_U_LINCAP, racc, rlin);
+            else
+                warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, sol, racc);
+        } else {
+            warp_rsum_shfl<float, KahanF>(m, lane, sol, racc);
+            if (!CAP) warp_rlin<float, KahanF>(valid && kind >= RA_U_LINCAP, lane, sol, rlin);
         }
         __syncthreads();  // stage consumed
         if (full) {
