@@ -311,8 +311,8 @@ def run_gpu(args):
                          f"(R scaled) took {dt:.0f} ms, {evals} evaluations, gap {gap:.2e}; "
                          f"scaled x{N_JOBS / sample_n:g} to n=1e7 (linear in n)"}
     evals = [i["evals"] for i in infos]
-    # per solve: initialisation + setup, then per evaluation: dual, master LP, update
-    launches = sum(2 + 3 * e for e in evals)
+    # per solve: initialisation + setup, then per evaluation: dual pass, solver step
+    launches = sum(2 + 2 * e for e in evals)
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",

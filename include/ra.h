@@ -129,6 +129,8 @@ typedef struct {
     double lam_floor;     /* lower bound on prices; <0 selects 0 (cap) / 1e-12 max(lambda^1)    */
     int32_t master_lb;    /* 1 = also bound U* by the master LP over evaluated allocations      */
     int32_t pad_;
+    double init_step;     /* length of the first price step (and of a restarted gradient step)
+                             as a fraction of |lambda|; default 0.05, smaller from a close start */
 } ra_solve_opts;
 
 typedef struct {
@@ -142,7 +144,8 @@ typedef struct {
     double gap_per_job;   /* (g - U_lb) / n, the paper's absolute measure (Algorithm 2)         */
 } ra_solve_info;
 
-/* Fill *opts with the defaults (tol 1e-6, 500 evals, memory 10, L-BFGS, graph). */
+/* Fill *opts with the defaults (tol 1e-6, 500 evals, memory 10, L-BFGS, graph,
+ * first step 0.05 |lambda|). */
 void ra_solve_opts_default(ra_solve_opts *opts);
 
 /*
@@ -353,6 +356,9 @@ ra_status ra_batch_features(ra_batch *b, float *feats);
  * and lambda0 (device, m FP64) receives lambda_w when g(lambda_w) is finite
  * and g(lambda_w) <= g(lambda_c), else lambda_c.  used_warm (host, or NULL
  * to stay asynchronous) receives 1 when the network's prices were kept.
+ * The statistics and the network run on a stream of the problem's own
+ * (created on the first call) joined back to the problem's stream, beside
+ * the cold start's pass; both g values come from one pass over the data.
  */
 ra_status ra_warmstart_prices(ra_problem *prob, ra_mlp *net, double *lambda0, int32_t *used_warm);
 

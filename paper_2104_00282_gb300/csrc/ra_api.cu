@@ -100,6 +100,7 @@ void ra_solve_opts_default(ra_solve_opts *o)
     o->lam_floor = -1.0;
     o->master_lb = 1;
     o->pad_ = 0;
+    o->init_step = 0.05;
 }
 
 ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t *kind,
@@ -195,6 +196,9 @@ void ra_problem_destroy(ra_problem *p)
     cudaFree(p->graph_flag);
     cudaFree(p->tmp);
     cudaFree(p->warm);
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
     delete p;
 }
 
@@ -531,8 +535,9 @@ constexpr size_t kWsY = kWsFeats + sizeof(float) * RA_MAX_M * RA_MLP_IN;
 constexpr size_t kWsLamW = kWsY + sizeof(float) * RA_MAX_M;
 constexpr size_t kWsLamC = kWsLamW + sizeof(double) * RA_MAX_M;
 constexpr size_t kWsUsed = kWsLamC + sizeof(double) * RA_MAX_M;
+constexpr size_t kWsG2 = kWsUsed + 16;                           // 2 doubles
 static_assert(kWsStats + sizeof(float) * RA_MAX_M * RA_MLP_STATS <= kWsFeats, "scratch layout");
-static_assert(kWsUsed + 16 <= ra::kWarmBytes, "scratch layout");
+static_assert(kWsG2 + 16 <= ra::kWarmBytes, "scratch layout");
 
 ra::FeatProblem feat_of(const ra_problem *p)
 {
@@ -666,29 +671,29 @@ ra_status ra_warmstart_prices(ra_problem *p, ra_mlp *net, double *lambda0, int32
     double *lam_w = reinterpret_cast<double *>(p->warm + kWsLamW);
     double *lam_c = reinterpret_cast<double *>(p->warm + kWsLamC);
     int32_t *used = reinterpret_cast<int32_t *>(p->warm + kWsUsed);
-    cudaError_t e = ra::launch_features(nullptr, feat_of(p), 1, p->m, stats, feats, s);
-    if (e == cudaSuccess) e = ra::mlp_forward(net, feats, p->m, y, s);
-    if (e == cudaSuccess) e = ra::launch_exp_prices(p->m, y, lam_w, s);
-    if (e == cudaSuccess) e = ra::launch_init(p, lam_c, s);
-    if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start launch: %s", cudaGetErrorString(e));
-    // g at both candidates: one dual pass each (results in the two EvalOut slots)
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        ra::DualParams dp{};
-        dp.A = p->A;
-        dp.kind = p->kind;
-        dp.w = p->w;
-        dp.param = p->param;
-        dp.R = p->R;
-        dp.n = p->n;
-        dp.m = p->m;
-        dp.lam = k == 0 ? lam_w : lam_c;
-        dp.partials = p->partials;
-        dp.ticket = p->ticket;
-        dp.status = p->status;
-        dp.out = p->ev + k;
-        e = ra::launch_dual(p, dp, s);
+    // the statistics and the network run on a side stream while the cold
+    // start's pass over A runs on the problem's stream (the two are
+    // independent; the side stream is created on the first call)
+    cudaError_t e = cudaSuccess;
+    if (!p->side) {
+        e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start stream: %s", cudaGetErrorString(e));
     }
-    if (e == cudaSuccess) e = ra::launch_choose(p->m, lam_w, lam_c, p->ev, p->ev + 1, lambda0, used, s);
+    e = cudaEventRecord(p->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
+    if (e == cudaSuccess) e = ra::launch_features(nullptr, feat_of(p), 1, p->m, stats, feats, p->side);
+    if (e == cudaSuccess) e = ra::mlp_forward(net, feats, p->m, y, p->side);
+    if (e == cudaSuccess) e = ra::launch_exp_prices(p->m, y, lam_w, p->side);
+    if (e == cudaSuccess) e = cudaEventRecord(p->join, p->side);
+    if (e == cudaSuccess) e = ra::launch_init(p, lam_c, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join, 0);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start launch: %s", cudaGetErrorString(e));
+    // g at both candidates in one pass over the data
+    double *g2 = reinterpret_cast<double *>(p->warm + kWsG2);
+    if (e == cudaSuccess) e = ra::launch_dual_g2(p, lam_w, lam_c, g2, s);
+    if (e == cudaSuccess) e = ra::launch_choose(p->m, lam_w, lam_c, g2, lambda0, used, s);
     if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start evaluation: %s", cudaGetErrorString(e));
     if (used_warm) {
         e = cudaMemcpyAsync(used_warm, used, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

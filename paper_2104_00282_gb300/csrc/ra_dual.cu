@@ -1029,6 +1029,58 @@ __global__ void __launch_bounds__(kTile, 2)
         if (tid < m) lam1[tid] = red[0][4 + tid] / static_cast<double>(n);
 }
 
+// Dual values g(lambda_a) and g(lambda_b) in one pass over the data (the
+// two start points a warm start chooses between): each job is solved at both
+// price vectors from the same staged row; only the two sums of h are
+// reduced.  g_out[0], g_out[1] receive lambda^T R + sum_i h_i for each.
+template <int MT, bool CAP>
+__global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
+    dual_g2_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
+                   const double *R, long long n, int m, const double *lam_a, const double *lam_b,
+                   int stages, long long num_full, double *partials, unsigned *ticket, int *status,
+                   double *g_out)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t bars[kMaxStages];
+    __shared__ __align__(16) float la_s[RA_MAX_M], ma_s[RA_MAX_M], lb_s[RA_MAX_M], mb_s[RA_MAX_M];
+    __shared__ double red[kWarps][kPartW];
+    const int tid = threadIdx.x;
+    const bool grouped = (m == MT);
+    constexpr int C = MT / 4;
+    const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
+    if (tid < RA_MAX_M) {
+        la_s[tid] = tid < m ? static_cast<float>(lam_a[tid]) : Fn<float>::inf();
+        lb_s[tid] = tid < m ? static_cast<float>(lam_b[tid]) : Fn<float>::inf();
+        ma_s[tid] = inv_price<float>(la_s[tid]);
+        mb_s[tid] = inv_price<float>(lb_s[tid]);
+    }
+    __syncthreads();
+    KahanF ha, hb;
+    auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
+                   float *warp_rows) {
+        (void)i;
+        (void)warp_rows;
+        if (!valid) return;
+        JobSol<float> sa, sb;
+        solve_job_sm<MT, CAP>(row, ma_s, la_s, m, grouped, rot, kd, wi, pi, sa);
+        solve_job_sm<MT, CAP>(row, mb_s, lb_s, m, grouped, rot, kd, wi, pi, sb);
+        ha.add(sa.h);
+        hb.add(sb.h);
+    };
+    unsigned char *smem = align128<MT>(smem_dyn);
+    stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
+    if (grid_reduce(ha.value(), hb.value(), 0.0, 0.0, 0.0, 0, false, true, partials, ticket, red) &&
+        tid == 0) {
+        double ra = 0.0, rb = 0.0;
+        for (int j = 0; j < m; ++j) {
+            ra += lam_a[j] * R[j];
+            rb += lam_b[j] * R[j];
+        }
+        g_out[0] = ra + red[0][0];
+        g_out[1] = rb + red[0][1];
+    }
+}
+
 // ---------------------------------------------------------------------------- batched kernels
 
 // Column sums of a warp's x block without shared memory: column c is summed
@@ -1741,6 +1793,20 @@ cudaError_t configure_dual(ra_problem *p)
     RA_IATTR(16)
     RA_IATTR(32)
 #undef RA_IATTR
+#define RA_GATTR(MT)                                                                               \
+    if ((e = cudaFuncSetAttribute(dual_g2_kernel<MT, true>,                                       \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+        cudaSuccess)                                                                               \
+        return e;                                                                                  \
+    if ((e = cudaFuncSetAttribute(dual_g2_kernel<MT, false>,                                      \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+        cudaSuccess)                                                                               \
+        return e;
+    RA_GATTR(4)
+    RA_GATTR(8)
+    RA_GATTR(16)
+    RA_GATTR(32)
+#undef RA_GATTR
     if ((e = set_attrs_mt<4, true>()) != cudaSuccess) return e;
     if ((e = set_attrs_mt<8, true>()) != cudaSuccess) return e;
     if ((e = set_attrs_mt<16, true>()) != cudaSuccess) return e;
@@ -1796,6 +1862,32 @@ cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaSt
     long long blocks = (p->n + kTile - 1) / kTile;
     if (blocks > p->grid_aux) blocks = p->grid_aux;
     records_kernel<<<static_cast<int>(blocks), kTile, 0, s>>>(p->lbt[0], p->lbj[0], p->n, j12, t12);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
+                           double *g_out, cudaStream_t s)
+{
+    const long long num_full = p->n / kTile;
+    int grid = p->grid_dual;
+    if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
+    const bool cap = !(p->flags & RA_NO_JOB_CAP);
+#define RA_G2(MT)                                                                                  \
+    if (cap)                                                                                       \
+        dual_g2_kernel<MT, true><<<grid, kTile, p->smem_dual, s>>>(                                \
+            p->A, p->kind, p->w, p->param, p->R, p->n, p->m, lam_a, lam_b, p->stages, num_full,    \
+            p->partials, p->ticket + 3, p->status, g_out);                                         \
+    else                                                                                           \
+        dual_g2_kernel<MT, false><<<grid, kTile, p->smem_dual, s>>>(                               \
+            p->A, p->kind, p->w, p->param, p->R, p->n, p->m, lam_a, lam_b, p->stages, num_full,    \
+            p->partials, p->ticket + 3, p->status, g_out);
+    switch (p->mt) {
+    case 4: RA_G2(4) break;
+    case 8: RA_G2(8) break;
+    case 16: RA_G2(16) break;
+    default: RA_G2(32) break;
+    }
+#undef RA_G2
     return cudaGetLastError();
 }
 

@@ -90,6 +90,7 @@ struct SolverState {
     double U_best;
     double gap;
     double sg_a0;         // subgradient step scale
+    double init_step;     // first step length / |lambda|
     double g_bt;          // best trial value of the current line search
     double last_step;     // norm of the last accepted price step
     int32_t sg_pending;   // the evaluation in flight is a fallback subgradient step
@@ -169,6 +170,8 @@ struct ra_problem {
     int32_t *graph_flag;
     double *tmp;         // small scratch (m + 8 doubles)
     unsigned char *warm; // warm-start scratch (kWarmBytes)
+    cudaStream_t side;   // warm start: statistics and network beside the cold-start pass
+    cudaEvent_t fork, join;
 };
 
 namespace ra {
@@ -243,6 +246,8 @@ cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t 
 cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
                                const EvalOut *src, double *U_lb, cudaStream_t s);
 cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s);
+cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
+                           double *g_out, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);
 cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jstar, int32_t *j12,
                            float *x12, float *t, float *X, double *U, uint8_t *near_tie,
@@ -274,8 +279,8 @@ cudaError_t mlp_forward(ra_mlp *net, const float *X, int rows, float *y_out, cud
 cudaError_t mlp_train_step(ra_mlp *net, const float *X, const float *target, int rows, float lr,
                            float *loss, cudaStream_t s);
 cudaError_t launch_exp_prices(int m, const float *y, double *lam, cudaStream_t s);
-cudaError_t launch_choose(int m, const double *lam_w, const double *lam_c, const EvalOut *ev_w,
-                          const EvalOut *ev_c, double *lam0, int32_t *used, cudaStream_t s);
+cudaError_t launch_choose(int m, const double *lam_w, const double *lam_c, const double *g2,
+                          double *lam0, int32_t *used, cudaStream_t s);
 
 // Solver (ra_solve.cu).
 ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, double *lambda_out,

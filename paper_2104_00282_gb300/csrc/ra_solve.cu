@@ -54,7 +54,7 @@ __device__ __forceinline__ unsigned long long device_ns()
 // NULL when the initial prices have already been written to st->lam_trial.
 __device__ void setup_one(SolverState *st, const double *lam0, const double *R, int m, double tol,
                           int max_evals, int mem, int update, double lam_floor, int cap,
-                          int use_master, int32_t *pingpong, int32_t *lag_on)
+                          int use_master, double init_step, int32_t *pingpong, int32_t *lag_on)
 {
     const int j = threadIdx.x;
     double l = 0.0;
@@ -90,7 +90,8 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
         st->gap = __longlong_as_double(0x7ff0000000000000ll);
         st->step = 1.0;
         st->g_bt = __longlong_as_double(0x7ff0000000000000ll);
-        st->last_step = 0.05 * lmax;
+        st->last_step = init_step * lmax;
+        st->init_step = init_step;
         st->sg_pending = 0;
         st->cand_count = 0;
         st->cand_head = 0;
@@ -108,11 +109,11 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
 
 __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const double *R, int m,
                                     double tol, int max_evals, int mem, int update,
-                                    double lam_floor, int cap, int use_master, int32_t *pingpong,
-                                    int32_t *lag_on)
+                                    double lam_floor, int cap, int use_master, double init_step,
+                                    int32_t *pingpong, int32_t *lag_on)
 {
-    setup_one(st, lam0, R, m, tol, max_evals, mem, update, lam_floor, cap, use_master, pingpong,
-              lag_on);
+    setup_one(st, lam0, R, m, tol, max_evals, mem, update, lam_floor, cap, use_master, init_step,
+              pingpong, lag_on);
 }
 
 // Batched setup: block p sets up problem p; its starting prices are
@@ -120,11 +121,11 @@ __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const d
 __global__ void batch_setup_kernel(SolverState *st, const BatchProblem *probs, const double *lam0,
                                    const long long *lam_off, double tol, int max_evals, int mem,
                                    int update, double lam_floor, int cap, int use_master,
-                                   int32_t *pingpong, int32_t *lag_on)
+                                   double init_step, int32_t *pingpong, int32_t *lag_on)
 {
     const int p = blockIdx.x;
     setup_one(st + p, lam0 + lam_off[p], probs[p].R, probs[p].m, tol, max_evals, mem, update,
-              lam_floor, cap, use_master, pingpong + p, lag_on + p);
+              lam_floor, cap, use_master, init_step, pingpong + p, lag_on + p);
 }
 
 // Graph condition of the batched loop: continue while any problem iterates.
@@ -170,7 +171,7 @@ __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
         gamma = wsum(sj * yj) / fmax(wsum(yj * yj), 1e-300);
     } else {
         const double ln = sqrt(wsum(l * l)), qn = sqrt(wsum(fixed ? 0.0 : q * q));
-        gamma = qn > 0.0 ? 0.05 * fmax(ln, 1e-300) / qn : 0.0;
+        gamma = qn > 0.0 ? st->init_step * fmax(ln, 1e-300) / qn : 0.0;
     }
     v *= gamma;
     for (int c = cnt - 1; c >= 0; --c) {  // oldest first
@@ -184,7 +185,7 @@ __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
     // not a descent direction: drop the memory and take a scaled gradient step
     if (wsum(d * (active ? q : 0.0)) >= 0.0) {
         const double ln = sqrt(wsum(l * l)), qn = sqrt(wsum(fixed ? 0.0 : q * q));
-        const double g0 = qn > 0.0 ? 0.05 * fmax(ln, 1e-300) / qn : 0.0;
+        const double g0 = qn > 0.0 ? st->init_step * fmax(ln, 1e-300) / qn : 0.0;
         d = fixed ? 0.0 : -g0 * q;
         if (j == 0) {
             st->mem_count = 0;
@@ -866,6 +867,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
     if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
     if (!(opts.tol_rel >= 0.0)) return fail(RA_EINVAL, "tol_rel must be >= 0");
+    if (!(opts.init_step > 0.0)) return fail(RA_EINVAL, "init_step must be > 0");
     if (!lambda_out) return fail(RA_EINVAL, "lambda_out is NULL");
     cudaStream_t s = p->stream;
     cudaError_t e;
@@ -882,7 +884,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     }
     solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, p->m, opts.tol_rel, opts.max_evals,
                                          opts.lbfgs_mem, opts.update, opts.lam_floor, cap,
-                                         opts.master_lb, pingpong, lag_on);
+                                         opts.master_lb, opts.init_step, pingpong, lag_on);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
@@ -1024,6 +1026,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
         return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
     if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
     if (!(opts.tol_rel >= 0.0)) return fail(RA_EINVAL, "tol_rel must be >= 0");
+    if (!(opts.init_step > 0.0)) return fail(RA_EINVAL, "init_step must be > 0");
     if (!lambda_out || !infos) return fail(RA_EINVAL, "lambda_out and infos must not be NULL");
     cudaStream_t s = b->stream;
     cudaError_t e;
@@ -1066,7 +1069,8 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
     }
     batch_setup_kernel<<<P, 32, 0, s>>>(b->st, b->probs, lam0, b->lam_off, opts.tol_rel,
                                         opts.max_evals, opts.lbfgs_mem, opts.update, opts.lam_floor,
-                                        cap, opts.master_lb, b->pingpong, b->lag_on);
+                                        cap, opts.master_lb, opts.init_step, b->pingpong,
+                                        b->lag_on);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "batched setup launch: %s", cudaGetErrorString(e));
     if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -49,12 +49,13 @@ __device__ __forceinline__ float fkey_inv(unsigned k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Statistics of resource blockIdx.x of problem blockIdx.y: the 8 quantiles of
+// Statistics of resource blockIdx.x < m of problem blockIdx.y: the 8 quantiles of
 // A[:, j] over the sample (order statistics of rank floor((2l+1) S / 16),
 // selected exactly by a radix select over the float's order-preserving key,
 // 8 bits a pass, all 8 ranks at once: integer bin counts, so the selection
-// does not depend on thread timing), log(R_j / n), the fractions of log,
-// power and linear utilities and the mean of log w over the sample.
+// does not depend on thread timing) and log(R_j / n); CTA m of the problem
+// adds the fractions of log, power and linear utilities and the mean of log w
+// over the sample to every resource's row.
 __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, FeatProblem one,
                                                      float *stats)
 {
@@ -65,30 +66,56 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
     __shared__ unsigned rank[kQuant];   // rank within the keys matching pref
     const FeatProblem P = probs ? probs[blockIdx.y] : one;
     const int j = blockIdx.x;
-    if (j >= P.m) return;
+    if (j > P.m) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = P.n;
     const int S = n < kSampleMax ? static_cast<int>(n) : kSampleMax;
-    for (int k = tid; k < S; k += blockDim.x) key[k] = fkey(P.A[sample_row(k, n, S) * P.m + j]);
-    double c_log = 0.0, c_pow = 0.0, s_lw = 0.0;
-    for (int k = tid; k < S; k += blockDim.x) {
-        const long long row = sample_row(k, n, S);
-        const int kd = P.kind[row];
-        c_log += kd == RA_U_LOG;
-        c_pow += kd == RA_U_POWER;
-        s_lw += static_cast<double>(logf(fmaxf(P.w[row], 1e-30f)));
-    }
+    if (j == P.m) {
+        // the statistics every resource shares (utility mix, mean log w), once
+        // per problem: integer counts and compensated FP32 sums (the FP64
+        // pipe is slow on this GPU), FP64 across warps in a fixed order
+        int cl = 0, cp = 0;
+        float sw = 0.f, cw = 0.f;
+        for (int k = tid; k < S; k += blockDim.x) {
+            const long long row = sample_row(k, n, S);
+            const int kd = P.kind[row];
+            cl += kd == RA_U_LOG;
+            cp += kd == RA_U_POWER;
+            const float y = logf(fmaxf(P.w[row], 1e-30f)) - cw;
+            const float t = sw + y;
+            cw = (t - sw) - y;
+            sw = t;
+        }
+        cl = __reduce_add_sync(0xffffffffu, cl);
+        cp = __reduce_add_sync(0xffffffffu, cp);
+        double swd = static_cast<double>(sw) - static_cast<double>(cw);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        c_log += __shfl_xor_sync(0xffffffffu, c_log, off);
-        c_pow += __shfl_xor_sync(0xffffffffu, c_pow, off);
-        s_lw += __shfl_xor_sync(0xffffffffu, s_lw, off);
+        for (int off = 16; off > 0; off >>= 1) swd += __shfl_xor_sync(0xffffffffu, swd, off);
+        if (lane == 0) {
+            red[warp][0] = cl;
+            red[warp][1] = cp;
+            red[warp][2] = swd;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0, c = 0.0;
+            const int nw = (blockDim.x + 31) / 32;
+            for (int w2 = 0; w2 < nw; ++w2) {
+                a += red[w2][0];
+                b += red[w2][1];
+                c += red[w2][2];
+            }
+            for (int jj = 0; jj < P.m; ++jj) {
+                float *o2 = stats + (P.row0 + jj) * kFeatRes;
+                o2[9] = static_cast<float>(a / S);
+                o2[10] = static_cast<float>(b / S);
+                o2[11] = static_cast<float>((S - a - b) / S);
+                o2[12] = static_cast<float>(c / S);
+            }
+        }
+        return;
     }
-    if (lane == 0) {
-        red[warp][0] = c_log;
-        red[warp][1] = c_pow;
-        red[warp][2] = s_lw;
-    }
+    for (int k = tid; k < S; k += blockDim.x) key[k] = fkey(P.A[sample_row(k, n, S) * P.m + j]);
     if (tid < kQuant) {
         pref[tid] = 0u;
         rank[tid] = static_cast<unsigned>(((2 * tid + 1) * S) / 16);
@@ -97,15 +124,21 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
         const int shift = 24 - 8 * pass;
         for (int e = tid; e < kQuant * 256; e += blockDim.x) (&hist[0][0])[e] = 0u;
         __syncthreads();
-        for (int k = tid; k < S; k += blockDim.x) {
-            const unsigned kv = key[k];
+        // first pass: warp-aggregated counts, the lanes holding the same bin
+        // add once (a column's values share few exponents, so per-key atomics
+        // would pile onto a handful of bins)
+        const int kend = (S + 31) & ~31;
+        for (int k = tid; k < kend; k += blockDim.x) {
+            const bool in = k < S;
+            const unsigned kv = in ? key[k] : 0u;
             const unsigned bin = (kv >> shift) & 255u;
-            if (pass == 0) {
-                atomicAdd(&hist[0][bin], 1u);   // the same histogram serves every rank
-            } else {
+            if (pass == 0) {   // the same histogram serves every rank
+                const unsigned grp = __match_any_sync(0xffffffffu, in ? bin : 0xffffffffu);
+                if (in && (__ffs(grp) - 1) == lane) atomicAdd(&hist[0][bin], __popc(grp));
+            } else {   // few keys still match a rank's prefix: plain atomics
 #pragma unroll
                 for (int l = 0; l < kQuant; ++l)
-                    if (((kv ^ pref[l]) >> (shift + 8)) == 0u) atomicAdd(&hist[l][bin], 1u);
+                    if (in && ((kv ^ pref[l]) >> (shift + 8)) == 0u) atomicAdd(&hist[l][bin], 1u);
             }
         }
         __syncthreads();
@@ -141,19 +174,6 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
     float *out = stats + (P.row0 + j) * kFeatRes;
     if (tid < kQuant) out[tid] = logf(fmaxf(fkey_inv(pref[tid]), 1e-30f));
     if (tid == kQuant) out[8] = static_cast<float>(log(fmax(P.R[j] / static_cast<double>(n), 1e-30)));
-    if (tid == kQuant + 1) {
-        double cl = 0.0, cp = 0.0, sl = 0.0;
-        const int nw = (blockDim.x + 31) / 32;
-        for (int w2 = 0; w2 < nw; ++w2) {
-            cl += red[w2][0];
-            cp += red[w2][1];
-            sl += red[w2][2];
-        }
-        out[9] = static_cast<float>(cl / S);
-        out[10] = static_cast<float>(cp / S);
-        out[11] = static_cast<float>((S - cl - cp) / S);
-        out[12] = static_cast<float>(sl / S);
-    }
 }
 
 // Network input of every resource of problem blockIdx.x: its statistics,
@@ -381,10 +401,10 @@ __global__ void exp_prices_kernel(int m, const float *y, double *lam)
 
 // Start prices: the network's when their dual value is finite and not larger
 // than that of the cold start (the fallback keeps Eq. e-initialization).
-__global__ void choose_kernel(int m, const double *lam_w, const double *lam_c, const EvalOut *ev_w,
-                              const EvalOut *ev_c, double *lam0, int32_t *used)
+__global__ void choose_kernel(int m, const double *lam_w, const double *lam_c, const double *g2,
+                              double *lam0, int32_t *used)
 {
-    const bool warm = isfinite(ev_w->g) && !(ev_w->g > ev_c->g);
+    const bool warm = isfinite(g2[0]) && !(g2[0] > g2[1]);
     const int j = threadIdx.x;
     if (j < m) lam0[j] = warm ? lam_w[j] : lam_c[j];
     if (j == 0) *used = warm ? 1 : 0;
@@ -408,7 +428,7 @@ cudaError_t launch_features(const FeatProblem *probs, const FeatProblem &one, in
     cudaError_t e = cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSampleMax * 4);
     if (e != cudaSuccess) return e;
-    stats_kernel<<<dim3(m_max, P), 1024, kSampleMax * 4, s>>>(probs, one, stats);
+    stats_kernel<<<dim3(m_max + 1, P), 1024, kSampleMax * 4, s>>>(probs, one, stats);
     features_kernel<<<P, 256, 0, s>>>(probs, one, stats, feats);
     return cudaGetLastError();
 }
@@ -504,10 +524,10 @@ cudaError_t launch_exp_prices(int m, const float *y, double *lam, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_choose(int m, const double *lam_w, const double *lam_c, const EvalOut *ev_w,
-                          const EvalOut *ev_c, double *lam0, int32_t *used, cudaStream_t s)
+cudaError_t launch_choose(int m, const double *lam_w, const double *lam_c, const double *g2,
+                          double *lam0, int32_t *used, cudaStream_t s)
 {
-    choose_kernel<<<1, 32, 0, s>>>(m, lam_w, lam_c, ev_w, ev_c, lam0, used);
+    choose_kernel<<<1, 32, 0, s>>>(m, lam_w, lam_c, g2, lam0, used);
     return cudaGetLastError();
 }
 

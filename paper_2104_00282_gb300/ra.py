@@ -33,7 +33,8 @@ class ra_solve_opts(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("max_evals", ctypes.c_int32),
                 ("lbfgs_mem", ctypes.c_int32), ("update", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("lam_floor", ctypes.c_double),
-                ("master_lb", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("master_lb", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("init_step", ctypes.c_double)]
 
 
 class ra_solve_info(ctypes.Structure):
@@ -386,9 +387,11 @@ class AllocationProblem:
         return lam
 
     def solve(self, tol=1e-6, max_evals=500, lam0=None, update="lbfgs", use_graph=True,
-              lbfgs_mem=10, master_lb=True):
+              lbfgs_mem=10, master_lb=True, init_step=None):
         o = ra_solve_opts_default()
         o.master_lb = 1 if master_lb else 0
+        if init_step is not None:
+            o.init_step = init_step
         o.tol_rel = tol
         o.max_evals = max_evals
         o.lbfgs_mem = lbfgs_mem
@@ -539,8 +542,10 @@ class AllocationBatch:
         return self
 
     def solve(self, tol=1e-6, max_evals=500, lam0=None, use_graph=True, master_lb=True,
-              lbfgs_mem=10):
+              lbfgs_mem=10, init_step=None):
         o = ra_solve_opts_default()
+        if init_step is not None:
+            o.init_step = init_step
         o.tol_rel = tol
         o.max_evals = max_evals
         o.use_graph = 1 if use_graph else 0

@@ -34,6 +34,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "warmstart_mlp.npy")
 M = 16
 TRAIN_SEED, EVAL_SEED = 0, 1
+# first price step from the network's prices, as a fraction of |lambda| (the
+# cold start's 0.05 overshoots from a start a few percent from the optimum)
+WARM_INIT_STEP = 0.01
 
 
 def _torch():
@@ -151,7 +154,8 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
 
         def warm():
             lam0, used = prob.warm_prices(net)
-            return prob.solve(tol=tol, max_evals=max_evals, lam0=lam0), used
+            step = WARM_INIT_STEP if used else None
+            return prob.solve(tol=tol, max_evals=max_evals, lam0=lam0, init_step=step), used
 
         if i % 2 == 0:
             ci, ct = timed(cold)
