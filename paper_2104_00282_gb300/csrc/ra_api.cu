@@ -479,7 +479,7 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
     for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
         if (!b->nchunks[c]) continue;
         int per_sm = 0;
-        e = ra::batch_configure(4 << c, &per_sm);
+        e = ra::batch_configure(4 << c, !(flags & RA_NO_JOB_CAP), &per_sm);
         if (e != cudaSuccess) break;
         if (per_sm < 1) per_sm = 1;
         const long long g = static_cast<long long>(b->num_sms) * per_sm;

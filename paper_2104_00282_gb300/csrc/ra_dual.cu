@@ -1142,11 +1142,12 @@ __device__ __forceinline__ bool tile_full(const BatchDualArgs &B, const TileCurs
 // partials in chunk order and writes its EvalOut, so the results equal a
 // deterministic single-problem evaluation up to the order of additions.
 template <int MT, bool CAP>
-__global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
+__global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDualArgs B)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
-    __shared__ float lam_s[RA_MAX_M];
+    __shared__ __align__(16) float lam_s[RA_MAX_M];
+    __shared__ __align__(16) float mu_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
     __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
@@ -1189,7 +1190,6 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
     TileCursor cur;
     cursor_first(B, cur);
     long long consumed = 0;
-    float lam_r[MT], mu_r[MT];
     KahanF hsum, uxsum, lbsum, racc, rlin;
     const int nv_lin = CAP ? 0 : 1;
     while (cur.c < B.nchunks) {
@@ -1208,16 +1208,11 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
             __syncthreads();
             if (tid < RA_MAX_M) {
                 lam_s[tid] = tid < m ? static_cast<float>(B.st[p].lam_trial[tid]) : Fn<float>::inf();
+                mu_s[tid] = inv_price<float>(lam_s[tid]);
                 s_s[tid] = (lag && tid < m) ? static_cast<float>(B.st[p].s_lag[tid]) : 1.0f;
                 sl_s[tid] = (lag && tid < m) ? static_cast<float>(B.st[p].s_lin_lag[tid]) : 1.0f;
             }
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < MT; ++k) {
-                const int c = colof<MT>(k, rot);
-                lam_r[k] = lam_s[c];
-                mu_r[k] = inv_price<float>(lam_s[c]);
-            }
             hsum = uxsum = lbsum = racc = rlin = KahanF{};
         }
         const long long t = B.chunk_tile0[cur.c] + cur.k;
@@ -1267,18 +1262,13 @@ __global__ void __launch_bounds__(kTile, 2) batch_dual_kernel(BatchDualArgs B)
             tp = lbt_prev[i];
             jp = lbj_prev[i];
         }
-        float a[MT];
-        load_row<MT>(a, row, P.A, i, valid, m, grouped, rot);
         JobSol<float> sol;
         sol.cP = sol.cQ = -1;
         sol.xP = sol.xQ = 0.f;
         if (valid) {
-            auto fetch = [&](int k, float &av, float &lv) {
-                const int c = colof<MT>(k, rot);
-                av = row != nullptr ? row[c] : __ldg(&P.A[i * m + c]);
-                lv = lam_s[c];
-            };
-            solve_job<MT, CAP, false, float>(a, lam_r, mu_r, rot, fetch, kind, w, pr, sol);
+            // full tiles read the staged row, a ragged tile the row in HBM
+            solve_job_sm<MT, CAP>(row != nullptr ? row : P.A + i * m, mu_s, lam_s, m, grouped, rot,
+                                  kind, w, pr, sol);
             hsum.add(sol.h);
             uxsum.add(sol.u);
             if (lag) {
@@ -1948,26 +1938,31 @@ cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jsta
 }
 
 
-int batch_stages(int mt)
+int batch_stages(int mt, int cap)
 {
+    const size_t budget = cap ? 106 * 1024 : 70 * 1024;   // two / three CTAs per SM
     switch (mt) {
-    case 4: return mt_stages<4>(4);
-    case 8: return mt_stages<8>(8);
-    case 16: return mt_stages<16>(16);
-    default: return mt_stages<32>(32);
+    case 4: return mt_stages<4>(4, budget);
+    case 8: return mt_stages<8>(8, budget);
+    case 16: return mt_stages<16>(16, budget);
+    default: return mt_stages<32>(32, budget);
     }
 }
 
-size_t batch_smem(int mt) { return batch_stages(mt) * StageLayout<4>::bytes(mt) + 128; }
+size_t batch_smem(int mt, int cap) { return batch_stages(mt, cap) * StageLayout<4>::bytes(mt) + 128; }
 
-cudaError_t batch_configure(int mt, int *blocks_per_sm)
+cudaError_t batch_configure(int mt, int cap, int *blocks_per_sm)
 {
     const void *fn = nullptr;
     switch (mt) {
-    case 4: fn = reinterpret_cast<const void *>(batch_dual_kernel<4, true>); break;
-    case 8: fn = reinterpret_cast<const void *>(batch_dual_kernel<8, true>); break;
-    case 16: fn = reinterpret_cast<const void *>(batch_dual_kernel<16, true>); break;
-    default: fn = reinterpret_cast<const void *>(batch_dual_kernel<32, true>); break;
+    case 4: fn = cap ? reinterpret_cast<const void *>(batch_dual_kernel<4, true>)
+                     : reinterpret_cast<const void *>(batch_dual_kernel<4, false>); break;
+    case 8: fn = cap ? reinterpret_cast<const void *>(batch_dual_kernel<8, true>)
+                     : reinterpret_cast<const void *>(batch_dual_kernel<8, false>); break;
+    case 16: fn = cap ? reinterpret_cast<const void *>(batch_dual_kernel<16, true>)
+                      : reinterpret_cast<const void *>(batch_dual_kernel<16, false>); break;
+    default: fn = cap ? reinterpret_cast<const void *>(batch_dual_kernel<32, true>)
+                      : reinterpret_cast<const void *>(batch_dual_kernel<32, false>); break;
     }
     cudaError_t e;
 #define RA_BATTR(MT)                                                                               \
@@ -1984,7 +1979,7 @@ cudaError_t batch_configure(int mt, int *blocks_per_sm)
     RA_BATTR(16)
     RA_BATTR(32)
 #undef RA_BATTR
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kTile, batch_smem(mt));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kTile, batch_smem(mt, cap));
 }
 
 cudaError_t launch_batch_dual(int mt, const BatchDualArgs &a, int grid, size_t smem, cudaStream_t s)

@@ -256,9 +256,9 @@ cudaError_t configure_dual(ra_problem *p);
 cudaError_t launch_batch_dual(int mt, const BatchDualArgs &a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_init(int mt, const BatchDualArgs &a, double *lam1_concat,
                               const long long *lam_off, int grid, cudaStream_t s);
-int batch_stages(int mt);
-size_t batch_smem(int mt);
-cudaError_t batch_configure(int mt, int *blocks_per_sm);
+int batch_stages(int mt, int cap);
+size_t batch_smem(int mt, int cap);
+cudaError_t batch_configure(int mt, int cap, int *blocks_per_sm);
 
 // One problem for the warm-start statistics (device copy or by value).
 struct FeatProblem {

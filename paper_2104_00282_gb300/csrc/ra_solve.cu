@@ -1052,7 +1052,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
         a.partials = b->partials[c];
         a.ticket = b->ticket;
         a.status = b->status;
-        a.stages = batch_stages(4 << c);
+        a.stages = batch_stages(4 << c, cap);
         a.cap = cap;
     }
     const double *lam0 = lambda0;
@@ -1080,7 +1080,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
     auto body = [&](cudaGraphConditionalHandle cond, int use_cond) -> cudaError_t {
         for (int c = 0; c < 4; ++c) {
             if (!b->nchunks[c]) continue;
-            cudaError_t e1 = launch_batch_dual(4 << c, args[c], b->grid[c], batch_smem(4 << c), s);
+            cudaError_t e1 = launch_batch_dual(4 << c, args[c], b->grid[c], batch_smem(4 << c, cap), s);
             if (e1 != cudaSuccess) return e1;
         }
         step_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, b->status, cond,
