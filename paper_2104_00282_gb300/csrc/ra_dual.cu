@@ -683,6 +683,38 @@ __device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real>
     }
 }
 
+// Column sums of the first nv entries of G rows of kPartW FP64 partials, by
+// the whole CTA: warp w adds rows w, w + kWarps, ... (lane l holds entries l,
+// l + 32, l + 64; one row is a coalesced read), eight rows' loads in flight
+// per trip, then the warps' sums are added in warp order -- a fixed order
+// whatever the timing.  red[0][c] receives column c's total; red is
+// overwritten, and every thread of the CTA must call this.
+static_assert(kPartW <= 96, "three entries per lane");
+__device__ __forceinline__ void sum_partial_rows(const double *partials, unsigned G, int nv,
+                                                 double (*red)[kPartW])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool h0 = lane < nv, h1 = lane + 32 < nv, h2 = lane + 64 < nv;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 8
+    for (unsigned b = warp; b < G; b += kWarps) {
+        const double *row = partials + static_cast<size_t>(b) * kPartW + lane;
+        if (h0) a0 += __ldcg(row);
+        if (h1) a1 += __ldcg(row + 32);
+        if (h2) a2 += __ldcg(row + 64);
+    }
+    __syncthreads();  // red's earlier contents have been read
+    if (h0) red[warp][lane] = a0;
+    if (h1) red[warp][lane + 32] = a1;
+    if (h2) red[warp][lane + 64] = a2;
+    __syncthreads();
+    if (tid < nv) {
+        double v = red[0][tid];
+        for (int w = 1; w < kWarps; ++w) v += red[w][tid];
+        red[0][tid] = v;
+    }
+}
+
 // Block stage + grid stage: per-thread FP64 values -> per-block partials
 // (fixed warp order) -> the last CTA to finish sums the partials in block
 // order.  Returns true in that CTA only, where red[0][0 .. m+4) then holds the
@@ -718,11 +750,7 @@ __device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    if (tid < nv) {
-        double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[static_cast<size_t>(b) * kPartW + tid]);
-        red[0][tid] = v;
-    }
+    sum_partial_rows(partials, gridDim.x, nv, red);
     if (tid == 0) *ticket = 0u;  // ready for the next launch
     __syncthreads();
     return true;
@@ -1327,12 +1355,9 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
             __syncthreads();
             if (is_last) {
                 __threadfence();
-                if (tid < (1 + nv_lin) * m + 4) {
-                    double v = 0.0;
-                    for (int c2 = P.chunk_begin; c2 < P.chunk_end; ++c2)
-                        v += __ldcg(&B.partials[static_cast<size_t>(c2) * kPartW + tid]);
-                    red[0][tid] = v;
-                }
+                sum_partial_rows(B.partials + static_cast<size_t>(P.chunk_begin) * kPartW,
+                                 static_cast<unsigned>(P.chunk_end - P.chunk_begin),
+                                 (1 + nv_lin) * m + 4, red);
                 __syncthreads();
                 EvalOut *out = B.ev + p;
                 if (tid < m) {
@@ -1421,12 +1446,9 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
         __syncthreads();
         if (is_last) {
             __threadfence();
-            if (tid < m) {
-                double v = 0.0;
-                for (int c2 = P.chunk_begin; c2 < P.chunk_end; ++c2)
-                    v += __ldcg(&B.partials[static_cast<size_t>(c2) * kPartW + tid]);
-                lam1[lam_off[p] + tid] = v / static_cast<double>(P.n);
-            }
+            sum_partial_rows(B.partials + static_cast<size_t>(P.chunk_begin) * kPartW,
+                             static_cast<unsigned>(P.chunk_end - P.chunk_begin), m, red);
+            if (tid < m) lam1[lam_off[p] + tid] = red[0][tid] / static_cast<double>(P.n);
             if (tid == 0) B.ticket[p] = 0u;
         }
     }
