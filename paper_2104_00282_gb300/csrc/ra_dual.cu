@@ -664,6 +664,64 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+// Float-float: the unevaluated sum hi + lo of two FP32 numbers (about 44
+// significant bits), the type of the block and grid stages of the FP32
+// path's reductions.  FP64 arithmetic issues at a small fraction of the FP32
+// rate on this GPU; the CTA that summed a grid's FP64 block partials took
+// about 20 us, which the same sum in float-float arithmetic does not.
+struct __align__(8) FF {
+    float hi, lo;
+};
+
+// hi + lo of a + b: Knuth's two-sum of the high parts (its error term is
+// exact and the same in either operand order, so the butterfly below leaves
+// every lane with bitwise the same value), plus the low parts, renormalised.
+// A non-finite sum is returned as (sum, 0).  Branch-free, so that loads
+// after it in a loop are not held behind it.
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float hi = s + e;
+    const float lo = e - (hi - s);
+    const bool fin = isfinite(s);
+    return FF{fin ? hi : s, fin ? lo : 0.0f};
+}
+__device__ __forceinline__ FF ff_of(const KahanF &k) { return FF{k.s, -k.c}; }
+
+// Reduction-stage arithmetic on FP64 values (the FP64 job-math kernel) and
+// on float-float values (the FP32 kernels).
+__device__ __forceinline__ double red_add(double a, double b) { return a + b; }
+__device__ __forceinline__ FF red_add(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(FF a)
+{
+    return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+__device__ __forceinline__ double ldcg_red(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ FF ldcg_red(const FF *p)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return FF{v.x, v.y};
+}
+template <typename T> __device__ __forceinline__ T red_zero();
+template <> __device__ __forceinline__ double red_zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ FF red_zero<FF>() { return FF{0.0f, 0.0f}; }
+__device__ __forceinline__ double warp_sum(double v) { return warp_sum_d(v); }
+__device__ __forceinline__ FF warp_sum(FF v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        FF o;
+        o.hi = __shfl_xor_sync(kFull, v.hi, off);
+        o.lo = __shfl_xor_sync(kFull, v.lo, off);
+        v = ff_add(v, o);
+    }
+    return v;
+}
+static_assert(sizeof(FF) == sizeof(double), "partial slots hold either type");
+
 // Usage of the warp's linear-utility jobs per column (no-cap mode, where a
 // job uses one column, cQ): one butterfly sum per distinct column among
 // those lanes, taken in lane order; lane c adds column c's sum to acc.
@@ -690,18 +748,34 @@ __device__ __forceinline__ void warp_rlin(bool lin, int lane, const JobSol<Real>
 // whatever the timing.  red[0][c] receives column c's total; red is
 // overwritten, and every thread of the CTA must call this.
 static_assert(kPartW <= 96, "three entries per lane");
-__device__ __forceinline__ void sum_partial_rows(const double *partials, unsigned G, int nv,
-                                                 double (*red)[kPartW])
+template <typename T>
+__device__ __forceinline__ void sum_partial_rows(const T *partials, unsigned G, int nv,
+                                                 T (*red)[kPartW])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool h0 = lane < nv, h1 = lane + 32 < nv, h2 = lane + 64 < nv;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-#pragma unroll 8
-    for (unsigned b = warp; b < G; b += kWarps) {
-        const double *row = partials + static_cast<size_t>(b) * kPartW + lane;
-        if (h0) a0 += __ldcg(row);
-        if (h1) a1 += __ldcg(row + 32);
-        if (h2) a2 += __ldcg(row + 64);
+    const T zero = red_zero<T>();
+    T a0 = zero, a1 = zero, a2 = zero;
+    constexpr int U = 8;  // rows per warp whose loads are issued before any add
+    for (unsigned b0 = warp; b0 < G; b0 += U * kWarps) {
+        T v0[U], v1[U], v2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned b = b0 + u * kWarps;
+            const T *row = partials + static_cast<size_t>(b) * kPartW + lane;
+            v0[u] = (b < G && h0) ? ldcg_red(row) : zero;
+            v1[u] = (b < G && h1) ? ldcg_red(row + 32) : zero;
+            v2[u] = (b < G && h2) ? ldcg_red(row + 64) : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned b = b0 + u * kWarps;
+            if (b < G) {
+                a0 = red_add(a0, v0[u]);
+                a1 = red_add(a1, v1[u]);
+                a2 = red_add(a2, v2[u]);
+            }
+        }
     }
     __syncthreads();  // red's earlier contents have been read
     if (h0) red[warp][lane] = a0;
@@ -709,8 +783,8 @@ __device__ __forceinline__ void sum_partial_rows(const double *partials, unsigne
     if (h2) red[warp][lane + 64] = a2;
     __syncthreads();
     if (tid < nv) {
-        double v = red[0][tid];
-        for (int w = 1; w < kWarps; ++w) v += red[w][tid];
+        T v = red[0][tid];
+        for (int w = 1; w < kWarps; ++w) v = red_add(v, red[w][tid]);
         red[0][tid] = v;
     }
 }
@@ -720,28 +794,31 @@ __device__ __forceinline__ void sum_partial_rows(const double *partials, unsigne
 // order.  Returns true in that CTA only, where red[0][0 .. m+4) then holds the
 // totals (h, U(X), lagged U_lb, spare, r_0..r_{m-1}, then r_lin_0..r_lin_{m-1}
 // when lin is set).  red is kWarps x kPartW.
-__device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc, double rlin,
-                            int m, bool lin, bool lane_owns_col, double *partials, unsigned *ticket,
-                            double (*red)[kPartW])
+template <typename T>
+__device__ __noinline__ bool grid_reduce(T hsum, T uxsum, T lbsum, T racc, T rlin, int m, bool lin,
+                            bool lane_owns_col, double *partial_slots, unsigned *ticket,
+                            T (*red)[kPartW])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ int is_last;
+    T *partials = reinterpret_cast<T *>(partial_slots);
     const int nv = lin ? 2 * m + 4 : m + 4;
-    hsum = warp_sum_d(hsum);
-    uxsum = warp_sum_d(uxsum);
-    lbsum = warp_sum_d(lbsum);
+    const T zero = red_zero<T>();
+    hsum = warp_sum(hsum);
+    uxsum = warp_sum(uxsum);
+    lbsum = warp_sum(lbsum);
     if (lane == 0) {
         red[warp][0] = hsum;
         red[warp][1] = uxsum;
         red[warp][2] = lbsum;
-        red[warp][3] = 0.0;
+        red[warp][3] = zero;
     }
-    if (lane < m) red[warp][4 + lane] = lane_owns_col ? racc : 0.0;
+    if (lane < m) red[warp][4 + lane] = lane_owns_col ? racc : zero;
     if (lin && lane < m) red[warp][4 + m + lane] = rlin;
     __syncthreads();
     if (tid < nv) {
-        double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += red[w][tid];
+        T v = red[0][tid];
+        for (int w = 1; w < kWarps; ++w) v = red_add(v, red[w][tid]);
         partials[static_cast<size_t>(blockIdx.x) * kPartW + tid] = v;
     }
     __threadfence();
@@ -757,26 +834,39 @@ __device__ bool grid_reduce(double hsum, double uxsum, double lbsum, double racc
 }
 
 // Dual outputs (Section 3): g = lambda^T R + sum h_i, q = R - r.
-__device__ void reduce_and_finalize(double hsum, double uxsum, double lbsum, double racc,
-                                    double rlin, int m, bool lin, bool lane_owns_col,
-                                    const DualParams &P, double (*red)[kPartW])
+// lambda^T R, summed in column order by one thread.  The streaming kernels
+// stage lambda and R in shared memory in their prologue and have a thread of
+// warp 1 take the sum while the first tiles are in flight (the loop is a
+// chain of dependent FP64 multiply-adds; from global memory under a full
+// stream every step would also wait for a load).
+__device__ __forceinline__ double lam_dot_R(const double *lam, const double *R, int m)
+{
+    double lr = 0.0;
+    for (int j = 0; j < m; ++j) lr += lam[j] * R[j];
+    return lr;
+}
+
+template <typename T>
+__device__ void reduce_and_finalize(T hsum, T uxsum, T lbsum, T racc, T rlin, int m, bool lin,
+                                    bool lane_owns_col, const DualParams &P, T (*red)[kPartW],
+                                    const double *lr_s)
 {
     if (!grid_reduce(hsum, uxsum, lbsum, racc, rlin, m, lin, lane_owns_col, P.partials, P.ticket,
                      red))
         return;
     const int tid = threadIdx.x;
     if (tid < m) {
-        P.out->r[tid] = red[0][4 + tid];
-        P.out->q[tid] = P.R[tid] - red[0][4 + tid];
-        P.out->r_lin[tid] = lin ? red[0][4 + m + tid] : 0.0;
+        const double r = to_double(red[0][4 + tid]);
+        P.out->r[tid] = r;
+        P.out->q[tid] = P.R[tid] - r;
+        P.out->r_lin[tid] = lin ? to_double(red[0][4 + m + tid]) : 0.0;
     }
     if (tid == 0) {
-        double lr = 0.0;
-        for (int j = 0; j < m; ++j) lr += P.lam[j] * P.R[j];
-        P.out->sumh = red[0][0];
-        P.out->g = lr + red[0][0];
-        P.out->Ux = red[0][1];
-        P.out->Ulb_prev = red[0][2];
+        const double sumh = to_double(red[0][0]);
+        P.out->sumh = sumh;
+        P.out->g = *lr_s + sumh;
+        P.out->Ux = to_double(red[0][1]);
+        P.out->Ulb_prev = to_double(red[0][2]);
     }
 }
 
@@ -799,10 +889,14 @@ struct StageLayout {
 // which the callee may overwrite once it has read its own row.  All 256
 // threads call job for every tile, valid or not, so warp collectives work.
 // Returns false if a bounded wait gave up (the status word is then set).
-template <int MT, class Job>
+struct NoPrologue {
+    __device__ void operator()() const {}
+};
+template <int MT, class Job, class Pre = NoPrologue>
 __device__ bool stream_jobs(const float *A, const float *W, const float *Par, const uint8_t *Kind,
                             long long n, int m, int stages, long long num_full,
-                            unsigned char *smem, uint64_t *bars, int *status, Job &&job)
+                            unsigned char *smem, uint64_t *bars, int *status, Job &&job,
+                            Pre &&pre = Pre{})
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t a_bytes = StageLayout<MT>::a_bytes(m);
@@ -828,6 +922,7 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
     };
     if (tid == 0)
         for (int s = 0; s < stages; ++s) issue(s);
+    pre();  // while the first tiles are in flight (no barrier before the first tile's end)
 
     for (long long it = 0; it < n_my; ++it) {
         const int st = static_cast<int>(it % stages);
@@ -917,7 +1012,9 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     __shared__ __align__(16) float mu_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
     __shared__ float sl_s[RA_MAX_M];
-    __shared__ double red[kWarps][kPartW];
+    __shared__ FF red[kWarps][kPartW];
+    __shared__ double lamd_s[RA_MAX_M], Rd_s[RA_MAX_M];
+    __shared__ double lr_s;
 
     if (P.skip != nullptr && *P.skip != 0) return;
 
@@ -940,7 +1037,9 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
 
     if (tid < RA_MAX_M) {
-        lam_s[tid] = tid < m ? static_cast<float>(P.lam[tid]) : Fn<float>::inf();
+        lamd_s[tid] = tid < m ? P.lam[tid] : 0.0;
+        Rd_s[tid] = tid < m ? P.R[tid] : 0.0;
+        lam_s[tid] = tid < m ? static_cast<float>(lamd_s[tid]) : Fn<float>::inf();
         mu_s[tid] = inv_price<float>(lam_s[tid]);
         s_s[tid] = (LAG && lag && tid < m) ? static_cast<float>(P.s_prev[tid]) : 1.0f;
         sl_s[tid] = (LAG && lag && tid < m)
@@ -986,9 +1085,12 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
             warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, s, racc);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
-    stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job);
-    reduce_and_finalize(hsum.value(), uxsum.value(), lbsum.value(), racc.value(), rlin.value(), m,
-                        !CAP && REC, grouped ? (lane / MT == 0) : true, P, red);
+    stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job,
+                    [&] {
+                        if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
+                    });
+    reduce_and_finalize(ff_of(hsum), ff_of(uxsum), ff_of(lbsum), ff_of(racc), ff_of(rlin), m,
+                        !CAP && REC, grouped ? (lane / MT == 0) : true, P, red, &lr_s);
 }
 
 // Initial prices, Eq. e-initialization:
@@ -1004,7 +1106,7 @@ __global__ void __launch_bounds__(kTile, 2)
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ float x0_s[RA_MAX_M];
-    __shared__ double red[kWarps][kPartW];
+    __shared__ FF red[kWarps][kPartW];
     const int tid = threadIdx.x, lane = tid & 31;
     const bool grouped = (m == MT);
     constexpr int C = MT / 4;
@@ -1052,9 +1154,10 @@ __global__ void __launch_bounds__(kTile, 2)
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
-    if (grid_reduce(0.0, 0.0, 0.0, racc.value(), 0.0, m, false, grouped ? (lane / MT == 0) : true, partials,
+    const FF z = red_zero<FF>();
+    if (grid_reduce(z, z, z, ff_of(racc), z, m, false, grouped ? (lane / MT == 0) : true, partials,
                     ticket, red))
-        if (tid < m) lam1[tid] = red[0][4 + tid] / static_cast<double>(n);
+        if (tid < m) lam1[tid] = to_double(red[0][4 + tid]) / static_cast<double>(n);
 }
 
 // Dual values g(lambda_a) and g(lambda_b) in one pass over the data (the
@@ -1071,7 +1174,9 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ __align__(16) float la_s[RA_MAX_M], ma_s[RA_MAX_M], lb_s[RA_MAX_M], mb_s[RA_MAX_M];
-    __shared__ double red[kWarps][kPartW];
+    __shared__ FF red[kWarps][kPartW];
+    __shared__ double lr_s[2];
+    __shared__ double lad_s[RA_MAX_M], lbd_s[RA_MAX_M], Rd_s[RA_MAX_M];
     const int tid = threadIdx.x;
     const bool grouped = (m == MT);
     constexpr int C = MT / 4;
@@ -1079,6 +1184,9 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     if (tid < RA_MAX_M) {
         la_s[tid] = tid < m ? static_cast<float>(lam_a[tid]) : Fn<float>::inf();
         lb_s[tid] = tid < m ? static_cast<float>(lam_b[tid]) : Fn<float>::inf();
+        lad_s[tid] = tid < m ? lam_a[tid] : 0.0;
+        lbd_s[tid] = tid < m ? lam_b[tid] : 0.0;
+        Rd_s[tid] = tid < m ? R[tid] : 0.0;
         ma_s[tid] = inv_price<float>(la_s[tid]);
         mb_s[tid] = inv_price<float>(lb_s[tid]);
     }
@@ -1096,16 +1204,17 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         hb.add(sb.h);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
-    stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
-    if (grid_reduce(ha.value(), hb.value(), 0.0, 0.0, 0.0, 0, false, true, partials, ticket, red) &&
-        tid == 0) {
-        double ra = 0.0, rb = 0.0;
-        for (int j = 0; j < m; ++j) {
-            ra += lam_a[j] * R[j];
-            rb += lam_b[j] * R[j];
+    stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job, [&] {
+        if (tid == 32) {
+            lr_s[0] = lam_dot_R(lad_s, Rd_s, m);
+            lr_s[1] = lam_dot_R(lbd_s, Rd_s, m);
         }
-        g_out[0] = ra + red[0][0];
-        g_out[1] = rb + red[0][1];
+    });
+    const FF z = red_zero<FF>();
+    if (grid_reduce(ff_of(ha), ff_of(hb), z, z, z, 0, false, true, partials, ticket, red) &&
+        tid == 0) {
+        g_out[0] = lr_s[0] + to_double(red[0][0]);
+        g_out[1] = lr_s[1] + to_double(red[0][1]);
     }
 }
 
@@ -1178,7 +1287,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
     __shared__ __align__(16) float mu_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
     __shared__ float sl_s[RA_MAX_M];
-    __shared__ double red[kWarps][kPartW];
+    __shared__ FF red[kWarps][kPartW];
     __shared__ int is_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int C = MT / 4;
@@ -1330,21 +1439,21 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
         // chunk end: block sums -> this chunk's partial slot -> per-problem ticket
         const bool chunk_end = cur.k + 1 >= B.chunk_ntiles[cur.c];
         if (chunk_end) {
-            double h = warp_sum_d(hsum.value()), ux = warp_sum_d(uxsum.value()),
-                   lb = warp_sum_d(lbsum.value());
+            const FF h = warp_sum(ff_of(hsum)), ux = warp_sum(ff_of(uxsum)),
+                     lb = warp_sum(ff_of(lbsum)), z = red_zero<FF>();
             if (lane == 0) {
                 red[warp][0] = h;
                 red[warp][1] = ux;
                 red[warp][2] = lb;
-                red[warp][3] = 0.0;
+                red[warp][3] = z;
             }
-            if (lane < m) red[warp][4 + lane] = (grouped ? (lane / MT == 0) : true) ? racc.value() : 0.0;
-            if (nv_lin && lane < m) red[warp][4 + m + lane] = rlin.value();
+            if (lane < m) red[warp][4 + lane] = (grouped ? (lane / MT == 0) : true) ? ff_of(racc) : z;
+            if (nv_lin && lane < m) red[warp][4 + m + lane] = ff_of(rlin);
             __syncthreads();
             if (tid < (1 + nv_lin) * m + 4) {
-                double v = 0.0;
-                for (int w2 = 0; w2 < kWarps; ++w2) v += red[w2][tid];
-                B.partials[static_cast<size_t>(cur.c) * kPartW + tid] = v;
+                FF v = red[0][tid];
+                for (int w2 = 1; w2 < kWarps; ++w2) v = ff_add(v, red[w2][tid]);
+                reinterpret_cast<FF *>(B.partials)[static_cast<size_t>(cur.c) * kPartW + tid] = v;
             }
             __threadfence();
             __syncthreads();
@@ -1355,23 +1464,24 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
             __syncthreads();
             if (is_last) {
                 __threadfence();
-                sum_partial_rows(B.partials + static_cast<size_t>(P.chunk_begin) * kPartW,
+                sum_partial_rows(reinterpret_cast<const FF *>(B.partials) +
+                                     static_cast<size_t>(P.chunk_begin) * kPartW,
                                  static_cast<unsigned>(P.chunk_end - P.chunk_begin),
                                  (1 + nv_lin) * m + 4, red);
                 __syncthreads();
                 EvalOut *out = B.ev + p;
                 if (tid < m) {
-                    out->r[tid] = red[0][4 + tid];
-                    out->q[tid] = P.R[tid] - red[0][4 + tid];
-                    out->r_lin[tid] = nv_lin ? red[0][4 + m + tid] : 0.0;
+                    const double r = to_double(red[0][4 + tid]);
+                    out->r[tid] = r;
+                    out->q[tid] = P.R[tid] - r;
+                    out->r_lin[tid] = nv_lin ? to_double(red[0][4 + m + tid]) : 0.0;
                 }
                 if (tid == 0) {
-                    double lr = 0.0;
-                    for (int j = 0; j < m; ++j) lr += B.st[p].lam_trial[j] * P.R[j];
-                    out->sumh = red[0][0];
-                    out->g = lr + red[0][0];
-                    out->Ux = red[0][1];
-                    out->Ulb_prev = red[0][2];
+                    const double sumh = to_double(red[0][0]);
+                    out->sumh = sumh;
+                    out->g = lam_dot_R(B.st[p].lam_trial, P.R, m) + sumh;
+                    out->Ux = to_double(red[0][1]);
+                    out->Ulb_prev = to_double(red[0][2]);
                     B.ticket[p] = 0u;
                 }
             }
@@ -1389,7 +1499,7 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
                                                            const long long *lam_off)
 {
     __shared__ float x0_s[RA_MAX_M];
-    __shared__ double red[kWarps][kPartW];
+    __shared__ FF red[kWarps][kPartW];
     __shared__ int is_last;
     __shared__ float rows[kTile * MT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1433,12 +1543,12 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
             __syncwarp();
             warp_colsum<MT, float, KahanF>(rows + warp * 32 * m, m, lane, false, racc);
         }
-        if (lane < m) red[warp][4 + lane] = racc.value();
+        if (lane < m) red[warp][4 + lane] = ff_of(racc);
         __syncthreads();
         if (tid < m) {
-            double v = 0.0;
-            for (int w2 = 0; w2 < kWarps; ++w2) v += red[w2][4 + tid];
-            B.partials[static_cast<size_t>(c) * kPartW + tid] = v;
+            FF v = red[0][4 + tid];
+            for (int w2 = 1; w2 < kWarps; ++w2) v = ff_add(v, red[w2][4 + tid]);
+            reinterpret_cast<FF *>(B.partials)[static_cast<size_t>(c) * kPartW + tid] = v;
         }
         __threadfence();
         __syncthreads();
@@ -1446,9 +1556,10 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
         __syncthreads();
         if (is_last) {
             __threadfence();
-            sum_partial_rows(B.partials + static_cast<size_t>(P.chunk_begin) * kPartW,
+            sum_partial_rows(reinterpret_cast<const FF *>(B.partials) +
+                                 static_cast<size_t>(P.chunk_begin) * kPartW,
                              static_cast<unsigned>(P.chunk_end - P.chunk_begin), m, red);
-            if (tid < m) lam1[lam_off[p] + tid] = red[0][tid] / static_cast<double>(P.n);
+            if (tid < m) lam1[lam_off[p] + tid] = to_double(red[0][tid]) / static_cast<double>(P.n);
             if (tid == 0) B.ticket[p] = 0u;
         }
     }
@@ -1467,6 +1578,7 @@ __global__ void __launch_bounds__(kTile)
     __shared__ float s_s[RA_MAX_M];
     __shared__ float sl_s[RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
+    __shared__ double lr_s;
     Real *rows = reinterpret_cast<Real *>(smem_simple);  // kTile x m
 
     if (P.skip != nullptr && *P.skip != 0) return;
@@ -1498,6 +1610,7 @@ __global__ void __launch_bounds__(kTile)
         lam_r[k] = lam_s[k];
         mu_r[k] = inv_price<Real>(lam_s[k]);
     }
+    if (tid == 32) lr_s = lam_dot_R(P.lam, P.R, m);  // read after the grid stage's barriers
     double hsum = 0.0, uxsum = 0.0, lbsum = 0.0, racc = 0.0, rlin = 0.0;
     const long long stride = static_cast<long long>(gridDim.x) * kTile;
     const long long nround = (P.n + stride - 1) / stride;
@@ -1540,7 +1653,7 @@ __global__ void __launch_bounds__(kTile)
         warp_rsum<MT, Real, double>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
         if (!CAP) warp_rlin<Real, double>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
     }
-    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, true, P, red);
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, true, P, red, &lr_s);
 }
 
 // ---------------------------------------------------------------------------- lower bound
