@@ -546,16 +546,63 @@ template <int MT, typename Real, typename Acc>
 __device__ __forceinline__ void warp_colsum(const Real *warp_rows, int m, int lane, bool grouped,
                                             Acc &racc);
 
+// Column sums of the warp's 32 x 32 FP32 block when m = 32, transposed: lane
+// l zeroes row l, writes its job's x into slot l of rows cQ and cP, and lane
+// c sums row c (the column-c usage of the warp's 32 jobs) with eight 128-bit
+// loads in rotated chunk order (four lanes per 16-byte bank group, the
+// minimum for a 512-byte warp access) -- a quarter of the load instructions
+// of a column walk.  Returns the four partial sums of lane `lane`'s row;
+// with `lm` non-zero, cl gets the partial sums of the slots whose lane bit
+// is set in lm.
+template <bool LIN>
+__device__ __forceinline__ void warp_rows_t32(float *warp_rows, int lane, int rot, int cP, float xP,
+                                              int cQ, float xQ, unsigned lm, float (&cs)[4],
+                                              float (&cl)[4])
+{
+    float *row = warp_rows + lane * 32;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        reinterpret_cast<float4 *>(row)[(c + rot) & 7] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    if (cP >= 0) warp_rows[cP * 32 + lane] = xP;
+    if (cQ >= 0) warp_rows[cQ * 32 + lane] = xQ;
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int q = (c + rot) & 7;
+        const float4 v = reinterpret_cast<const float4 *>(row)[q];
+        cs[0] += v.x;
+        cs[1] += v.y;
+        cs[2] += v.z;
+        cs[3] += v.w;
+        if (LIN) {
+            const unsigned b = lm >> (4 * q);
+            cl[0] += (b & 1u) ? v.x : 0.f;
+            cl[1] += (b & 2u) ? v.y : 0.f;
+            cl[2] += (b & 4u) ? v.z : 0.f;
+            cl[3] += (b & 8u) ? v.w : 0.f;
+        }
+    }
+    __syncwarp();
+}
+
 // Warp-cooperative r accumulation: each lane's `row` (m entries of shared
 // memory that the lane alone owns) becomes its dense x_i; the 32 x m block is
 // then summed column-wise in a fixed order.  `racc` of lane c (< m) gains the
 // column-c sum.  `grouped` selects the lane-split column sum used when
-// m == MT is a power of two >= 4.
+// m == MT is a power of two >= 4 (and the transposed sum when m = 32).
 template <int MT, typename Real, typename Acc>
 __device__ __forceinline__ void warp_rsum(Real *warp_rows, int m, int lane, bool grouped,
                                           int rot, const JobSol<Real> &s, Acc &racc)
 {
     Real *row = warp_rows + lane * m;
+    if (MT == 32 && grouped && sizeof(Real) == 4) {
+        float cs[4] = {0.f, 0.f, 0.f, 0.f}, cl[4];
+        warp_rows_t32<false>(reinterpret_cast<float *>(warp_rows), lane, rot, s.cP,
+                             static_cast<float>(s.xP), s.cQ, static_cast<float>(s.xQ), 0u, cs, cl);
+        acc_add(racc, static_cast<Real>((cs[0] + cs[1]) + (cs[2] + cs[3])));
+        return;
+    }
     if (grouped && sizeof(Real) == 4) {
         constexpr int C = MT / 4;
 #pragma unroll
@@ -606,6 +653,14 @@ __device__ __forceinline__ void warp_rsum_lin(float *warp_rows, int m, int lane,
                                               int rot, const JobSol<float> &s, bool lin, Acc &racc,
                                               Acc &rlin)
 {
+    const unsigned lm = __ballot_sync(kFull, lin);
+    if (MT == 32 && grouped) {
+        float cs[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+        warp_rows_t32<true>(warp_rows, lane, rot, s.cP, s.xP, s.cQ, s.xQ, lm, cs, cl);
+        acc_add(racc, (cs[0] + cs[1]) + (cs[2] + cs[3]));
+        acc_add(rlin, (cl[0] + cl[1]) + (cl[2] + cl[3]));
+        return;
+    }
     float *row = warp_rows + lane * m;
     if (grouped) {
         constexpr int C = MT / 4;
@@ -619,7 +674,6 @@ __device__ __forceinline__ void warp_rsum_lin(float *warp_rows, int m, int lane,
     }
     if (s.cP >= 0) row[s.cP] = s.xP;
     if (s.cQ >= 0) row[s.cQ] = s.xQ;
-    const unsigned lm = __ballot_sync(kFull, lin);
     __syncwarp();
     if (grouped) {
         constexpr int G = 32 / MT;
