@@ -14,13 +14,15 @@
 // parameters and kinds are contiguous, so one elected thread moves each with
 // a 1-D bulk TMA copy (cp.async.bulk) into a multi-stage shared-memory ring
 // completed on mbarriers.  Threads read their row with 128-bit shared loads
-// in a per-thread rotated chunk order (conflict-free); prices live in
-// registers in the same rotated order, so the argmin and hull loops are fully
-// unrolled register code.  The per-resource sums r_j use the tile's own rows
-// as a warp-private dense 32 x m scratch (each job writes its <= 2 nonzeros),
-// reduced column-wise in a fixed order.  Per-thread FP64 accumulators, a
-// fixed-order block stage and a last-block-done grid stage make every output
-// bitwise deterministic for a given GPU.
+// in a per-thread rotated chunk order (conflict-free) against the prices and
+// inverse prices in shared memory (broadcast reads), so the argmin and hull
+// loops hold no per-job register array.  The per-resource sums r_j use the
+// tile's own rows as a warp-private dense 32 x m scratch (each job writes its
+// <= 2 nonzeros; transposed when m = 32), reduced in a fixed order.
+// Compensated FP32 per-thread accumulators, a fixed-order float-float block
+// stage and a last-block-done grid stage make every output bitwise
+// deterministic for a given GPU.  The FP64 job-math kernel keeps FP64
+// accumulators and stages.
 
 #include <cstdio>
 
