@@ -860,6 +860,7 @@ __device__ __noinline__ bool grid_reduce(T hsum, T uxsum, T lbsum, T racc, T rli
     T *partials = reinterpret_cast<T *>(partial_slots);
     const int nv = lin ? 2 * m + 4 : m + 4;
     const T zero = red_zero<T>();
+    __syncthreads();  // red may alias tile memory that other warps still read
     hsum = warp_sum(hsum);
     uxsum = warp_sum(uxsum);
     lbsum = warp_sum(lbsum);
@@ -934,29 +935,48 @@ struct StageLayout {
     static __host__ __device__ size_t bytes(int m) { return a_bytes(m) + kTile * 9; }
 };
 
+// A stage of the single-problem streaming ring also has room for the tile's
+// records of the previous evaluation (kTile float2 then kTile uchar2), which
+// the solver's evaluation loads with the tile instead of per thread.
+constexpr size_t kRecBytes = kTile * (sizeof(float2) + sizeof(uchar2));
+constexpr int kRingSmemMax = 112 * 1024;  // dynamic allowance of the single-problem streaming kernels
+__host__ __device__ inline size_t ring_stage_bytes(int m) { return StageLayout<4>::bytes(m) + kRecBytes; }
+
+// The block stage's rows of the single-problem streaming kernels live in the
+// tile ring, idle by then (one row of kPartW per warp).
+__device__ __forceinline__ FF (*ring_red(unsigned char *smem))[kPartW]
+{
+    return reinterpret_cast<FF (*)[kPartW]>(smem);
+}
+
 // Per-job stream over this CTA's share of the jobs.  Full 256-job tiles come
-// in through a ring of `stages` shared-memory buffers filled by 1-D bulk TMA
-// copies (one elected thread issues A's rows, w, param and kind of a tile and
-// arms the stage's mbarrier with the byte count); the ragged tail (n mod 256
-// jobs) is handled by one CTA, its rows staged in the idle stage 0.  For every
-// job the callee receives job(i, valid, row, kind, w, p, warp_rows): row points
-// at the job's m efficiencies in shared memory, warp_rows at the 32 x
-// m block of rows the calling warp owns (tile rows or idle stage-0 space),
-// which the callee may overwrite once it has read its own row.  All 256
-// threads call job for every tile, valid or not, so warp collectives work.
-// Returns false if a bounded wait gave up (the status word is then set).
+// in through a ring of `stages` shared-memory buffers (ring_stage_bytes(m)
+// apart) filled by 1-D bulk TMA copies (one elected thread issues A's rows,
+// w, param and kind of a tile -- and, when rec_t is set, the tile's records
+// rec_t / rec_j -- and arms the stage's mbarrier with the byte count); the
+// ragged tail (n mod 256 jobs) is handled by one CTA, its rows staged in the
+// idle stage 0.  For every job the callee receives job(i, valid, row, kind,
+// w, p, warp_rows, rec): row points at the job's m efficiencies in shared
+// memory, warp_rows at the 32 x m block of rows the calling warp owns (tile
+// rows or idle stage-0 space), which the callee may overwrite once it has
+// read its own row, and rec at the tile's staged records (NULL for the tail
+// or without records).  All 256 threads call job for every tile, valid or
+// not, so warp collectives work.  Returns false if a bounded wait gave up
+// (the status word is then set).
 struct NoPrologue {
     __device__ void operator()() const {}
 };
 template <int MT, class Job, class Pre = NoPrologue>
 __device__ bool stream_jobs(const float *A, const float *W, const float *Par, const uint8_t *Kind,
-                            long long n, int m, int stages, long long num_full,
-                            unsigned char *smem, uint64_t *bars, int *status, Job &&job,
-                            Pre &&pre = Pre{})
+                            const float2 *rec_t, const uchar2 *rec_j, long long n, int m,
+                            int stages, long long num_full, unsigned char *smem, uint64_t *bars,
+                            int *status, Job &&job, Pre &&pre = Pre{})
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t a_bytes = StageLayout<MT>::a_bytes(m);
-    const size_t st_bytes = StageLayout<MT>::bytes(m);
+    const size_t core_bytes = StageLayout<MT>::bytes(m);
+    const size_t st_bytes = ring_stage_bytes(m);
+    const bool recs = rec_t != nullptr;
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
@@ -970,11 +990,16 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
         const int st = static_cast<int>(it % stages);
         unsigned char *base = smem + st * st_bytes;
         const long long j0 = tile * kTile;
-        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
+        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(core_bytes + (recs ? kRecBytes : 0)));
         bulk_load(base, A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
         bulk_load(base + a_bytes, W + j0, kTile * 4, &bars[st]);
         bulk_load(base + a_bytes + kTile * 4, Par + j0, kTile * 4, &bars[st]);
         bulk_load(base + a_bytes + kTile * 8, Kind + j0, kTile, &bars[st]);
+        if (recs) {
+            bulk_load(base + core_bytes, rec_t + j0, kTile * sizeof(float2), &bars[st]);
+            bulk_load(base + core_bytes + kTile * sizeof(float2), rec_j + j0, kTile * sizeof(uchar2),
+                      &bars[st]);
+        }
     };
     if (tid == 0)
         for (int s = 0; s < stages; ++s) issue(s);
@@ -1001,7 +1026,7 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
         const uint8_t *k_s = base + a_bytes + kTile * 8;
         const long long i = (blockIdx.x + it * G) * kTile + tid;
         job(i, true, a_s + tid * m, static_cast<int>(k_s[tid]), w_s[tid], p_s[tid],
-            a_s + warp * 32 * m);
+            a_s + warp * 32 * m, recs ? base + core_bytes : nullptr);
         __syncthreads();  // stage fully consumed
         if (tid == 0) {
             fence_proxy_async();
@@ -1018,7 +1043,8 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
         for (int k = 0; k < m; ++k) own[k] = valid ? A[i * m + k] : 0.0f;
         __syncthreads();
         job(i, valid, own, valid ? static_cast<int>(Kind[i]) : RA_U_LINCAP,
-            valid ? W[i] : 1.0f, valid ? Par[i] : 0.0f, scratch + warp * 32 * m);
+            valid ? W[i] : 1.0f, valid ? Par[i] : 0.0f, scratch + warp * 32 * m,
+            static_cast<const unsigned char *>(nullptr));
     }
     return true;
 }
@@ -1068,7 +1094,6 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     __shared__ __align__(16) float mu_s[RA_MAX_M];
     __shared__ float s_s[RA_MAX_M];
     __shared__ float sl_s[RA_MAX_M];
-    __shared__ FF red[kWarps][kPartW];
     __shared__ double lamd_s[RA_MAX_M], Rd_s[RA_MAX_M];
     __shared__ double lr_s;
 
@@ -1106,14 +1131,19 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
 
     KahanF hsum, uxsum, lbsum, racc, rlin;
     auto job = [&](long long i, bool valid, const float *row, int kind, float w, float p,
-                   float *warp_rows) {
-        // the previous evaluation's record is read first so that its latency
-        // overlaps this job's solve
+                   float *warp_rows, const unsigned char *rec) {
+        // the previous evaluation's record: staged with the tile, or (ragged
+        // tail) read first so that its latency overlaps this job's solve
         float2 tp = make_float2(0.f, 0.f);
         uchar2 jp = make_uchar2(255, 255);
         if (LAG && lag && valid) {
-            tp = lbt_prev[i];
-            jp = lbj_prev[i];
+            if (rec != nullptr) {
+                tp = reinterpret_cast<const float2 *>(rec)[tid];
+                jp = reinterpret_cast<const uchar2 *>(rec + kTile * sizeof(float2))[tid];
+            } else {
+                tp = lbt_prev[i];
+                jp = lbj_prev[i];
+            }
         }
         JobSol<float> s;
         s.cP = s.cQ = -1;
@@ -1141,12 +1171,13 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
             warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, s, racc);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
-    stream_jobs<MT>(P.A, P.w, P.param, P.kind, P.n, m, stages, num_full, smem, bars, P.status, job,
-                    [&] {
+    stream_jobs<MT>(P.A, P.w, P.param, P.kind, (LAG && lag) ? lbt_prev : nullptr,
+                    (LAG && lag) ? lbj_prev : nullptr, P.n, m, stages, num_full, smem, bars,
+                    P.status, job, [&] {
                         if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
                     });
     reduce_and_finalize(ff_of(hsum), ff_of(uxsum), ff_of(lbsum), ff_of(racc), ff_of(rlin), m,
-                        !CAP && REC, grouped ? (lane / MT == 0) : true, P, red, &lr_s);
+                        !CAP && REC, grouped ? (lane / MT == 0) : true, P, ring_red(smem), &lr_s);
 }
 
 // Initial prices, Eq. e-initialization:
@@ -1162,7 +1193,6 @@ __global__ void __launch_bounds__(kTile, 2)
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ float x0_s[RA_MAX_M];
-    __shared__ FF red[kWarps][kPartW];
     const int tid = threadIdx.x, lane = tid & 31;
     const bool grouped = (m == MT);
     constexpr int C = MT / 4;
@@ -1180,7 +1210,7 @@ __global__ void __launch_bounds__(kTile, 2)
     for (int k = 0; k < MT; ++k) x0_r[k] = x0_s[colof<MT>(k, rot)];
     KahanF racc;
     auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
-                   float *warp_rows) {
+                   float *warp_rows, const unsigned char *) {
         float a[MT];
         load_row<MT>(a, row, A, i, valid, m, grouped, rot);
         float tc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1209,8 +1239,10 @@ __global__ void __launch_bounds__(kTile, 2)
         warp_colsum<MT, float, KahanF>(warp_rows, m, lane, grouped, racc);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
-    stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job);
+    stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
+                    job);
     const FF z = red_zero<FF>();
+    FF(*red)[kPartW] = ring_red(smem);
     if (grid_reduce(z, z, z, ff_of(racc), z, m, false, grouped ? (lane / MT == 0) : true, partials,
                     ticket, red))
         if (tid < m) lam1[tid] = to_double(red[0][4 + tid]) / static_cast<double>(n);
@@ -1230,7 +1262,6 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ __align__(16) float la_s[RA_MAX_M], ma_s[RA_MAX_M], lb_s[RA_MAX_M], mb_s[RA_MAX_M];
-    __shared__ FF red[kWarps][kPartW];
     __shared__ double lr_s[2];
     __shared__ double lad_s[RA_MAX_M], lbd_s[RA_MAX_M], Rd_s[RA_MAX_M];
     const int tid = threadIdx.x;
@@ -1249,7 +1280,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     __syncthreads();
     KahanF ha, hb;
     auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
-                   float *warp_rows) {
+                   float *warp_rows, const unsigned char *) {
         (void)i;
         (void)warp_rows;
         if (!valid) return;
@@ -1260,13 +1291,15 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         hb.add(sb.h);
     };
     unsigned char *smem = align128<MT>(smem_dyn);
-    stream_jobs<MT>(A, w, param, kind, n, m, stages, num_full, smem, bars, status, job, [&] {
-        if (tid == 32) {
-            lr_s[0] = lam_dot_R(lad_s, Rd_s, m);
-            lr_s[1] = lam_dot_R(lbd_s, Rd_s, m);
-        }
-    });
+    stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
+                    job, [&] {
+                        if (tid == 32) {
+                            lr_s[0] = lam_dot_R(lad_s, Rd_s, m);
+                            lr_s[1] = lam_dot_R(lbd_s, Rd_s, m);
+                        }
+                    });
     const FF z = red_zero<FF>();
+    FF(*red)[kPartW] = ring_red(smem);
     if (grid_reduce(ff_of(ha), ff_of(hb), z, z, z, 0, false, true, partials, ticket, red) &&
         tid == 0) {
         g_out[0] = lr_s[0] + to_double(red[0][0]);
@@ -1926,7 +1959,7 @@ cudaError_t set_attrs_mt()
     cudaError_t e;
 #define RA_ATTR(L, R)                                                                              \
     e = cudaFuncSetAttribute(dual_tma_kernel<MT, CAP, L, R>,                                      \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);            \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemMax);            \
     if (e != cudaSuccess) return e;
     RA_ATTR(false, false)
     RA_ATTR(false, true)
@@ -1955,19 +1988,19 @@ cudaError_t configure_dual(ra_problem *p)
     const int m = p->m;
     p->mt = m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
     const bool cap = !(p->flags & RA_NO_JOB_CAP);
-    const size_t budget = cap ? 106 * 1024 : 70 * 1024;   // two / three CTAs per SM
-    switch (p->mt) {
-    case 4: p->stages = mt_stages<4>(m, budget); break;
-    case 8: p->stages = mt_stages<8>(m, budget); break;
-    case 16: p->stages = mt_stages<16>(m, budget); break;
-    default: p->stages = mt_stages<32>(m, budget); break;
-    }
-    const size_t sb = StageLayout<4>::bytes(m);  // layout does not depend on MT
+    // two / three CTAs per SM; a stage also holds the tile's 2.5 KB of records
+    const size_t budget = cap ? 111 * 1024 : 70 * 1024;
+    const size_t sb = ring_stage_bytes(m);  // layout does not depend on MT
+    int stages = static_cast<int>(budget / sb);
+    if (stages > kMaxStages) stages = kMaxStages;
+    if (stages < 2) stages = 2;
+    p->stages = stages;
     p->smem_dual = p->stages * sb + 128;
+    if (p->smem_dual < kWarps * kPartW * sizeof(FF) + 128) p->smem_dual = kWarps * kPartW * sizeof(FF) + 128;
     cudaError_t e;
 #define RA_IATTR(MT)                                                                               \
     if ((e = cudaFuncSetAttribute(init_tma_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                  110 * 1024)) != cudaSuccess)                                     \
+                                  kRingSmemMax)) != cudaSuccess)                                     \
         return e;
     RA_IATTR(4)
     RA_IATTR(8)
@@ -1976,11 +2009,11 @@ cudaError_t configure_dual(ra_problem *p)
 #undef RA_IATTR
 #define RA_GATTR(MT)                                                                               \
     if ((e = cudaFuncSetAttribute(dual_g2_kernel<MT, true>,                                       \
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemMax)) !=     \
         cudaSuccess)                                                                               \
         return e;                                                                                  \
     if ((e = cudaFuncSetAttribute(dual_g2_kernel<MT, false>,                                      \
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemMax)) !=     \
         cudaSuccess)                                                                               \
         return e;
     RA_GATTR(4)
@@ -2158,11 +2191,11 @@ cudaError_t batch_configure(int mt, int cap, int *blocks_per_sm)
     cudaError_t e;
 #define RA_BATTR(MT)                                                                               \
     if ((e = cudaFuncSetAttribute(batch_dual_kernel<MT, true>,                                    \
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemMax)) !=     \
         cudaSuccess)                                                                               \
         return e;                                                                                  \
     if ((e = cudaFuncSetAttribute(batch_dual_kernel<MT, false>,                                   \
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024)) !=     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemMax)) !=     \
         cudaSuccess)                                                                               \
         return e;
     RA_BATTR(4)
