@@ -27,7 +27,9 @@
  *                    points (0,0), (a_j, lam_j) defines an affine cost on
  *                    [a_P, a_Q] (Eqs. e-xixj, e-optcostij); maximise u minus
  *                    each affine piece on its interval and keep the best.
- *                    This is the definition, O(m^2) per job.
+ *                    This is the definition, O(m^2) per job.  Without the
+ *                    cap the pieces are the rays from the origin through
+ *                    each point, O(m) per job (job_rays).
  *   ora_job_hull  -- Section 4.1 kink-point form: build the lower convex hull
  *                    c(t) of the same points, then walk its segments left to
  *                    right applying Eq. e-opt-t-log / e-opt-t-target on each
@@ -58,7 +60,7 @@
 
 enum { K_LOG = 0, K_POWER = 1, K_LINCAP = 2, K_TARGET = 3 };
 
-int ora_version(void) { return 3; }
+int ora_version(void) { return 4; }
 
 /* u(t), Section 2.2. */
 static double util(int kind, double w, double par, double t)
@@ -182,11 +184,45 @@ static void job_nocap(int m, const double *a, const double *lam, int kind, doubl
     double alpha = lam[js] / a[js];
     double t = argmax_interval(kind, w, par, alpha, 0.0, INFINITY);
     o[0] = t;
-    o[1] = util(kind, w, par, t) - alpha * t;
+    /* a free resource (alpha = 0) leaves a strictly increasing utility's
+     * demand unbounded: the supremum, and so g, is +inf (Section 3) */
+    o[1] = isinf(t) ? INFINITY : util(kind, w, par, t) - alpha * t;
     o[2] = js;
     if (t > 0.0) { o[3] = js; o[5] = t / a[js]; }
     o[8] = tie;
     if (kind >= K_LINCAP) o[9] = fabs(w - alpha) / fmax(alpha, 1e-300);
+}
+
+/* Algorithm 1 without the per-job cap, read literally: with 1^T x <= 1
+ * dropped, each point (a_j, lam_j) spans a ray t -> (t / a_j) lam_j from the
+ * origin, and c(t) is their pointwise minimum; maximise u minus each ray over
+ * t >= 0 and keep the best (larger value, then smaller t, then larger a_j,
+ * then lower j).  An independent reading of the same subproblem as
+ * job_nocap, which goes straight to the cheapest ray. */
+static void job_rays(int m, const double *a, const double *lam, int kind, double w, double par,
+                     double *o)
+{
+    set_empty(o);
+    double tie;
+    o[2] = ratio_argmin(m, a, lam, &tie);
+    o[7] = tie;
+    double best = -INFINITY, bt = 0.0, balpha = 0.0;
+    int bj = -1;
+    for (int j = 0; j < m; ++j) {
+        if (!(a[j] > 0.0)) continue;
+        double alpha = lam[j] / a[j];
+        double t = argmax_interval(kind, w, par, alpha, 0.0, INFINITY);
+        double v = isinf(t) ? INFINITY : util(kind, w, par, t) - alpha * t;
+        int take = bj < 0 || v > best ||
+                   (v == best && (t < bt || (t == bt && a[j] > a[bj])));
+        if (take) { best = v; bt = t; bj = j; balpha = alpha; }
+    }
+    if (bj < 0) { o[0] = 0.0; o[1] = util(kind, w, par, 0.0); return; }
+    o[0] = bt;
+    o[1] = best;
+    if (bt > 0.0) { o[3] = bj; o[5] = bt / a[bj]; }
+    o[8] = tie;
+    if (kind >= K_LINCAP) o[9] = fabs(w - balpha) / fmax(balpha, 1e-300);
 }
 
 /* Algorithm 1 read literally: maximise u minus every pairwise affine piece
@@ -196,7 +232,7 @@ static void job_nocap(int m, const double *a, const double *lam, int kind, doubl
 void ora_job_pairs(int m, const double *a, const double *lam, int kind, double w, double par,
                    int cap, double *o)
 {
-    if (!cap) { job_nocap(m, a, lam, kind, w, par, o); return; }
+    if (!cap) { job_rays(m, a, lam, kind, w, par, o); return; }
     set_empty(o);
     double tie;
     o[2] = ratio_argmin(m, a, lam, &tie);

@@ -18,7 +18,7 @@ import os
 
 import numpy as np
 import pytest
-from scipy.optimize import linprog, minimize
+from scipy.optimize import linprog, minimize, minimize_scalar
 
 from paper_2104_00282_gb300 import workloads as W
 
@@ -161,6 +161,119 @@ def test_subproblem_against_generic_solvers(oracle):
             best = max(_u(kind, w, p, t) - _lp_cost(a, lam, t)[0]
                        for t in cands if 0 <= t <= a.max())
             assert ref["h"] == pytest.approx(best, abs=1e-9)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_uncapped_subproblem_against_generic_solvers(oracle, kind):
+    """Without the per-job cap the subproblem is max_{x >= 0} u(a^T x) - lam^T x.
+    The cost of one unit of throughput c1 = min lam^T x s.t. a^T x = 1, x >= 0
+    comes from scipy's LP solver; then strictly concave kinds are maximised
+    over t by a bounded scalar search on log t, and the piecewise-linear
+    kinds (concave, kinks at T only) by comparing t = 0 with t = T.  Both
+    cases w < c1 (stay idle) and w > c1 (run to T) are drawn."""
+    rng = np.random.default_rng(40 + kind)
+    idle = busy = 0
+    for trial in range(150):
+        m = int(rng.integers(1, 6))
+        a = rng.uniform(0.1, 1.5, m)
+        lam = rng.uniform(0.05, 2.0, m)
+        w = rng.uniform(0.1, 3.0)
+        p = rng.uniform(0.2, 0.8) if kind == 1 else rng.uniform(0.1, 2.0)
+        lp = linprog(c=lam, A_eq=a[None, :], b_eq=[1.0], bounds=[(0, None)] * m, method="highs")
+        assert lp.status == 0
+        c1 = lp.fun
+        for method in ("hull", "pairs"):
+            ref = oracle.job(a, lam, kind, w, p, False, method)
+            if kind in (0, 1):
+                f = lambda s: -(_u(kind, w, p, math.exp(s)) - c1 * math.exp(s))
+                res = minimize_scalar(f, bounds=(-40.0, 40.0), method="bounded",
+                                      options=dict(xatol=1e-12))
+                assert ref["h"] == pytest.approx(-res.fun, rel=1e-9, abs=1e-12)
+                assert ref["t"] == pytest.approx(math.exp(res.x), rel=1e-5)
+            else:
+                v0, vT = _u(kind, w, p, 0.0), _u(kind, w, p, p) - c1 * p
+                assert ref["h"] == pytest.approx(max(v0, vT), rel=1e-12, abs=1e-12)
+                if abs(w - c1) > 1e-9 * c1:
+                    assert ref["t"] == (p if vT > v0 else 0.0)
+                    idle += vT < v0
+                    busy += vT > v0
+            # x spends on the cheapest resource only: lam^T x = c1 t, a^T x = t
+            x = np.zeros(m)
+            if ref["j1"] >= 0:
+                x[ref["j1"]] = ref["x1"]
+            assert ref["j2"] == -1
+            assert float(a @ x) == pytest.approx(ref["t"], rel=1e-12, abs=1e-15)
+            assert float(lam @ x) == pytest.approx(c1 * ref["t"], rel=1e-9, abs=1e-15)
+    if kind >= 2:
+        assert idle > 20 and busy > 20
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bruteforce_primal_tiny_uncapped(oracle, seed):
+    """Strong duality without the per-job cap, all four utility kinds: the
+    primal max sum_i u_i(a_i^T x_i) over X >= 0, X^T 1 <= R, solved by SLSQP
+    in epigraph form (s_i <= each smooth piece of u_i), equals the oracle's
+    dual minimum; g bounds it from above and U_lb from below.  One job with a
+    small weight makes a linear-with-cap job stay idle at the optimum."""
+    rng = np.random.default_rng(200 + seed)
+    n, m = 6, 3
+    A = rng.uniform(0.2, 1.0, (n, m)).astype(np.float32)
+    kind = np.array([0, 1, 2, 3, 2, 0], np.uint8)
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    w[4] = 0.02
+    par = np.zeros(n, np.float32)
+    par[1] = rng.uniform(0.3, 0.7)
+    par[2], par[3], par[4] = rng.uniform(0.2, 0.6, 3)
+    R = rng.uniform(0.4, 1.2, m)
+    p = W.Problem(A, kind, w, par, R)
+    Af = A.astype(float)
+    nx = n * m
+
+    def t_of(z, i):
+        return float(Af[i] @ z[i * m:(i + 1) * m])
+
+    cons = [{"type": "ineq", "fun": lambda z, j=j: R[j] - z[:nx].reshape(n, m)[:, j].sum()}
+            for j in range(m)]
+    for i in range(n):
+        k, wi, pi = int(kind[i]), float(w[i]), float(par[i])
+        s = lambda z, i=i: z[nx + i]
+        if k == 0:
+            cons.append({"type": "ineq", "fun": lambda z, i=i, wi=wi: wi * math.log(max(t_of(z, i), 1e-300)) - z[nx + i]})
+        elif k == 1:
+            cons.append({"type": "ineq", "fun": lambda z, i=i, wi=wi, pi=pi: wi * max(t_of(z, i), 0.0) ** pi - z[nx + i]})
+        elif k == 2:
+            cons.append({"type": "ineq", "fun": lambda z, i=i, wi=wi: wi * t_of(z, i) - z[nx + i]})
+            cons.append({"type": "ineq", "fun": lambda z, i=i, wi=wi, pi=pi: wi * pi - z[nx + i]})
+        else:
+            cons.append({"type": "ineq", "fun": lambda z, i=i, wi=wi, pi=pi: wi * (t_of(z, i) - pi) - z[nx + i]})
+            cons.append({"type": "ineq", "fun": lambda z, i=i: -z[nx + i]})
+    best = -np.inf
+    for _ in range(10):
+        X0 = rng.uniform(0.01, 0.1, nx)
+        s0 = np.array([(_u(int(kind[i]), float(w[i]), float(par[i]), t_of(X0, i)) if kind[i] != 1
+                        else 0.0) - 1.0 for i in range(n)])
+        res = minimize(lambda z: -z[nx:].sum(), np.concatenate([X0, s0]), method="SLSQP",
+                       bounds=[(1e-12, None)] * nx + [(-50, None)] * n, constraints=cons,
+                       options=dict(ftol=1e-15, maxiter=3000))
+        if res.success and min(c["fun"](res.x) for c in cons) > -1e-9:
+            Xs = res.x[:nx].reshape(n, m)
+            U = sum(_u(int(kind[i]), float(w[i]), float(par[i]), float(Af[i] @ Xs[i]))
+                    for i in range(n))
+            best = max(best, U)
+    assert np.isfinite(best)
+    sol = oracle.solve(p, cap=False, tol=1e-12, max_evals=400)
+    assert sol.g >= best - 1e-8 * max(1.0, abs(best))          # weak duality
+    assert sol.U_lb <= best + 1e-8 * max(1.0, abs(best))
+    # zero gap: min_{lam >= 0} g(lam) by a derivative-free search (g has
+    # kinks at the optimum, where n = 6 jobs tie between resources)
+    gfun = lambda lam: oracle.dual(p, np.abs(lam), cap=False)[0]
+    g_min, x = np.inf, sol.lam
+    for _ in range(4):
+        res = minimize(gfun, x, method="Nelder-Mead",
+                       options=dict(xatol=1e-13, fatol=1e-15, maxiter=20000, maxfev=20000))
+        x = np.abs(res.x)
+        g_min = min(g_min, res.fun)
+    assert g_min == pytest.approx(best, rel=1e-7, abs=1e-8)
 
 
 def test_interior_optimum_meets_marginal_utility(oracle):
