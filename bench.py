@@ -132,54 +132,84 @@ def ncu_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+ORACLE_MAX_EVALS = 2000
+REF_BUDGET_S = 120.0        # host seconds the whole --impl reference run may take
+ORACLE_US_PER_JOB = 4.0     # oracle solve time per job of the workload (16 host cores)
+
+
+def oracle_sample_size(steps, warmup):
+    """Jobs in the oracle's sample: the reference arm solves it once per step
+    (warm-up included) within about REF_BUDGET_S; the GPU arm's cpu_baseline
+    leg uses the same size for the same --steps/--warmup, so the two oracle
+    figures of one run describe the same computation."""
+    per_step = REF_BUDGET_S / max(steps + warmup, 1)
+    n = int(per_step / (ORACLE_US_PER_JOB * 1e-6))
+    return int(min(max(n, 500_000), 2_000_000) // 100_000 * 100_000)
+
+
 def cpu_baseline(sample_n, seed=0, cap=False):
-    """Oracle solve (FP64, OpenMP, scipy L-BFGS-B) on the first sample_n jobs
-    of the workload with R scaled to the sample; returns (ms for the sample,
-    ms scaled linearly to n = 1e7, threads, evals)."""
+    """Oracle solve (FP64, OpenMP, scipy L-BFGS-B) of the first sample_n jobs
+    of the workload with R scaled to the sample, to the same 1e-6 relative
+    gap; returns a dict with the time for the sample, the time scaled
+    linearly to n = 1e7, the thread count, the evaluations, the gap reached
+    and whether it converged (an unconverged time is flagged, not hidden)."""
     from oracle import oracle as O
     from paper_2104_00282_gb300 import workloads as W
     prob = W.config_large(n=sample_n, m=M_RES, seed=seed)
     t0 = time.perf_counter()
-    sol = O.solve(prob, cap=cap, tol=TOL, max_evals=400)
+    sol = O.solve(prob, cap=cap, tol=TOL, max_evals=ORACLE_MAX_EVALS)
     dt = (time.perf_counter() - t0) * 1e3
-    return dt, dt * (N_JOBS / sample_n), O.max_threads(), sol.evals, sol.gap
+    return dict(ms=dt, scaled=dt * (N_JOBS / sample_n), threads=O.max_threads(), evals=sol.evals,
+                gap=sol.gap, converged=bool(sol.converged), sample_n=sample_n)
 
 
-def _sample_size(seconds, cap):
-    """Jobs of the workload the oracle solves in about `seconds` on 16 host
-    cores: measured about 2.5 us per job and solve with the per-job cap (about
-    ten evaluations) and about 60 us without it (a few hundred); >= 1e5."""
-    n = int(seconds / (2.5e-6 if cap else 6e-5))
-    return int(min(max(n, 100_000), N_JOBS) // 1000 * 1000)
+def _sample_text(r):
+    return (f"oracle solve of the first {r['sample_n']} jobs of the workload (seed 0, R scaled to the "
+            f"sample) to a {TOL:g} relative gap: {r['evals']} evaluations, gap {r['gap']:.2e}, "
+            f"{'converged' if r['converged'] else 'NOT converged'}, {r['ms']:.0f} ms; "
+            f"time scaled x{N_JOBS / r['sample_n']:g} to n=1e7 (linear in n)")
 
 
 def run_reference(args):
     dist, rank, ws = _dist()
     if rank != 0:
         return
-    # bounded so that the whole --steps/--warmup run ends within about three minutes
-    sample_n = args.cpu_sample or _sample_size(min(20.0, 180.0 / max(args.steps + args.warmup, 1)),
-                                               args.job_cap)
-    vals = []
-    evals = gap = threads = None
+    sample_n = args.cpu_sample or oracle_sample_size(args.steps, args.warmup)
+    vals, runs = [], []
     for k in range(args.warmup + args.steps):
-        _, scaled, threads, evals, gap = cpu_baseline(sample_n, seed=0, cap=args.job_cap)
+        r = cpu_baseline(sample_n, seed=0, cap=args.job_cap)
         if k >= args.warmup:
-            vals.append(scaled)
+            vals.append(r["scaled"])
+            runs.append(r)
     v = statistics.median(vals)
+    last = runs[-1]
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_JOBS, "m": M_RES, "tol_rel": TOL,
                    "job_cap": args.job_cap},
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": threads, "kind": "oracle",
-                         "sample": f"oracle solve of the first {sample_n} jobs (R scaled), "
-                                   f"{evals} evaluations to gap {gap:.2e}, time scaled x{N_JOBS // sample_n} "
-                                   f"to n=1e7 (linear in n)"},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": last["threads"], "kind": "oracle",
+                         "converged": all(r["converged"] for r in runs), "gap": last["gap"],
+                         "sample": _sample_text(last)},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def certify_headline(prob, P, cap):
+    """FP64 oracle check of a GPU solve of the full workload: g at the GPU's
+    best prices, the utility of the GPU's lower-bound allocation rebuilt by
+    the oracle, the relative gap between them, the worst usage / R of that
+    allocation, and the GPU's own g and U_lb against the oracle's."""
+    from oracle import oracle as O
+    import numpy as np
+    lam = P.prices.cpu().numpy()
+    theta, lams, scaled = P.certificate()
+    c = O.certify(prob, lam, theta, lams, scaled, cap)
+    return {"rel_gap_oracle": c["rel_gap"], "g_oracle": c["g"], "U_lb_oracle": c["U_lb"],
+            "max_usage_over_R": c["max_usage_over_R"], "oracle_seconds": c["seconds"],
+            "certificate_entries": int(np.sum(np.asarray(theta) > 0))}
 
 
 def run_gpu(args):
@@ -233,6 +263,10 @@ def run_gpu(args):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
+
+    # FP64 oracle certificate of the last timed solve (error against the oracle
+    # stated for the headline result)
+    cert = certify_headline(prob, P, cap) if (rank == 0 and not args.no_certify) else None
 
     # roofline of one dual evaluation (the dominant kernel), CUDA events on its stream
     lam0 = P.init_prices()
@@ -297,6 +331,33 @@ def run_gpu(args):
     other = {"ms": statistics.median(o_times), "evals": o_info["evals"],
              "rel_gap": o_info["rel_gap"], "status": o_info["status"]}
 
+    # precision study: the same workload with FP64 per-job arithmetic
+    # (RA_FP64_JOBMATH), timed and certified by the oracle like the headline
+    prec = None
+    if args.fp64_study:
+        with torch.cuda.stream(stream):
+            P64 = ra.AllocationProblem.from_numpy(prob, dev, stream=stream, job_cap=cap,
+                                                  fp64_jobmath=True)
+        p_times, p_info = [], None
+        for k in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            p_info = P64.solve(tol=TOL, max_evals=args.max_evals, use_graph=use_graph)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                p_times.append(e0.elapsed_time(e1))
+        c64 = certify_headline(prob, P64, cap) if (rank == 0 and not args.no_certify) else None
+        P64.close()
+        prec = {"fp32_jobmath": {"ms": ms, "evals": infos[-1]["evals"],
+                                 "rel_gap_gpu": infos[-1]["rel_gap"], "oracle": cert},
+                "fp64_jobmath": {"ms": statistics.median(p_times), "evals": p_info["evals"],
+                                 "rel_gap_gpu": p_info["rel_gap"], "status": p_info["status"],
+                                 "oracle": c64},
+                "note": "per-job arithmetic in FP32 (headline) or FP64; reductions, dual value "
+                        "and price update FP64 in both; each result re-checked by the FP64 oracle"}
+
     batch = run_batch(args, dev, stream) if args.batch > 0 else None
     warm = run_warm(args) if args.warm > 0 else None
 
@@ -304,12 +365,10 @@ def run_gpu(args):
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        sample_n = args.cpu_sample or _sample_size(12.0, cap)
-        dt, scaled, threads, evals, gap = cpu_baseline(sample_n, cap=cap)
-        cpu = {"value": scaled, "unit": "ms", "cores": threads, "kind": "oracle",
-               "sample": f"oracle solve of the first {sample_n} jobs of the workload "
-                         f"(R scaled) took {dt:.0f} ms, {evals} evaluations, gap {gap:.2e}; "
-                         f"scaled x{N_JOBS / sample_n:g} to n=1e7 (linear in n)"}
+        sample_n = args.cpu_sample or oracle_sample_size(args.steps, args.warmup)
+        r = cpu_baseline(sample_n, cap=cap)
+        cpu = {"value": r["scaled"], "unit": "ms", "cores": r["threads"], "kind": "oracle",
+               "converged": r["converged"], "gap": r["gap"], "sample": _sample_text(r)}
     evals = [i["evals"] for i in infos]
     # per solve: initialisation + setup, then per evaluation: dual pass, solver step
     launches = sum(2 + 2 * e for e in evals)
@@ -324,7 +383,9 @@ def run_gpu(args):
                    "precision": "per-job math f32; reductions, dual value, price update f64"},
         "solve": {"evals_median": statistics.median(evals), "rel_gap": infos[-1]["rel_gap"],
                   "status": infos[-1]["status"], "ms_per_eval_in_solve": ms / statistics.median(evals),
-                  "step_ms_all": times},
+                  "g": infos[-1]["g"], "U_lb": infos[-1]["U_lb"],
+                  "oracle_certificate": cert, "step_ms_all": times},
+        "precision_study": prec,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(),
                      "kernel": f"dual_tma_kernel, {'with' if cap else 'no'} per-job cap "
@@ -407,6 +468,52 @@ def run_batch(args, dev, stream):
                         "e-res-alloc), cold start to 1e-6 relative gap, at most 500 evaluations"}
 
 
+def run_profile(args):
+    """Small, self-contained workloads for a profiler (ncu), one per kind of
+    launch: ``eval`` runs --reps standalone dual evaluations (ra_eval_dual) at
+    the Eq. e-initialization prices of the large recipe (n = --n, m = --m);
+    ``solve`` one solve with the host-driven loop, so that every launch is a
+    separate kernel the profiler can see (inside a CUDA graph's conditional
+    node it cannot); ``batch`` one batched solve of the batched workload's
+    first --problems problems with the host loop; ``warm`` one warm-started
+    solve (statistics, network, start prices, solve) of a held-out problem of
+    the warm-start recipe (n = --n, m = 16)."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_2104_00282_gb300 import ra
+    from paper_2104_00282_gb300 import workloads as W
+    what = args.profile
+    if what in ("eval", "solve"):
+        prob = W.config_large(n=args.n, m=args.m, seed=0)
+        P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=args.job_cap)
+        if what == "eval":
+            lam = P.init_prices()
+            for _ in range(args.reps):
+                ra.ra_eval_dual(P.handle, lam)
+            out = f"{args.reps} evaluations"
+        else:
+            out = P.solve(tol=TOL, max_evals=args.max_evals, use_graph=False)
+        P.close()
+    elif what == "batch":
+        probs = W.batched_workload(args.problems)
+        B = ra.AllocationBatch(probs, job_cap=True)
+        infos, _ = B.solve(tol=TOL, max_evals=BATCH_MAX_EVALS, use_graph=False)
+        out = f"{sum(i['status'] == 0 for i in infos)} of {len(infos)} converged"
+        B.close()
+    else:
+        from paper_2104_00282_gb300 import warmstart as WS
+        net = WS.load()
+        A, kind, w, param, R = W.hetero_device(args.n, 16, WS.EVAL_SEED, 5, "cuda")
+        P = ra.AllocationProblem(A, kind, w, param, R, job_cap=False)
+        lam0, used = P.warm_prices(net)
+        out = P.solve(tol=TOL, max_evals=BATCH_MAX_EVALS, lam0=lam0, use_graph=False)
+        P.close()
+        net.close()
+    torch.cuda.synchronize()
+    print("profile", what, out, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,6 +521,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_JOBS)
+    ap.add_argument("--m", type=int, default=M_RES, help="resources (--profile eval/solve only)")
+    ap.add_argument("--profile", choices=["eval", "solve", "batch", "warm"], default=None,
+                    help="run one small workload for a profiler instead of the benchmark")
+    ap.add_argument("--reps", type=int, default=6, help="evaluations of --profile eval")
+    ap.add_argument("--problems", type=int, default=512, help="problems of --profile batch")
     ap.add_argument("--max-evals", type=int, default=400)
     ap.add_argument("--cpu-sample", type=int, default=0, help="jobs in the oracle sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -423,10 +535,16 @@ def main():
                     help="host-driven solver loop (same kernels; lets ncu see every launch)")
     ap.add_argument("--warm", type=int, default=200,
                     help="held-out problems in the warm-start comparison (0 = skip)")
+    ap.add_argument("--no-certify", action="store_true",
+                    help="skip the FP64 oracle re-check of the headline solve")
+    ap.add_argument("--fp64-study", type=int, default=1,
+                    help="1 = also solve the workload with FP64 per-job arithmetic (precision study)")
     ap.add_argument("--batch", type=int, default=4096,
                     help="problems in the batched solve reported beside the headline (0 = skip)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -96,10 +96,18 @@ void ra_problem_destroy(ra_problem *prob);
  *   g       1 FP64 output (may be NULL)
  *   q       m FP64 output (may be NULL)
  *   U_lb    1 FP64 output or NULL: utility of the column-scaled feasible
- *           allocation X diag(min(1, R/r)) (Section 5); costs a second,
- *           lighter pass over the jobs.
+ *           allocation (Section 5); costs a second, lighter pass over the
+ *           jobs.  With the per-job cap the scaling is the paper's
+ *           X diag(min(1, R/r)).  Without it the columns are scaled to use
+ *           exactly R (up as well as down), except that jobs with a linear
+ *           utility keep their allocation while they use less than R_j and
+ *           the other jobs share what is left of it.
  * Deterministic: identical inputs give bitwise identical outputs on the
- * same GPU (fixed-order two-stage reductions, FP64 across blocks).
+ * same GPU.  Per-thread sums are compensated FP32; the block and grid stages
+ * add float-float pairs (about 44 significant bits) in a fixed order and the
+ * totals are converted to FP64 (with RA_FP64_JOBMATH every stage is FP64).
+ * If a bounded device wait gave up (RA_ETIMEOUT, see ra_set_wait_timeout),
+ * g, q and U_lb are NaN.
  */
 ra_status ra_eval_dual(ra_problem *prob, const double *lambda, double *g, double *q, double *U_lb);
 
@@ -211,14 +219,14 @@ ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jst
 
 /*
  * ra_eval_dual_static -- g(lambda) and q = R - r exactly as ra_eval_dual
- * computes them, but without creating a problem and without allocating any
+ * computes them (the same kernel, launch shape and reduction order, so the
+ * same bits), but without creating a problem and without allocating any
  * device memory.  (The paper has no counterpart; this is a deployment aid.)
  *
- * For callers that must not allocate: code running while a CUDA stream is
- * being captured into a graph (allocation calls break or are refused during
- * capture), latency-bound serving loops with a no-allocation rule (cudaMalloc
- * can synchronise the device), and hosts whose framework owns all device
- * memory through its own pool.
+ * For callers that must not allocate: latency-bound serving loops with a
+ * no-allocation rule (cudaMalloc can synchronise the device and its latency
+ * is unbounded), and hosts whose framework owns all device memory through
+ * its own pool allocator and forbids allocations behind its back.
  *
  * Arguments are those of ra_problem_create plus lambda (m FP64 device prices)
  * and the outputs g (1 FP64, device) and q (m FP64, device); flags may only
@@ -230,13 +238,18 @@ ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jst
  * every GPU that loads libra.so keeps until the process exits.  It holds the
  * per-CTA partial sums of at most 1024 CTAs; a GPU whose evaluation would use
  * more CTAs is refused with RA_EINVAL.  Any n and 1 <= m <= RA_MAX_M are
- * accepted.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * previous call's contents (the kernel's counters are cleared on the stream
- * before each launch): calls whose work overlaps on the GPU -- on different
- * streams or devices sharing a context -- race and must be serialised by the
- * caller.
+ * accepted.  The first call on a device (per m and cap mode) does the
+ * set-up with that device current: it looks up the array's device address
+ * (cudaGetSymbolAddress) and sets the kernels' launch attributes; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the previous call's contents (the kernel's ticket and status word
+ * are cleared on the stream before each launch): calls whose work overlaps
+ * on the GPU -- on different streams or devices sharing a context -- race
+ * and must be serialised by the caller.
+ *
+ * The call returns before the work is done, so it cannot return
+ * RA_ETIMEOUT: when a bounded device wait gives up (ra_set_wait_timeout),
+ * g and q receive NaN instead.
  */
 ra_status ra_eval_dual_static(int64_t n, int32_t m, const float *A, const uint8_t *kind,
                               const float *w, const float *param, const double *R,
@@ -361,6 +374,17 @@ ra_status ra_batch_features(ra_batch *b, float *feats);
  * the cold start's pass; both g values come from one pass over the data.
  */
 ra_status ra_warmstart_prices(ra_problem *prob, ra_mlp *net, double *lambda0, int32_t *used_warm);
+
+/*
+ * ra_set_wait_timeout -- bound of every device-side wait of the library's
+ * kernels (a CTA waiting for its bulk copies), in seconds of device time; 2
+ * by default, process-wide, read when work is enqueued (or captured).  A
+ * kernel whose wait expires records it and returns instead of hanging: the
+ * solvers then report RA_ETIMEOUT and the evaluations' outputs are NaN.  0
+ * makes every such wait give up at once (for testing a caller's handling of
+ * RA_ETIMEOUT).  RA_EINVAL unless 0 <= seconds <= 60.  (Not in the paper.)
+ */
+ra_status ra_set_wait_timeout(double seconds);
 
 /* Static strings; ra_last_error() is thread-local and valid until the next call. */
 const char *ra_status_string(ra_status s);

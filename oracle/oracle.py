@@ -53,6 +53,8 @@ def lib():
         L.ora_jobs.restype = i32
         L.ora_cost.argtypes = [i32, P, P, d, P]
         L.ora_cost.restype = d
+        L.ora_mixture_utility.argtypes = [i64, i32, P, P, P, P, i32, P, P, P, P, i32, i32, P, i32]
+        L.ora_mixture_utility.restype = i32
         _lib = L
     return _lib
 
@@ -219,6 +221,56 @@ def init_prices(prob, cap=True, nthreads=0):
 
 def rel_gap(g, lb):
     return (g - lb) / max(abs(lb), abs(g), 1.0)
+
+
+def mixture_utility(prob, theta, lams, sc_oth, sc_lin, cap=True, method="hull", nthreads=0):
+    """U(sum_k theta_k X(lam_k) diag(sc_k)) in FP64 without forming X: column j
+    of allocation k is scaled by sc_lin[k, j] for jobs with a linear utility
+    and by sc_oth[k, j] otherwise."""
+    A, kind, w, par, _ = _arrays(prob)
+    theta = np.ascontiguousarray(theta, np.float64)
+    lams = np.ascontiguousarray(lams, np.float64).reshape(len(theta), prob.m)
+    so = np.ascontiguousarray(sc_oth, np.float64).reshape(len(theta), prob.m)
+    sl = np.ascontiguousarray(sc_lin, np.float64).reshape(len(theta), prob.m)
+    U = np.zeros(1)
+    rc = lib().ora_mixture_utility(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), len(theta),
+                                   _p(theta), _p(lams), _p(so), _p(sl), int(bool(cap)),
+                                   0 if method == "hull" else 1, _p(U), nthreads)
+    assert rc == 0
+    return float(U[0])
+
+
+def certify(prob, lam_best, theta, lams, scaled, cap=True, nthreads=0):
+    """FP64 re-check of a solver's result (Section 5's bounds): the dual value
+    g at ``lam_best`` (an upper bound on U*), and the utility of the
+    allocation behind the solver's lower bound -- the mixture sum_k theta_k
+    X(lam_k), allocation k column-scaled (``column_scales``) where
+    ``scaled[k]`` -- once more scaled by min(1, R/usage) so that it meets
+    X^T 1 <= R exactly in FP64 (a lower bound on U*).  Returns a dict with g,
+    U_lb, the relative gap, usage / R of the mixture before that last
+    scaling (its worst entry is the solver's constraint violation), and the
+    seconds taken."""
+    t0 = time.perf_counter()
+    R = np.asarray(prob.R, np.float64)
+    lam_best = np.asarray(lam_best, np.float64)
+    g, _, _ = dual(prob, lam_best, cap, nthreads=nthreads)
+    theta = np.asarray(theta, np.float64)
+    lams = np.asarray(lams, np.float64).reshape(len(theta), prob.m)
+    keep = theta > 0
+    theta, lams, scaled = theta[keep], lams[keep], np.asarray(scaled)[keep]
+    so = np.ones_like(lams)
+    sl = np.ones_like(lams)
+    usage = np.zeros(prob.m)
+    for k in range(len(theta)):
+        _, r, _, r_lin = dual(prob, lams[k], cap, nthreads=nthreads, split=True)
+        if scaled[k]:
+            so[k], sl[k] = column_scales(R, r, r_lin, cap)
+        usage += theta[k] * (so[k] * (r - r_lin) + sl[k] * r_lin)
+    f = column_scale(R, usage, cap=True)
+    U = mixture_utility(prob, theta, lams, so * f[None, :], sl * f[None, :], cap, nthreads=nthreads)
+    ratio = np.where(R > 0, usage / np.where(R > 0, R, 1.0), np.where(usage > 0, np.inf, 0.0))
+    return dict(g=g, U_lb=U, rel_gap=rel_gap(g, U), usage_over_R=ratio,
+                max_usage_over_R=float(ratio.max()), seconds=time.perf_counter() - t0)
 
 
 # --------------------------------------------------------------------------- solve

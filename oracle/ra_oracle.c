@@ -535,3 +535,46 @@ void ora_job(int m, const double *a, const double *lam, int kind, double w, doub
 {
     solve_job(m, a, lam, kind, w, par, cap, method, out);
 }
+
+/* Utility of a convex combination of subproblem allocations (Section 5: any
+ * mixture sum_k theta_k X(lam_k) with usage <= R is feasible, and since every
+ * u_i is concave its utility is at least sum_k theta_k U(X(lam_k))):
+ *   t_i = sum_k theta_k sum_j a_ij x_ij(lam_k) sc_k[j],   U = sum_i u_i(t_i),
+ * where sc_k = sc_lin + k*m for jobs with a linear utility (kinds 2, 3) and
+ * sc_oth + k*m otherwise (the column scalings applied to allocation k).
+ * No dense allocation is formed: each job is solved at every lam_k.  Sums
+ * per block of ORA_BLOCK jobs, added in block order. */
+int ora_mixture_utility(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
+                        const float *par, int K, const double *theta, const double *lams,
+                        const double *sc_oth, const double *sc_lin, int cap, int method,
+                        double *U_out, int nthreads)
+{
+    if (m <= 0 || m > ORA_MAXM || n < 0 || K <= 0) return 1;
+    int64_t nb = (n + ORA_BLOCK - 1) / ORA_BLOCK;
+    double *part = (double *)calloc((size_t)(nb > 0 ? nb : 1), sizeof(double));
+    if (!part) return 2;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads))
+    for (int64_t b = 0; b < nb; ++b) {
+        double a[ORA_MAXM], o[ORA_NOUT];
+        int64_t i1 = (b + 1) * ORA_BLOCK < n ? (b + 1) * ORA_BLOCK : n;
+        for (int64_t i = b * ORA_BLOCK; i < i1; ++i) {
+            load_row(m, A, i, a);
+            double t = 0.0;
+            for (int k = 0; k < K; ++k) {
+                if (!(theta[k] > 0.0)) continue;
+                solve_job(m, a, lams + (size_t)k * m, kind[i], w[i], par[i], cap, method, o);
+                const double *sc = (kind[i] >= 2 ? sc_lin : sc_oth) + (size_t)k * m;
+                double tk = 0.0;
+                if (o[3] >= 0) tk += a[(int)o[3]] * o[5] * sc[(int)o[3]];
+                if (o[4] >= 0) tk += a[(int)o[4]] * o[6] * sc[(int)o[4]];
+                t += theta[k] * tk;
+            }
+            part[b] += util(kind[i], w[i], par[i], t);
+        }
+    }
+    double su = 0.0;
+    for (int64_t b = 0; b < nb; ++b) su += part[b];
+    *U_out = su;
+    free(part);
+    return 0;
+}

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -25,6 +26,10 @@ ra_status fail(ra_status s, const char *fmt, ...)
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static std::atomic<uint64_t> g_wait_ns{2000000000ull};
+
+uint64_t wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 // Host-side data checks (RA_VALIDATE): problem (e-res-alloc) needs A >= 0,
 // w > 0, p in (0,1), T > 0, R >= 0, all finite, and a positive efficiency for
@@ -87,7 +92,15 @@ const char *ra_status_string(ra_status s)
 
 const char *ra_last_error(void) { return ra::g_err; }
 
-const char *ra_version(void) { return "libra 0.1 sm_103a"; }
+const char *ra_version(void) { return "libra 0.2 sm_103a"; }
+
+ra_status ra_set_wait_timeout(double seconds)
+{
+    if (!(seconds >= 0.0 && seconds <= 60.0))
+        return fail(RA_EINVAL, "wait timeout %g s must lie in [0, 60]", seconds);
+    ra::g_wait_ns.store(static_cast<uint64_t>(seconds * 1e9 + 0.5), std::memory_order_relaxed);
+    return RA_OK;
+}
 
 void ra_solve_opts_default(ra_solve_opts *o)
 {
@@ -230,7 +243,10 @@ ra_status ra_eval_dual(ra_problem *p, const double *lambda, double *g, double *q
     dp.ticket = p->ticket;
     dp.status = p->status;
     dp.out = p->ev;
-    cudaError_t e = ra::launch_dual(p, dp, p->stream);
+    // the status word reports this call's waits only
+    cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "status reset: %s", cudaGetErrorString(e));
+    e = ra::launch_dual(p, dp, p->stream);
     if (e != cudaSuccess) return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
     if (U_lb) {
         e = ra::launch_lower_bound(p, p->lbt[0], p->lbj[0], p->ev, U_lb, p->stream);
@@ -258,7 +274,8 @@ ra_status ra_eval_records(ra_problem *p, int32_t *j12, float *t12)
 ra_status ra_init_prices(ra_problem *p, double *lambda1)
 {
     if (!p || !lambda1) return fail(RA_EINVAL, "NULL problem or output");
-    cudaError_t e = ra::launch_init(p, lambda1, p->stream);
+    cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = ra::launch_init(p, lambda1, p->stream);
     if (e != cudaSuccess) return fail(RA_ECUDA, "init launch: %s", cudaGetErrorString(e));
     return RA_OK;
 }
@@ -681,7 +698,8 @@ ra_status ra_warmstart_prices(ra_problem *p, ra_mlp *net, double *lambda0, int32
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start stream: %s", cudaGetErrorString(e));
     }
-    e = cudaEventRecord(p->fork, s);
+    e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaEventRecord(p->fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
     if (e == cudaSuccess) e = ra::launch_features(nullptr, feat_of(p), 1, p->m, stats, feats, p->side);
     if (e == cudaSuccess) e = ra::mlp_forward(net, feats, p->m, y, p->side);

@@ -93,17 +93,25 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
-// Wait for completion of phase `parity`; gives up after about two seconds.
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for completion of phase `parity`; gives up after limit_ns of device
+// time (ra_set_wait_timeout; two seconds by default).  A zero limit gives up
+// at once, without polling.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
+    if (limit_ns == 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 0; it < (1u << 28); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31) == 31 && globaltimer() - t0 > 2000000000ull) return false;
+        if ((it & 31) == 31 && globaltimer() - t0 > limit_ns) return false;
     }
     return false;
 }
+
+// Bound of the waits that let copies still in flight land before a CTA that
+// gave up exits: independent of the caller's limit, since the copies are
+// valid and complete within microseconds.
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------- utilities
 
@@ -890,6 +898,10 @@ __device__ __noinline__ bool grid_reduce(T hsum, T uxsum, T lbsum, T racc, T rli
     return true;
 }
 
+// The status word as the last CTA sees it after the grid stage's fences.
+__device__ __forceinline__ int ld_status(const int *status) { return __ldcg(status); }
+__device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000ll); }
+
 // Dual outputs (Section 3): g = lambda^T R + sum h_i, q = R - r.
 // lambda^T R, summed in column order by one thread.  The streaming kernels
 // stage lambda and R in shared memory in their prologue and have a thread of
@@ -912,18 +924,22 @@ __device__ void reduce_and_finalize(T hsum, T uxsum, T lbsum, T racc, T rlin, in
                      red))
         return;
     const int tid = threadIdx.x;
+    // a CTA whose bounded wait gave up left its jobs out of the sums: the
+    // outputs become NaN, so that a caller who cannot read the status word
+    // (ra_eval_dual_static) still sees that the evaluation is incomplete
+    const bool bad = (ld_status(P.status) & kStatusTimeout) != 0;
     if (tid < m) {
-        const double r = to_double(red[0][4 + tid]);
+        const double r = bad ? nan_d() : to_double(red[0][4 + tid]);
         P.out->r[tid] = r;
         P.out->q[tid] = P.R[tid] - r;
-        P.out->r_lin[tid] = lin ? to_double(red[0][4 + m + tid]) : 0.0;
+        P.out->r_lin[tid] = bad ? nan_d() : lin ? to_double(red[0][4 + m + tid]) : 0.0;
     }
     if (tid == 0) {
-        const double sumh = to_double(red[0][0]);
+        const double sumh = bad ? nan_d() : to_double(red[0][0]);
         P.out->sumh = sumh;
         P.out->g = *lr_s + sumh;
-        P.out->Ux = to_double(red[0][1]);
-        P.out->Ulb_prev = to_double(red[0][2]);
+        P.out->Ux = bad ? nan_d() : to_double(red[0][1]);
+        P.out->Ulb_prev = bad ? nan_d() : to_double(red[0][2]);
     }
 }
 
@@ -970,7 +986,7 @@ template <int MT, class Job, class Pre = NoPrologue>
 __device__ bool stream_jobs(const float *A, const float *W, const float *Par, const uint8_t *Kind,
                             const float2 *rec_t, const uchar2 *rec_j, long long n, int m,
                             int stages, long long num_full, unsigned char *smem, uint64_t *bars,
-                            int *status, Job &&job, Pre &&pre = Pre{})
+                            int *status, uint64_t wait_ns, Job &&job, Pre &&pre = Pre{})
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t a_bytes = StageLayout<MT>::a_bytes(m);
@@ -1008,13 +1024,14 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
     for (long long it = 0; it < n_my; ++it) {
         const int st = static_cast<int>(it % stages);
         const uint32_t parity = static_cast<uint32_t>((it / stages) & 1);
-        const bool ok = mbar_wait_bounded(&bars[st], parity);
+        const bool ok = mbar_wait_bounded(&bars[st], parity, wait_ns);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(status, kStatusTimeout);
                 // let copies already in flight land before the CTA exits (bounded)
                 for (long long it2 = it; it2 < n_my && it2 < it + stages; ++it2)
-                    (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1));
+                    (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1),
+                                            kDrainNs);
             }
             __syncthreads();
             return false;
@@ -1173,7 +1190,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(P.A, P.w, P.param, P.kind, (LAG && lag) ? lbt_prev : nullptr,
                     (LAG && lag) ? lbj_prev : nullptr, P.n, m, stages, num_full, smem, bars,
-                    P.status, job, [&] {
+                    P.status, P.wait_ns, job, [&] {
                         if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
                     });
     reduce_and_finalize(ff_of(hsum), ff_of(uxsum), ff_of(lbsum), ff_of(racc), ff_of(rlin), m,
@@ -1188,7 +1205,7 @@ template <int MT>
 __global__ void __launch_bounds__(kTile, 2)
     init_tma_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
                     const double *R, long long n, int m, int cap, int stages, long long num_full,
-                    double *partials, unsigned *ticket, int *status, double *lam1)
+                    double *partials, unsigned *ticket, int *status, uint64_t wait_ns, double *lam1)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
@@ -1240,12 +1257,15 @@ __global__ void __launch_bounds__(kTile, 2)
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
-                    job);
+                    wait_ns, job);
     const FF z = red_zero<FF>();
     FF(*red)[kPartW] = ring_red(smem);
     if (grid_reduce(z, z, z, ff_of(racc), z, m, false, grouped ? (lane / MT == 0) : true, partials,
-                    ticket, red))
-        if (tid < m) lam1[tid] = to_double(red[0][4 + tid]) / static_cast<double>(n);
+                    ticket, red)) {
+        // a CTA whose wait gave up left its share out of the sums: no prices
+        const bool bad = (ld_status(status) & kStatusTimeout) != 0;
+        if (tid < m) lam1[tid] = bad ? nan_d() : to_double(red[0][4 + tid]) / static_cast<double>(n);
+    }
 }
 
 // Dual values g(lambda_a) and g(lambda_b) in one pass over the data (the
@@ -1257,7 +1277,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     dual_g2_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
                    const double *R, long long n, int m, const double *lam_a, const double *lam_b,
                    int stages, long long num_full, double *partials, unsigned *ticket, int *status,
-                   double *g_out)
+                   uint64_t wait_ns, double *g_out)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
@@ -1292,7 +1312,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
-                    job, [&] {
+                    wait_ns, job, [&] {
                         if (tid == 32) {
                             lr_s[0] = lam_dot_R(lad_s, Rd_s, m);
                             lr_s[1] = lam_dot_R(lbd_s, Rd_s, m);
@@ -1302,8 +1322,9 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     FF(*red)[kPartW] = ring_red(smem);
     if (grid_reduce(ff_of(ha), ff_of(hb), z, z, z, 0, false, true, partials, ticket, red) &&
         tid == 0) {
-        g_out[0] = lr_s[0] + to_double(red[0][0]);
-        g_out[1] = lr_s[1] + to_double(red[0][1]);
+        const bool bad = (ld_status(status) & kStatusTimeout) != 0;
+        g_out[0] = bad ? nan_d() : lr_s[0] + to_double(red[0][0]);
+        g_out[1] = bad ? nan_d() : lr_s[1] + to_double(red[0][1]);
     }
 }
 
@@ -1452,14 +1473,16 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
         int st = 0;
         if (full) {
             st = static_cast<int>(consumed % stages);
-            const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>((consumed / stages) & 1));
+            const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>((consumed / stages) & 1),
+                                              B.wait_ns);
             if (__syncthreads_or(!ok)) {
                 // a copy never completed: record it, let the copies still in
                 // flight land (bounded) and give up
                 if (tid == 0) {
                     atomicOr(B.status, kStatusTimeout);
                     for (long long it2 = consumed; it2 < issued; ++it2)
-                        (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1));
+                        (void)mbar_wait_bounded(&bars[it2 % stages], static_cast<uint32_t>((it2 / stages) & 1),
+                                                kDrainNs);
                 }
                 __syncthreads();
                 return;
@@ -1798,7 +1821,7 @@ __global__ void __launch_bounds__(kTile)
         __threadfence();
         double v = 0.0;
         for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[b]);
-        *U_lb = v;
+        *U_lb = isnan(src->sumh) ? src->sumh : v;   // the evaluation it scales was incomplete
         *ticket = 0u;
     }
 }
@@ -1919,11 +1942,13 @@ int mt_stages(int m, size_t budget = 106 * 1024)
 }
 
 template <int MT, bool CAP, bool LAG, bool REC>
-cudaError_t launch_tma(const ra_problem *p, const DualParams &dp, cudaStream_t s)
+cudaError_t launch_tma(const ra_problem *p, const DualParams &dp_in, cudaStream_t s)
 {
     const long long num_full = p->n / kTile;
     int grid = p->grid_dual;
     if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
+    DualParams dp = dp_in;
+    dp.wait_ns = wait_limit_ns();
     dual_tma_kernel<MT, CAP, LAG, REC><<<grid, kTile, p->smem_dual, s>>>(dp, p->stages, num_full);
     return cudaGetLastError();
 }
@@ -2090,11 +2115,11 @@ cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const doubl
     if (cap)                                                                                       \
         dual_g2_kernel<MT, true><<<grid, kTile, p->smem_dual, s>>>(                                \
             p->A, p->kind, p->w, p->param, p->R, p->n, p->m, lam_a, lam_b, p->stages, num_full,    \
-            p->partials, p->ticket + 3, p->status, g_out);                                         \
+            p->partials, p->ticket + 3, p->status, wait_limit_ns(), g_out);                        \
     else                                                                                           \
         dual_g2_kernel<MT, false><<<grid, kTile, p->smem_dual, s>>>(                               \
             p->A, p->kind, p->w, p->param, p->R, p->n, p->m, lam_a, lam_b, p->stages, num_full,    \
-            p->partials, p->ticket + 3, p->status, g_out);
+            p->partials, p->ticket + 3, p->status, wait_limit_ns(), g_out);
     switch (p->mt) {
     case 4: RA_G2(4) break;
     case 8: RA_G2(8) break;
@@ -2115,7 +2140,7 @@ cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s)
     init_tma_kernel<MT><<<grid, kTile, p->smem_dual, s>>>(p->A, p->kind, p->w, p->param, p->R,      \
                                                           p->n, p->m, cap, p->stages, num_full,    \
                                                           p->partials, p->ticket + 2, p->status,   \
-                                                          lam1)
+                                                          wait_limit_ns(), lam1)
     switch (p->mt) {
     case 4: RA_INIT(4); break;
     case 8: RA_INIT(8); break;
@@ -2206,8 +2231,10 @@ cudaError_t batch_configure(int mt, int cap, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kTile, batch_smem(mt, cap));
 }
 
-cudaError_t launch_batch_dual(int mt, const BatchDualArgs &a, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_batch_dual(int mt, const BatchDualArgs &a_in, int grid, size_t smem, cudaStream_t s)
 {
+    BatchDualArgs a = a_in;
+    a.wait_ns = wait_limit_ns();
 #define RA_BD(MT)                                                                                  \
     if (a.cap) batch_dual_kernel<MT, true><<<grid, kTile, smem, s>>>(a);                          \
     else batch_dual_kernel<MT, false><<<grid, kTile, smem, s>>>(a);

@@ -204,6 +204,7 @@ struct DualParams {
     uchar2 *lbj_buf[2];
     const int32_t *pingpong;
     const int32_t *lag_on;
+    uint64_t wait_ns;         // bound of the mbarrier waits (set by the launchers)
 };
 
 // One problem of a batch (device copy).
@@ -239,6 +240,7 @@ struct BatchDualArgs {
     int *status;
     int stages;
     int cap;
+    uint64_t wait_ns;     // bound of the mbarrier waits (set by the launcher)
 };
 
 // Launchers (ra_dual.cu).
@@ -293,6 +295,9 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
 
 // Error reporting (ra_api.cu).
 ra_status fail(ra_status s, const char *fmt, ...);
+
+// Bound of the kernels' device waits in ns (ra_set_wait_timeout; ra_api.cu).
+uint64_t wait_limit_ns();
 
 }  // namespace ra
 

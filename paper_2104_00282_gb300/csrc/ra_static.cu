@@ -1,7 +1,10 @@
 // ra_eval_dual_static: the dual evaluation of ra_eval_dual without any device
-// allocation.  Its scratch (per-CTA partial sums, the last-CTA ticket, the
-// status word and the result slots) lives in one file-scope static device
-// array that every GPU loading this library holds until the process exits.
+// allocation, for callers that may not allocate (serving loops with a
+// no-allocation rule, hosts whose framework owns all device memory).  Its
+// scratch (per-CTA partial sums, the last-CTA ticket, the status word and
+// the result slots) lives in one file-scope static device array that every
+// GPU loading this library holds until the process exits.  The call is
+// asynchronous: a bounded wait that gave up shows as NaN in g and q.
 
 #include <cstring>
 #include <mutex>
@@ -23,6 +26,15 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
+
+// Launch configuration per (device, m, cap mode), computed on the first call
+// (configure_dual also sets the kernels' attributes on that device).
+struct LaunchConfig {
+    bool valid;
+    int num_sms, mt, stages, grid_dual, grid_aux;
+    size_t smem_dual;
+};
+LaunchConfig g_config[kMaxDevices][RA_MAX_M][2] = {};
 
 // Device address of the scratch array on `dev` (the current device), looked
 // up once per device: in host code the symbol names a host-side stand-in, so
@@ -78,9 +90,23 @@ extern "C" ra_status ra_eval_dual_static(int64_t n, int32_t m, const float *A, c
     p.R = R;
     p.stream = static_cast<cudaStream_t>(stream);
     p.device = dev;
-    e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = ra::configure_dual(&p);
-    if (e != cudaSuccess) return ra::fail(RA_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        LaunchConfig &c = g_config[dev][m - 1][(flags & RA_NO_JOB_CAP) ? 1 : 0];
+        if (!c.valid) {
+            e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = ra::configure_dual(&p);
+            if (e != cudaSuccess)
+                return ra::fail(RA_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+            c = LaunchConfig{true, p.num_sms, p.mt, p.stages, p.grid_dual, p.grid_aux, p.smem_dual};
+        }
+        p.num_sms = c.num_sms;
+        p.mt = c.mt;
+        p.stages = c.stages;
+        p.grid_dual = c.grid_dual;
+        p.grid_aux = c.grid_aux;
+        p.smem_dual = c.smem_dual;
+    }
     if (p.grid_dual > kStaticMaxCtas)
         return ra::fail(RA_EINVAL,
                         "this GPU runs %d CTAs per evaluation; the static scratch holds partial sums "

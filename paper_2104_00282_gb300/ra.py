@@ -109,6 +109,8 @@ def lib():
         L.ra_last_error.argtypes = []
         L.ra_last_error.restype = ctypes.c_char_p
         L.ra_version.restype = ctypes.c_char_p
+        L.ra_set_wait_timeout.argtypes = [ctypes.c_double]
+        L.ra_set_wait_timeout.restype = i32
         _lib = L
     return _lib
 
@@ -331,6 +333,10 @@ def ra_warmstart_prices(h, net, lam0, sync=True):
     _check(lib().ra_warmstart_prices(h, net, _ptr(lam0, torch.float64),
                                      ctypes.byref(flag) if sync else None))
     return int(flag.value) if sync else None
+
+
+def ra_set_wait_timeout(seconds):
+    _check(lib().ra_set_wait_timeout(float(seconds)))
 
 
 def ra_version():

@@ -281,3 +281,27 @@ def test_invalid_arguments_are_rejected(ra):
         assert e.value.status == ra.RA_EINVAL
     h = ra.ra_problem_create(A, kind, w, p, R, ra.RA_VALIDATE)
     ra.ra_problem_destroy(h)
+
+
+def test_expired_wait_is_reported(ra):
+    """A bounded device wait that gives up (zero timeout: every wait expires
+    at once) makes the evaluation's outputs NaN and the solve return
+    RA_ETIMEOUT; with the default timeout the same problem solves again."""
+    prob = W.random_small(100_003, 8, seed=21, r_scale=0.3)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda")
+    lam = torch.tensor(W.random_prices(8, seed=22), dtype=torch.float64, device="cuda")
+    try:
+        ra.ra_set_wait_timeout(0.0)
+        g, q, U = P.eval_dual(lam, lower_bound=True)
+        torch.cuda.synchronize()
+        assert np.isnan(g.item()) and np.all(np.isnan(q.cpu().numpy())) and np.isnan(U.item())
+        with pytest.raises(ra.RaError) as e:
+            P.solve(tol=1e-6, max_evals=50)
+        assert e.value.status == ra.RA_ETIMEOUT
+    finally:
+        ra.ra_set_wait_timeout(2.0)
+    info = P.solve(tol=1e-6, max_evals=200)
+    P.close()
+    assert info["status"] == ra.RA_OK
+    with pytest.raises(ra.RaError):
+        ra.ra_set_wait_timeout(-1.0)

@@ -619,3 +619,34 @@ def test_master_bound_is_feasible_and_valid(oracle):
     assert lb <= ref.g + 1e-9 * abs(ref.g)                # weak duality
     best_single = max(oracle.lower_bound(p, lam)[0] for lam in lams)
     assert lb >= best_single - 1e-9 * abs(lb)
+
+
+@pytest.mark.parametrize("cap", [True, False])
+def test_certify_matches_dense_mixture(oracle, cap):
+    """The large-scale certificate check (no dense X) equals the mixture built
+    densely from the per-job records: usage, feasibility after the final
+    scaling, its utility, and g."""
+    p = W.config_large(n=20_000, m=6, seed=11)
+    sol = oracle.solve(p, cap=cap, tol=1e-6, max_evals=200)
+    rng = np.random.default_rng(2)
+    lams = np.stack([sol.lam * rng.uniform(0.98, 1.02, p.m) for _ in range(3)])
+    theta = np.array([0.5, 0.3, 0.2])
+    scaled = np.array([1, 0, 1])
+    c = oracle.certify(p, sol.lam, theta, lams, scaled, cap)
+    R = p.R
+    lin = (p.kind >= 2)[:, None]
+    Xbar = np.zeros((p.n, p.m))
+    for th, l, sc in zip(theta, lams, scaled):
+        X, _ = oracle.allocation(p, l, cap=cap)
+        if sc:
+            s, s_lin = oracle.column_scales(R, X.sum(0), X[lin[:, 0]].sum(0), cap)
+            X = X * np.where(lin, s_lin[None, :], s[None, :])
+        Xbar += th * X
+    usage = Xbar.sum(0)
+    np.testing.assert_allclose(c["usage_over_R"], usage / R, rtol=1e-12)
+    Xbar *= np.minimum(1.0, R / usage)[None, :]
+    assert np.all(Xbar.sum(0) <= R * (1 + 1e-12))
+    U = oracle.utility_of(p, (p.A.astype(np.float64) * Xbar).sum(1))
+    assert c["U_lb"] == pytest.approx(U, rel=1e-12)
+    assert c["g"] == pytest.approx(oracle.dual(p, sol.lam, cap=cap)[0], rel=1e-15)
+    assert c["U_lb"] <= c["g"]

@@ -1,11 +1,14 @@
 """The allocation-free dual evaluation (ra_eval_dual_static) against the
 regular entry point (ra_eval_dual), through the C ABI.
 
-Callers that cannot allocate device memory -- code inside a CUDA graph
-capture, serving loops that forbid allocation, hosts whose framework owns all
-device memory -- use ra_eval_dual_static, whose scratch is a static array in
-the library.  This file is collected last on purpose; it must pass alone in a
-fresh process and after every other test.
+Callers that cannot allocate device memory -- serving loops that forbid
+allocation (cudaMalloc may synchronise the device), hosts whose framework
+owns all device memory through its own pool -- use ra_eval_dual_static,
+whose scratch is a static array in the library.  The two entry points run
+the same kernel with the same launch shape, so their results must agree bit
+for bit, on two calls in a row that share the array.  This file is
+collected last on purpose; it must pass alone in a fresh process and after
+every other test.
 """
 import ctypes
 
@@ -64,11 +67,32 @@ def test_static_scratch_matches_regular_entry_point(ra, n, m, cap):
         g, q = _static_call(ra, A, kind, w, par, R, lam, flags)
         torch.cuda.synchronize()
         g, q, g_ref, q_ref = g.item(), q.cpu().numpy(), g_ref.item(), q_ref.cpu().numpy()
-        lam_h = lam.cpu().numpy()
-        mag = float(np.abs(lam_h * prob.R).sum()) + abs(g_ref)
-        assert abs(g - g_ref) <= 2e-6 * mag
-        assert np.all(np.abs(q - q_ref) <= 2e-6 * np.maximum(prob.R, 1.0))
+        # the same kernel, launch shape and fixed reduction order: the same bits
+        assert g == g_ref
+        assert np.array_equal(q, q_ref)
     P.close()
+
+
+def test_static_timeout_shows_as_nan(ra):
+    """The call returns before its work is done, so an expired device wait
+    cannot be returned as RA_ETIMEOUT; g and q become NaN instead.  A zero
+    wait timeout makes every wait give up at once; the next call with the
+    default timeout is complete again."""
+    prob = W.random_small(200_003, 16, seed=5, r_scale=0.3)
+    dev = "cuda"
+    A, kind, w, par, R = (torch.from_numpy(x).to(dev) for x in
+                          (prob.A, prob.kind, prob.w, prob.param, prob.R))
+    lam = torch.tensor(W.random_prices(16, seed=3), dtype=torch.float64, device=dev)
+    try:
+        ra.ra_set_wait_timeout(0.0)
+        g, q = _static_call(ra, A, kind, w, par, R, lam, 0)
+        torch.cuda.synchronize()
+        assert np.isnan(g.item()) and np.all(np.isnan(q.cpu().numpy()))
+    finally:
+        ra.ra_set_wait_timeout(2.0)
+    g, q = _static_call(ra, A, kind, w, par, R, lam, 0)
+    torch.cuda.synchronize()
+    assert np.isfinite(g.item()) and np.all(np.isfinite(q.cpu().numpy()))
 
 
 def test_static_entry_point_rejects_bad_arguments(ra):
