@@ -206,7 +206,11 @@ def certify_headline(prob, P, cap):
     import numpy as np
     lam = P.prices.cpu().numpy()
     theta, lams, scaled = P.certificate()
-    c = O.certify(prob, lam, theta, lams, scaled, cap)
+    repaired = None
+    if 2 in list(scaled):   # the bound is the repaired allocation at lams[0]
+        out = P.recover_feasible(lams[0])
+        repaired = (out["jk"].cpu().numpy(), out["xk"].cpu().numpy())
+    c = O.certify(prob, lam, theta, lams, scaled, cap, repaired=repaired)
     return {"rel_gap_oracle": c["rel_gap"], "g_oracle": c["g"], "U_lb_oracle": c["U_lb"],
             "max_usage_over_R": c["max_usage_over_R"], "oracle_seconds": c["seconds"],
             "certificate_entries": int(np.sum(np.asarray(theta) > 0))}

@@ -129,14 +129,19 @@ ra_status ra_eval_records(ra_problem *prob, int32_t *j12, float *t12);
 ra_status ra_init_prices(ra_problem *prob, double *lambda1);
 
 typedef struct {
-    double tol_rel;       /* stop when (g_best - U_best)/max(|U_best|,|g_best|,1) <= tol_rel */
+    double tol_rel;       /* target relative gap (g_best - U_best)/max(|U_best|,|g_best|,1);
+                             with FP32 per-job arithmetic the loop stops at tol_rel / 2, leaving
+                             room for the FP32 rounding of its own estimate of the gap           */
     int32_t max_evals;    /* cap on dual evaluations (line-search trials included)             */
     int32_t lbfgs_mem;    /* L-BFGS memory, 1..16 (Section 6.1 uses 10)                         */
     int32_t update;       /* 0 = projected L-BFGS, 1 = projected subgradient (Section 5)        */
     int32_t use_graph;    /* 1 = run the loop as one CUDA graph with a device-side while node   */
     double lam_floor;     /* lower bound on prices; <0 selects 0 (cap) / 1e-12 max(lambda^1)    */
     int32_t master_lb;    /* 1 = also bound U* by the master LP over evaluated allocations      */
-    int32_t pad_;
+    int32_t repair_window;/* > 0: when the gap has not halved in this many evaluations, leave the
+                             device loop, re-mix the jobs at ties at the best prices (as
+                             ra_recover_feasible) and resume; also tried once at max_evals.
+                             0 = off.  Default 16                                               */
     double init_step;     /* length of the first price step (and of a restarted gradient step)
                              as a fraction of |lambda|; default 0.05, smaller from a close start */
 } ra_solve_opts;
@@ -150,6 +155,8 @@ typedef struct {
     double U_lb;          /* best feasible utility (lower bound on U*)                          */
     double rel_gap;       /* relative duality gap at exit                                      */
     double gap_per_job;   /* (g - U_lb) / n, the paper's absolute measure (Algorithm 2)         */
+    int32_t repairs;      /* repairs of the lower bound run (see repair_window)                 */
+    int32_t n_flex;       /* jobs the last repair re-mixed                                      */
 } ra_solve_info;
 
 /* Fill *opts with the defaults (tol 1e-6, 500 evals, memory 10, L-BFGS, graph,
@@ -182,7 +189,9 @@ ra_status ra_solve(ra_problem *prob, const ra_solve_opts *opts, const double *la
  * has weight theta[k] (summing to 1), prices lam[k*m .. k*m+m) and scaled[k]
  * = 1 when that allocation was column-scaled to X diag(min(1, R/r)) (Section
  * 5) before mixing.  The mixture meets sum_i x_i <= R, and since every u_i is
- * concave its utility is at least U_lb.  theta, scaled: host arrays of
+ * concave its utility is at least U_lb.  A single entry with scaled[0] = 2
+ * means the bound came from a repair (see repair_window): the allocation is
+ * the one ra_recover_feasible returns at lam[0] with default options.  theta, scaled: host arrays of
  * RA_MAX_CERT entries; lam: host array of RA_MAX_CERT * m doubles.  Returns
  * the number of entries written, or -1 on error.  Synchronises.
  */
@@ -216,6 +225,53 @@ int32_t ra_solve_history(ra_problem *prob, double *hist, int32_t cap);
 ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jstar, int32_t *j12,
                             float *x12, float *t, float *X_dense, double *U, uint8_t *near_tie,
                             int64_t *n_near_ties);
+
+/*
+ * ra_recover_feasible -- an allocation that meets the resource limits, at
+ * prices lambda (Section 3, "Recovering an optimal allocation from optimal
+ * prices").  Every job gets its subproblem's optimum (as ra_recover_primal);
+ * the jobs whose optimum is within tie_rel of a tie -- two effective prices
+ * lambda_j / A_ij, two hull segments, or (linear utilities) w and a segment
+ * slope -- are re-mixed: each job's optimal extreme allocations are listed and
+ * a small LP (FP64, on the host) picks convex weights that first minimise the
+ * total relative overuse sum_j max(r_j - R_j, 0) / R_j and then maximise the
+ * weighted utility.  Overuse the LP cannot remove is taken out by the column
+ * scaling of Section 5 (without the per-job cap, under-used columns are also
+ * scaled up).  The paper is silent on this step; at optimal prices the
+ * re-mixed allocation closes the duality gap that column scaling alone
+ * leaves when few jobs share a resource.
+ *   lambda   m FP64 prices
+ *   opts     host or NULL: tie_rel (default 1e-3), max_flex jobs re-mixed at
+ *            most (default 512, <= 4096; the jobs closest to a tie are taken)
+ *   jk, xk   4n int32 / 4n FP32 outputs or both NULL: per job up to four
+ *            (resource, time fraction) pairs, resource -1 = unused slot;
+ *            RA_EINVAL if a re-mixed job uses more than four (then use X)
+ *   X_dense  n*m FP32 output or NULL
+ *   info     host output (required): the utility U of the returned allocation
+ *            (a lower bound on the optimum), its worst usage_j / R_j, the jobs
+ *            re-mixed and the LP's outcome
+ * Synchronises.  Overwrites the records that ra_eval_records returns.
+ * Allocates about 4n bytes of workspace on its first call.
+ */
+typedef struct {
+    double tie_rel;        /* margin below which a job's optimum counts as tied (0, 1]      */
+    int32_t max_flex;      /* jobs re-mixed at most, 1..4096                                 */
+    int32_t pad_;
+} ra_repair_opts;
+
+typedef struct {
+    int64_t n_flex;           /* jobs re-mixed by the LP                                      */
+    int32_t n_alt;            /* optimal extreme allocations offered to the LP               */
+    int32_t lp_status;        /* 0 optimal; 1 iteration limit; -1 no LP was needed           */
+    double tie_cut;           /* the re-mixed jobs have tie margins below this              */
+    double overuse;           /* sum_j max(r_j - R_j, 0) / R_j left by the LP (then scaled)  */
+    double U;                 /* utility of the returned allocation (lower bound on U*)      */
+    double max_usage_over_R;  /* worst usage_j / R_j of the returned allocation            */
+} ra_repair_info;
+
+void ra_repair_opts_default(ra_repair_opts *opts);
+ra_status ra_recover_feasible(ra_problem *prob, const double *lambda, const ra_repair_opts *opts,
+                              int32_t *jk, float *xk, float *X_dense, ra_repair_info *info);
 
 /*
  * ra_eval_dual_static -- g(lambda) and q = R - r exactly as ra_eval_dual
@@ -255,6 +311,50 @@ ra_status ra_eval_dual_static(int64_t n, int32_t m, const float *A, const uint8_
                               const float *w, const float *param, const double *R,
                               const double *lambda, uint32_t flags, void *stream, double *g,
                               double *q);
+
+/*
+ * One problem split by job range across devices or processes (shards).  Given
+ * the prices the jobs are independent (Section 3, "Evaluating the dual
+ * function"), so each shard evaluates its own jobs and only m-sized sums
+ * cross between shards; a shard is a problem created with ra_problem_create
+ * over a contiguous range of the jobs (the pointers offset to the range's
+ * first job -- a range starting at a multiple of 16 jobs keeps them 16-byte
+ * aligned) and the whole problem's R.  (Not in the paper.)
+ *
+ * Exchanged per shard: RA_SHARD_WIDTH(m) FP64 values [sum_i h_i, sum_i
+ * u_i(t_i), lagged lower bound, status word, r_0..r_{m-1}, r_lin_0..]; shards
+ * are always added in shard (rank) order, so every shard computes the same
+ * bits.
+ */
+#define RA_SHARD_WIDTH(m) (4 + 2 * (m))
+
+/* ra_eval_partial -- this shard's sums at lambda: part (device,
+ * RA_SHARD_WIDTH(m) FP64) as laid out above (the lagged bound is 0). */
+ra_status ra_eval_partial(ra_problem *shard, const double *lambda, double *part);
+
+/* ra_combine_partials -- g = lambda^T R + sum_s h_s and q = R - sum_s r_s from
+ * S shards' parts (device, S x RA_SHARD_WIDTH(m), shard order); g (1) and q
+ * (m) are device outputs (either may be NULL); enqueued on `stream`. */
+ra_status ra_combine_partials(int32_t S, int32_t m, const double *parts, const double *lambda,
+                              const double *R, double *g, double *q, void *stream);
+
+/*
+ * ra_solve_sharded -- ra_solve for one shard of a problem of n_total jobs
+ * split across `world` shards; shard `rank` of them.  Every shard calls it
+ * with the same options and start prices.  Once per evaluation (and once for
+ * Eq. e-initialization) the library writes `count` FP64 values into send
+ * (device, >= RA_SHARD_WIDTH(m)) and calls fn(ctx, count, stream): fn must
+ * all-gather every shard's send into recv (device, world x count, shard
+ * order), enqueued on `stream` (for example an NCCL all-gather), and return
+ * 0.  The price update then runs on every shard on the same combined values,
+ * so the prices agree bit for bit.  Host-driven loop (no CUDA graph, no
+ * repair of the lower bound); synchronises every evaluation.
+ */
+typedef int32_t (*ra_allgather_fn)(void *ctx, int32_t count, void *stream);
+ra_status ra_solve_sharded(ra_problem *shard, int64_t n_total, int32_t rank, int32_t world,
+                           double *send, double *recv, ra_allgather_fn fn, void *ctx,
+                           const ra_solve_opts *opts, const double *lambda0, double *lambda_out,
+                           ra_solve_info *info);
 
 /*
  * Batched price discovery (a throughput mode; the paper solves one problem at

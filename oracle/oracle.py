@@ -240,20 +240,50 @@ def mixture_utility(prob, theta, lams, sc_oth, sc_lin, cap=True, method="hull", 
     return float(U[0])
 
 
-def certify(prob, lam_best, theta, lams, scaled, cap=True, nthreads=0):
+def sparse_allocation_check(prob, jk, xk):
+    """FP64 utility and usage of an allocation given as per-job (resource,
+    time fraction) pairs (resource -1 = unused): t_i = sum_k A[i, jk] xk,
+    U = sum_i u_i(t_i), usage_j = sum of the fractions on resource j.
+    Returns (U, usage, t)."""
+    n, m = prob.n, prob.m
+    jk = np.asarray(jk, np.int64).reshape(n, -1)
+    xk = np.asarray(xk, np.float64).reshape(n, -1)
+    valid = jk >= 0
+    rows = np.broadcast_to(np.arange(n)[:, None], jk.shape)
+    a = np.where(valid, prob.A[rows, np.where(valid, jk, 0)].astype(np.float64), 0.0)
+    x = np.where(valid, xk, 0.0)
+    t = (a * x).sum(1)
+    usage = np.bincount(jk[valid], weights=x[valid], minlength=m)
+    return utility_of(prob, t), usage, t
+
+
+def certify(prob, lam_best, theta, lams, scaled, cap=True, nthreads=0, repaired=None):
     """FP64 re-check of a solver's result (Section 5's bounds): the dual value
     g at ``lam_best`` (an upper bound on U*), and the utility of the
     allocation behind the solver's lower bound -- the mixture sum_k theta_k
     X(lam_k), allocation k column-scaled (``column_scales``) where
-    ``scaled[k]`` -- once more scaled by min(1, R/usage) so that it meets
-    X^T 1 <= R exactly in FP64 (a lower bound on U*).  Returns a dict with g,
-    U_lb, the relative gap, usage / R of the mixture before that last
-    scaling (its worst entry is the solver's constraint violation), and the
-    seconds taken."""
+    ``scaled[k]`` is 1 -- once more scaled by min(1, R/usage) so that it
+    meets X^T 1 <= R exactly in FP64 (a lower bound on U*).  When the bound
+    came from a repaired allocation (``scaled == [2]``), ``repaired`` holds
+    that allocation as (jk, xk) pairs and is checked as given.  Returns a
+    dict with g, U_lb, the relative gap, usage / R of the allocation before
+    that last scaling (its worst entry is the solver's constraint
+    violation), and the seconds taken."""
     t0 = time.perf_counter()
     R = np.asarray(prob.R, np.float64)
     lam_best = np.asarray(lam_best, np.float64)
     g, _, _ = dual(prob, lam_best, cap, nthreads=nthreads)
+    if 2 in list(np.asarray(scaled)):
+        jk, xk = repaired
+        U0, usage, t = sparse_allocation_check(prob, jk, xk)
+        ratio = np.where(R > 0, usage / np.where(R > 0, R, 1.0), np.where(usage > 0, np.inf, 0.0))
+        f = column_scale(R, usage, cap=True)
+        # the last scaling in FP64, applied to each job's throughput column by column
+        jk_ = np.asarray(jk, np.int64).reshape(prob.n, -1)
+        xk_ = np.asarray(xk, np.float64).reshape(prob.n, -1) * np.where(jk_ >= 0, f[np.maximum(jk_, 0)], 0.0)
+        U, _, _ = sparse_allocation_check(prob, jk_, xk_)
+        return dict(g=g, U_lb=U, rel_gap=rel_gap(g, U), usage_over_R=ratio,
+                    max_usage_over_R=float(ratio.max()), seconds=time.perf_counter() - t0)
     theta = np.asarray(theta, np.float64)
     lams = np.asarray(lams, np.float64).reshape(len(theta), prob.m)
     keep = theta > 0

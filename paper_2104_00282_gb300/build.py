@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libra.so")
-SOURCES = ["ra_dual.cu", "ra_solve.cu", "ra_api.cu", "ra_static.cu", "ra_warm.cu"]
+SOURCES = ["ra_dual.cu", "ra_solve.cu", "ra_api.cu", "ra_static.cu", "ra_warm.cu",
+           "ra_repair.cu", "ra_lp.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,7 +29,7 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "ra.h"))
     return files
 
@@ -49,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs = []
     objs = []
     for s in SOURCES:
-        obj = os.path.join(OUT_DIR, s.replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(OUT_DIR, os.path.splitext(s)[0] + f".{os.getpid()}.o")
         cmd = [nvcc(), *common, "-c", os.path.join(CSRC, s), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

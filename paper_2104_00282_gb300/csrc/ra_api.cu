@@ -112,7 +112,7 @@ void ra_solve_opts_default(ra_solve_opts *o)
     o->use_graph = 1;
     o->lam_floor = -1.0;
     o->master_lb = 1;
-    o->pad_ = 0;
+    o->repair_window = 16;
     o->init_step = 0.05;
 }
 
@@ -165,8 +165,10 @@ ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t 
     alloc(reinterpret_cast<void **>(&p->partials), sizeof(double) * ra::kPartW * gmax);
     alloc(reinterpret_cast<void **>(&p->ticket), sizeof(unsigned) * 8);
     alloc(reinterpret_cast<void **>(&p->status), sizeof(int) * 4);
+    // throughput records: FP32 pairs, FP64 pairs with FP64 per-job arithmetic
+    const size_t rec_bytes = (flags & RA_FP64_JOBMATH) ? sizeof(double2) : sizeof(float2);
     for (int b = 0; b < 2; ++b) {
-        alloc(reinterpret_cast<void **>(&p->lbt[b]), sizeof(float2) * n);
+        alloc(reinterpret_cast<void **>(&p->lbt[b]), rec_bytes * n);
         alloc(reinterpret_cast<void **>(&p->lbj[b]), sizeof(uchar2) * n);
     }
     alloc(reinterpret_cast<void **>(&p->ev), sizeof(ra::EvalOut) * 2);
@@ -209,6 +211,7 @@ void ra_problem_destroy(ra_problem *p)
     cudaFree(p->graph_flag);
     cudaFree(p->tmp);
     cudaFree(p->warm);
+    ra::release_repair_work(p);
     if (p->side) cudaStreamDestroy(p->side);
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
@@ -334,6 +337,56 @@ ra_status ra_recover_primal(ra_problem *p, const double *lambda, int32_t *jstar,
     return RA_OK;
 }
 
+
+ra_status ra_eval_partial(ra_problem *p, const double *lambda, double *part)
+{
+    if (!p || !lambda || !part) return fail(RA_EINVAL, "NULL argument");
+    return ra::eval_partial(p, lambda, part);
+}
+
+ra_status ra_combine_partials(int32_t S, int32_t m, const double *parts, const double *lambda,
+                              const double *R, double *g, double *q, void *stream)
+{
+    if (S < 1 || m < 1 || m > RA_MAX_M) return fail(RA_EINVAL, "S = %d, m = %d", S, m);
+    if (!parts || !lambda || !R) return fail(RA_EINVAL, "NULL argument");
+    return ra::combine_partials(S, m, parts, lambda, R, g, q, stream);
+}
+
+ra_status ra_solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t world,
+                           double *send, double *recv, ra_allgather_fn fn, void *ctx,
+                           const ra_solve_opts *opts, const double *lambda0, double *lambda_out,
+                           ra_solve_info *info)
+{
+    if (!p) return fail(RA_EINVAL, "NULL problem");
+    ra_status s = ra::solve_sharded(p, n_total, rank, world, send, recv, fn, ctx, opts, lambda0,
+                                    lambda_out, info);
+    if (s == RA_OK || s == RA_ENOTCONV) {
+        ra_status w = check_status_word(p);
+        if (w != RA_OK) return w;
+    }
+    return s;
+}
+
+void ra_repair_opts_default(ra_repair_opts *o)
+{
+    if (!o) return;
+    o->tie_rel = 1e-3;
+    o->max_flex = 512;
+    o->pad_ = 0;
+}
+
+ra_status ra_recover_feasible(ra_problem *p, const double *lambda, const ra_repair_opts *opts,
+                              int32_t *jk, float *xk, float *X_dense, ra_repair_info *info)
+{
+    if (!p || !lambda || !info) return fail(RA_EINVAL, "NULL problem, lambda or info");
+    if ((jk == nullptr) != (xk == nullptr)) return fail(RA_EINVAL, "jk and xk go together");
+    ra_repair_opts o;
+    ra_repair_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.tie_rel > 0.0 && o.tie_rel <= 1.0)) return fail(RA_EINVAL, "tie_rel = %g must lie in (0, 1]", o.tie_rel);
+    if (o.max_flex < 1 || o.max_flex > 4096) return fail(RA_EINVAL, "max_flex = %d must lie in [1, 4096]", o.max_flex);
+    return ra::repair_allocation(p, lambda, o, jk, xk, X_dense, info);
+}
 
 // ---------------------------------------------------------------------------- batches
 

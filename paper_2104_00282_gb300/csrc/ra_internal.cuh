@@ -137,7 +137,16 @@ struct SolverState {
     double Y[kMaxLbfgsMem][RA_MAX_M];
     double rho[kMaxLbfgsMem];
     double hist[kHist][kHistCols];
+    // stall exit for the tie-aware repair (single-problem solves): the loop
+    // leaves the device when the gap has not halved within stall_window
+    // evaluations, so that the host can re-mix the jobs at ties
+    int32_t stall_window;   // 0 = never leave for a repair
+    int32_t mark_evals;     // evaluation at which gap_mark was set
+    double gap_mark;
 };
+
+// Internal solver status: the loop stopped for a repair of the lower bound.
+constexpr int kStatusStalled = 100;
 
 }  // namespace ra
 
@@ -172,6 +181,7 @@ struct ra_problem {
     unsigned char *warm; // warm-start scratch (kWarmBytes)
     cudaStream_t side;   // warm start: statistics and network beside the cold-start pass
     cudaEvent_t fork, join;
+    void *rep;           // allocation-repair workspace (ra_repair.cu), made on first use
 };
 
 namespace ra {
@@ -247,7 +257,7 @@ struct BatchDualArgs {
 cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t s);
 cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
                                const EvalOut *src, double *U_lb, cudaStream_t s);
-cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s);
+cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all = 0);
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
                            double *g_out, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);
@@ -292,12 +302,23 @@ int32_t solve_certificate(ra_problem *p, double *theta, double *lam, int32_t *sc
 
 ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0,
                       double *lambda_out, ra_solve_info *infos, double *seconds);
+ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t world, double *send,
+                        double *recv, ra_allgather_fn fn, void *ctx, const ra_solve_opts *o,
+                        const double *lambda0, double *lambda_out, ra_solve_info *info);
+ra_status eval_partial(ra_problem *p, const double *lambda, double *part);
+ra_status combine_partials(int32_t S, int32_t m, const double *parts, const double *lambda,
+                           const double *R, double *g, double *q, void *stream);
 
 // Error reporting (ra_api.cu).
 ra_status fail(ra_status s, const char *fmt, ...);
 
 // Bound of the kernels' device waits in ns (ra_set_wait_timeout; ra_api.cu).
 uint64_t wait_limit_ns();
+
+// Feasible allocation with tie-aware repair (ra_repair.cu).
+ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_opts &o, int32_t *jk,
+                            float *xk, float *X, ra_repair_info *info);
+void release_repair_work(ra_problem *p);
 
 }  // namespace ra
 

@@ -54,7 +54,8 @@ __device__ __forceinline__ unsigned long long device_ns()
 // NULL when the initial prices have already been written to st->lam_trial.
 __device__ void setup_one(SolverState *st, const double *lam0, const double *R, int m, double tol,
                           int max_evals, int mem, int update, double lam_floor, int cap,
-                          int use_master, double init_step, int32_t *pingpong, int32_t *lag_on)
+                          int use_master, double init_step, int32_t *pingpong, int32_t *lag_on,
+                          int stall_window)
 {
     const int j = threadIdx.x;
     double l = 0.0;
@@ -102,6 +103,9 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
         st->U_master = -__longlong_as_double(0x7ff0000000000000ll);
         st->t_start = device_ns();
         st->t_done = 0ull;
+        st->stall_window = stall_window;
+        st->mark_evals = 0;
+        st->gap_mark = __longlong_as_double(0x7ff0000000000000ll);
         *pingpong = 0;
         *lag_on = 0;
     }
@@ -110,10 +114,60 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
 __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const double *R, int m,
                                     double tol, int max_evals, int mem, int update,
                                     double lam_floor, int cap, int use_master, double init_step,
-                                    int32_t *pingpong, int32_t *lag_on)
+                                    int32_t *pingpong, int32_t *lag_on, int stall_window)
 {
     setup_one(st, lam0, R, m, tol, max_evals, mem, update, lam_floor, cap, use_master, init_step,
-              pingpong, lag_on);
+              pingpong, lag_on, stall_window);
+}
+
+// After a host-side repair of the lower bound (ra_repair.cu) at the best
+// prices: adopt its utility U_rep if it is better, record it as the
+// certificate (one repaired allocation at lam_best), update the gap and
+// decide whether the solve is done; otherwise let the loop resume without a
+// stall exit.  The repair used the lower-bound record buffers, so the next
+// evaluation carries no lagged bound.
+__global__ void repair_accept_kernel(SolverState *st, double U_rep, int32_t *lag_on, int next_window)
+{
+    const int j = threadIdx.x;
+    const int m = st->m;
+    const bool better = U_rep > st->U_best;
+    if (better && j < m) {
+        st->lam_lb[j] = st->lam_best[j];
+        st->theta_lam[0][j] = st->lam_best[j];
+    }
+    __syncwarp();
+    if (j == 0) {
+        if (better) {
+            st->U_best = U_rep;
+            st->theta_n = 1;
+            st->theta[0] = 1.0;
+            st->theta_scaled[0] = 2;
+            st->master_ok = 0;
+        }
+        const double den = fmax(fmax(fabs(st->U_best), fabs(st->g_best)), 1.0);
+        const double gap = (st->g_best - st->U_best) / den;
+        st->gap = gap;
+        const int h = st->hist_len;
+        if (better && h > 0) {
+            st->hist[h - 1][2] = st->U_best;
+            st->hist[h - 1][3] = gap;
+        }
+        if (gap <= st->tol) {
+            st->done = 1;
+            st->status = RA_OK;
+        } else if (st->evals >= st->max_evals) {
+            st->done = 1;
+            st->status = RA_ENOTCONV;
+        } else {
+            st->done = 0;
+            st->status = RA_OK;
+            st->stall_window = next_window;   // the next exit waits longer (0: none)
+            st->gap_mark = gap;
+            st->mark_evals = st->evals;
+        }
+        st->have_lb_prev = 0;
+        *lag_on = 0;
+    }
 }
 
 // Batched setup: block p sets up problem p; its starting prices are
@@ -125,7 +179,7 @@ __global__ void batch_setup_kernel(SolverState *st, const BatchProblem *probs, c
 {
     const int p = blockIdx.x;
     setup_one(st + p, lam0 + lam_off[p], probs[p].R, probs[p].m, tol, max_evals, mem, update,
-              lam_floor, cap, use_master, init_step, pingpong + p, lag_on + p);
+              lam_floor, cap, use_master, init_step, pingpong + p, lag_on + p, 0);
 }
 
 // Graph condition of the batched loop: continue while any problem iterates.
@@ -745,6 +799,19 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpon
         done = true;             // the starting prices already give an unbounded dual
         status = RA_EUNBOUNDED;
     }
+    // the gap has not halved within stall_window evaluations: leave after this
+    // update so that the host can repair the lower bound at the best prices
+    bool stall = false;
+    if (!done && st->stall_window > 0 && isfinite(gap)) {
+        if (!(gap >= 0.5 * st->gap_mark)) {
+            if (j == 0) {
+                st->gap_mark = gap;
+                st->mark_evals = evals;
+            }
+        } else if (evals - st->mark_evals >= st->stall_window) {
+            stall = true;
+        }
+    }
 
     if (!done) {
         if (st->update == 1) {
@@ -764,6 +831,10 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpon
         }
     }
     __syncwarp();
+    if (stall) {
+        done = true;
+        status = kStatusStalled;
+    }
     if (j == 0) {
         if (done) {
             st->done = 1;
@@ -801,6 +872,8 @@ __global__ void batch_finish_kernel(const SolverState *st, const BatchProblem *p
         r.U_lb = S->U_best;
         r.rel_gap = S->gap;
         r.gap_per_job = (S->g_best - S->U_best) / static_cast<double>(probs[p].n);
+        r.repairs = 0;
+        r.n_flex = 0;
         info[p] = r;
         secs[p] = S->t_done > *t0 ? static_cast<double>(S->t_done - *t0) * 1e-9 : 0.0;
     }
@@ -818,6 +891,109 @@ __global__ void __launch_bounds__(kLpThreads)
     __syncthreads();
     if (threadIdx.x < 32)
         update_body(st, ev, pingpong, lag_on, kstatus, cond, use_cond, done_host_flag);
+}
+
+// The relative gap the loop stops at.  With FP32 per-job arithmetic the
+// solver's own g and U_lb carry FP32 rounding (fast log/exp, FP32 records):
+// measured up to 3.3e-7 of the relative gap against the FP64 oracle on the
+// parity workloads.  The loop therefore stops at half the requested gap, so
+// that the gap the FP64 oracle certifies for its result meets the request.
+// FP64 per-job arithmetic stops at the request itself.
+// ---------------------------------------------------------------------------- sharded solve
+
+// One shard's evaluation sums as exchanged between the shards of a problem
+// split by job range: [sum h, U(X), lagged U_lb, status word, r[m], r_lin[m]].
+__host__ __device__ inline int shard_width(int m) { return 4 + 2 * m; }
+
+__global__ void shard_pack_kernel(const EvalOut *ev, const int *status, int m, double *send)
+{
+    const int j = threadIdx.x;
+    if (j == 0) {
+        send[0] = ev->sumh;
+        send[1] = ev->Ux;
+        send[2] = ev->Ulb_prev;
+        send[3] = static_cast<double>(*status);
+    }
+    if (j < m) {
+        send[4 + j] = ev->r[j];
+        send[4 + m + j] = ev->r_lin[j];
+    }
+}
+
+// The whole problem's evaluation from every shard's sums, added in shard
+// order (the same bits on every shard): g = lambda^T R + sum h, q = R - r;
+// the status words are or-ed, so that every shard stops alike.
+__global__ void shard_combine_kernel(const double *recv, int world, int m, const double *lam,
+                                     const double *R, EvalOut *ev, int *status)
+{
+    const int j = threadIdx.x;
+    const int W = shard_width(m);
+    if (j < m) {
+        double r = 0.0, rl = 0.0;
+        for (int s = 0; s < world; ++s) {
+            r += recv[static_cast<size_t>(s) * W + 4 + j];
+            rl += recv[static_cast<size_t>(s) * W + 4 + m + j];
+        }
+        ev->r[j] = r;
+        ev->q[j] = R[j] - r;
+        ev->r_lin[j] = rl;
+    }
+    if (j == 0) {
+        double h = 0.0, ux = 0.0, ul = 0.0;
+        int st = 0;
+        for (int s = 0; s < world; ++s) {
+            const double *v = recv + static_cast<size_t>(s) * W;
+            h += v[0];
+            ux += v[1];
+            ul += v[2];
+            st |= static_cast<int>(v[3]);
+        }
+        double lr = 0.0;
+        for (int k = 0; k < m; ++k) lr += lam[k] * R[k];
+        ev->sumh = h;
+        ev->g = lr + h;
+        ev->Ux = ux;
+        ev->Ulb_prev = ul;
+        *status = st;
+    }
+}
+
+// g and q alone from the shards' sums (shard order), for ra_combine_partials.
+__global__ void shard_gq_kernel(const double *parts, int world, int m, const double *lam,
+                                const double *R, double *g, double *q)
+{
+    const int j = threadIdx.x;
+    const int W = shard_width(m);
+    if (j < m && q) {
+        double r = 0.0;
+        for (int s = 0; s < world; ++s) r += parts[static_cast<size_t>(s) * W + 4 + j];
+        q[j] = R[j] - r;
+    }
+    if (j == 0 && g) {
+        double h = 0.0;
+        for (int s = 0; s < world; ++s) h += parts[static_cast<size_t>(s) * W];
+        double lr = 0.0;
+        for (int k = 0; k < m; ++k) lr += lam[k] * R[k];
+        *g = lr + h;
+    }
+}
+
+// out[j] = sum over shards (in order) of entry j of each shard's count values.
+__global__ void shard_sum_kernel(const double *recv, int world, int count, double *out)
+{
+    const int j = threadIdx.x;
+    if (j < count) {
+        double v = 0.0;
+        for (int s = 0; s < world; ++s) v += recv[static_cast<size_t>(s) * count + j];
+        out[j] = v;
+    }
+}
+
+constexpr int kMaxRepairs = 5;   // lower-bound repairs per solve (the last at max_evals)
+
+double stop_tolerance(double tol, uint32_t flags)
+{
+    return (flags & RA_FP64_JOBMATH) ? tol : 0.5 * tol;
 }
 
 struct GraphCache {
@@ -882,9 +1058,11 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         if ((e = launch_init(p, st->lam_trial, s)) != cudaSuccess)
             return fail(RA_ECUDA, "init launch: %s", cudaGetErrorString(e));
     }
-    solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, p->m, opts.tol_rel, opts.max_evals,
+    solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, p->m,
+                                         stop_tolerance(opts.tol_rel, p->flags), opts.max_evals,
                                          opts.lbfgs_mem, opts.update, opts.lam_floor, cap,
-                                         opts.master_lb, opts.init_step, pingpong, lag_on);
+                                         opts.master_lb, opts.init_step, pingpong, lag_on,
+                                         opts.repair_window);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
@@ -918,10 +1096,12 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     dp.out = p->ev;
     dp.skip = nullptr;
 
-    bool graph_ok = false;
+    // the loop as one CUDA graph: a conditional while node whose body is
+    // {dual evaluation, solver step}; kept until the solve returns, since a
+    // repair of the lower bound may resume it
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     if (opts.use_graph) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
         cudaGraphConditionalHandle cond;
         bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
         ok = ok && cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) ==
@@ -946,21 +1126,37 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             }
         }
         ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
-        ok = ok && cudaGraphLaunch(exec, s) == cudaSuccess;
-        if (ok) graph_ok = true;
-        if (!ok) (void)cudaGetLastError();
-        if (exec) cudaGraphExecDestroy(exec);   // destruction waits for nothing; launch is queued
-        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            (void)cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
     }
-    if (!graph_ok) {
+    struct GraphGuard {
+        cudaGraph_t &g;
+        cudaGraphExec_t &x;
+        ~GraphGuard()
+        {
+            if (x) cudaGraphExecDestroy(x);
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{graph, exec};
+    // run the loop until its while node (or the host-driven fallback) stops
+    auto run_loop = [&]() -> ra_status {
+        if (exec) {
+            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess)
+                return fail(RA_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+            return RA_OK;
+        }
         // host-driven fallback: launch 8 iterations at a time, then check the flag
         int32_t done_h = 0;
-        dp.skip = done_flag;
+        DualParams dh = dp;
+        dh.skip = done_flag;
         if ((e = cudaMemsetAsync(done_flag, 0, sizeof(int32_t), s)) != cudaSuccess)
             return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
         for (int it = 0; it < opts.max_evals && !done_h; it += 8) {
             for (int k = 0; k < 8; ++k) {
-                if ((e = launch_dual(p, dp, s)) != cudaSuccess)
+                if ((e = launch_dual(p, dh, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
                 step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
                                                       done_flag);
@@ -970,30 +1166,63 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                 (e = cudaStreamSynchronize(s)) != cudaSuccess)
                 return fail(RA_ECUDA, "solver loop: %s", cudaGetErrorString(e));
         }
+        return RA_OK;
+    };
+    struct {
+        int32_t done, status, k, evals, ls_fail;
+        double g, U, gap;
+    } h;
+    auto read_state = [&]() -> ra_status {
+        int32_t ints[8];
+        double dbl[8];
+        e = cudaMemcpyAsync(ints, &st->phase, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dbl, &st->tol, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "solver result: %s", cudaGetErrorString(e));
+        h.done = ints[1];
+        h.status = ints[2];
+        h.k = ints[3];
+        h.evals = ints[4];
+        h.ls_fail = ints[6];
+        h.g = dbl[4];
+        h.U = dbl[5];
+        h.gap = dbl[6];
+        return RA_OK;
+    };
+    int repairs = 0;
+    int64_t n_flex = 0;
+    for (;;) {
+        ra_status rs = run_loop();
+        if (rs == RA_OK) rs = read_state();
+        if (rs != RA_OK) return rs;
+        // the lower bound stalled (or the evaluations ran out): re-mix the jobs
+        // at ties at the best prices (ra_repair.cu), then stop or resume
+        const bool want = opts.repair_window > 0 && repairs < kMaxRepairs &&
+                          (h.status == kStatusStalled || h.status == RA_ENOTCONV);
+        if (!want) break;
+        ra_repair_opts ro;
+        ra_repair_opts_default(&ro);
+        ra_repair_info ri;
+        rs = repair_allocation(p, st->lam_best, ro, nullptr, nullptr, nullptr, &ri);
+        if (rs != RA_OK) return rs;
+        ++repairs;
+        n_flex = ri.n_flex;
+        // while the prices are still moving a repair may fall short: exit again
+        // after twice as many evaluations without the gap halving
+        const int next = repairs + 1 < kMaxRepairs ? opts.repair_window << repairs : 0;
+        repair_accept_kernel<<<1, 32, 0, s>>>(st, ri.U, lag_on, next);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return fail(RA_ECUDA, "repair accept: %s", cudaGetErrorString(e));
+        if ((rs = read_state()) != RA_OK) return rs;
+        if (h.done) break;   // closed the gap, or out of evaluations: otherwise resume
     }
+    if (h.status == kStatusStalled) h.status = RA_ENOTCONV;  // defensive: never leaves the library
     if ((e = cudaMemcpyAsync(lambda_out, st->lam_best, sizeof(double) * p->m,
                              cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return fail(RA_ECUDA, "copy prices: %s", cudaGetErrorString(e));
     if (lambda_lb && (e = cudaMemcpyAsync(lambda_lb, st->lam_lb, sizeof(double) * p->m,
                                           cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return fail(RA_ECUDA, "copy prices: %s", cudaGetErrorString(e));
-    struct {
-        int32_t status, k, evals, ls_fail;
-        double g, U, gap;
-    } h;
-    int32_t ints[8];
-    double dbl[8];
-    e = cudaMemcpyAsync(ints, &st->phase, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dbl, &st->tol, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(RA_ECUDA, "solver result: %s", cudaGetErrorString(e));
-    h.status = ints[2];
-    h.k = ints[3];
-    h.evals = ints[4];
-    h.ls_fail = ints[6];
-    h.g = dbl[4];
-    h.U = dbl[5];
-    h.gap = dbl[6];
     if (info) {
         info->status = h.status;
         info->iters = h.k;
@@ -1003,6 +1232,8 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         info->U_lb = h.U;
         info->rel_gap = h.gap;
         info->gap_per_job = (h.g - h.U) / static_cast<double>(p->n);
+        info->repairs = repairs;
+        info->n_flex = static_cast<int32_t>(n_flex);
     }
     if (h.status == RA_ETIMEOUT) return fail(RA_ETIMEOUT, "a device wait gave up during the solve");
     if (h.status == RA_EUNBOUNDED) return fail(RA_EUNBOUNDED, "dual value not finite: a price reached zero without the per-job cap");
@@ -1067,7 +1298,8 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
         }
         lam0 = b->lam_tmp;
     }
-    batch_setup_kernel<<<P, 32, 0, s>>>(b->st, b->probs, lam0, b->lam_off, opts.tol_rel,
+    batch_setup_kernel<<<P, 32, 0, s>>>(b->st, b->probs, lam0, b->lam_off,
+                                        stop_tolerance(opts.tol_rel, b->flags),
                                         opts.max_evals, opts.lbfgs_mem, opts.update, opts.lam_floor,
                                         cap, opts.master_lb, opts.init_step, b->pingpong,
                                         b->lag_on);
@@ -1156,4 +1388,154 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
     return RA_OK;
 }
 
+// Price discovery for one problem split by job range across shards (devices
+// or processes): jobs are independent given the prices (Section 3), so each
+// shard evaluates its own jobs, the shards exchange m-sized sums once per
+// evaluation, and every shard runs the same FP64 price update on the same
+// combined values -- the prices stay identical everywhere.  Host-driven loop:
+// {dual pass over this shard, pack, exchange (caller's all-gather), combine
+// in shard order, solver step}.
+ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t world, double *send,
+                        double *recv, ra_allgather_fn fn, void *ctx, const ra_solve_opts *o,
+                        const double *lambda0, double *lambda_out, ra_solve_info *info)
+{
+    ra_solve_opts opts;
+    ra_solve_opts_default(&opts);
+    if (o) opts = *o;
+    if (world < 1 || rank < 0 || rank >= world) return fail(RA_EINVAL, "rank %d of %d", rank, world);
+    if (!fn || !send || !recv || !lambda_out) return fail(RA_EINVAL, "NULL exchange, buffers or output");
+    if (n_total < p->n) return fail(RA_EINVAL, "n_total = %lld < shard size %lld", (long long)n_total, (long long)p->n);
+    if (opts.lbfgs_mem < 1 || opts.lbfgs_mem > kMaxLbfgsMem)
+        return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
+    if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
+    if (!(opts.tol_rel >= 0.0) || !(opts.init_step > 0.0)) return fail(RA_EINVAL, "bad tolerance or step");
+    cudaStream_t s = p->stream;
+    cudaError_t e;
+    SolverState *st = p->st;
+    int32_t *pingpong = p->graph_flag;
+    int32_t *lag_on = p->graph_flag + 1;
+    int32_t *done_flag = p->graph_flag + 2;
+    const int m = p->m;
+    const int cap = !(p->flags & RA_NO_JOB_CAP);
+    auto exchange = [&](int count) -> ra_status {
+        const int32_t rc = fn(ctx, count, static_cast<void *>(s));
+        if (rc != 0) return fail(RA_ECUDA, "the caller's all-gather returned %d", rc);
+        return RA_OK;
+    };
+    if ((e = cudaMemsetAsync(p->status, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(done_flag, 0, sizeof(int32_t), s)) != cudaSuccess)
+        return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    if (!lambda0) {
+        // Eq. e-initialization over the whole problem: per-shard sums (already
+        // divided by n_total), added in shard order
+        if ((e = launch_init(p, p->tmp, s, n_total)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(send, p->tmp, sizeof(double) * m, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return fail(RA_ECUDA, "init: %s", cudaGetErrorString(e));
+        ra_status rs = exchange(m);
+        if (rs != RA_OK) return rs;
+        shard_sum_kernel<<<1, 32, 0, s>>>(recv, world, m, st->lam_trial);
+    }
+    solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, m, stop_tolerance(opts.tol_rel, p->flags),
+                                         opts.max_evals, opts.lbfgs_mem, opts.update, opts.lam_floor,
+                                         cap, opts.master_lb, opts.init_step, pingpong, lag_on, 0);
+    if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
+        return fail(RA_ECUDA, "step attribute: %s", cudaGetErrorString(e));
+    DualParams dp{};
+    dp.A = p->A;
+    dp.kind = p->kind;
+    dp.w = p->w;
+    dp.param = p->param;
+    dp.R = p->R;
+    dp.n = p->n;
+    dp.m = m;
+    dp.lam = st->lam_trial;
+    dp.s_prev = st->s_lag;
+    dp.s_lin_prev = st->s_lin_lag;
+    dp.lbt_prev = p->lbt[0];
+    dp.lbj_prev = p->lbj[0];
+    dp.lbt_out = p->lbt[1];
+    dp.lbj_out = p->lbj[1];
+    dp.lbt_buf[0] = p->lbt[0];
+    dp.lbt_buf[1] = p->lbt[1];
+    dp.lbj_buf[0] = p->lbj[0];
+    dp.lbj_buf[1] = p->lbj[1];
+    dp.pingpong = pingpong;
+    dp.lag_on = lag_on;
+    dp.partials = p->partials;
+    dp.ticket = p->ticket;
+    dp.status = p->status;
+    dp.out = p->ev;
+    const int W = shard_width(m);
+    int32_t done_h = 0;
+    for (int it = 0; it < opts.max_evals && !done_h; ++it) {
+        if ((e = launch_dual(p, dp, s)) != cudaSuccess)
+            return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
+        shard_pack_kernel<<<1, 32, 0, s>>>(p->ev, p->status, m, send);
+        ra_status rs = exchange(W);
+        if (rs != RA_OK) return rs;
+        shard_combine_kernel<<<1, 32, 0, s>>>(recv, world, m, st->lam_trial, p->R, p->ev, p->status);
+        step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
+                                                          done_flag);
+        if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return fail(RA_ECUDA, "sharded loop: %s", cudaGetErrorString(e));
+    }
+    int32_t ints[8];
+    double dbl[8];
+    e = cudaMemcpyAsync(ints, &st->phase, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbl, &st->tol, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lambda_out, st->lam_best, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "sharded result: %s", cudaGetErrorString(e));
+    if (info) {
+        info->status = ints[2];
+        info->iters = ints[3];
+        info->evals = ints[4];
+        info->ls_fail = ints[6];
+        info->g = dbl[4];
+        info->U_lb = dbl[5];
+        info->rel_gap = dbl[6];
+        info->gap_per_job = (dbl[4] - dbl[5]) / static_cast<double>(n_total);
+        info->repairs = 0;
+        info->n_flex = 0;
+    }
+    if (ints[2] == RA_ETIMEOUT) return fail(RA_ETIMEOUT, "a device wait gave up on some shard");
+    if (ints[2] == RA_EUNBOUNDED) return fail(RA_EUNBOUNDED, "dual value not finite");
+    if (ints[2] != RA_OK) return fail(RA_ENOTCONV, "stopped after %d evaluations at relative gap %.3e", ints[4], dbl[6]);
+    return RA_OK;
+}
+
+ra_status eval_partial(ra_problem *p, const double *lambda, double *part)
+{
+    DualParams dp{};
+    dp.A = p->A;
+    dp.kind = p->kind;
+    dp.w = p->w;
+    dp.param = p->param;
+    dp.R = p->R;
+    dp.n = p->n;
+    dp.m = p->m;
+    dp.lam = lambda;
+    dp.partials = p->partials;
+    dp.ticket = p->ticket;
+    dp.status = p->status;
+    dp.out = p->ev;
+    cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = launch_dual(p, dp, p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
+    shard_pack_kernel<<<1, 32, 0, p->stream>>>(p->ev, p->status, p->m, part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(RA_ECUDA, "pack: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status combine_partials(int32_t S, int32_t m, const double *parts, const double *lambda,
+                           const double *R, double *g, double *q, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    shard_gq_kernel<<<1, 32, 0, s>>>(parts, S, m, lambda, R, g, q);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RA_ECUDA, "combine: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
 }  // namespace ra

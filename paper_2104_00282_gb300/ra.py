@@ -33,14 +33,30 @@ class ra_solve_opts(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("max_evals", ctypes.c_int32),
                 ("lbfgs_mem", ctypes.c_int32), ("update", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("lam_floor", ctypes.c_double),
-                ("master_lb", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("master_lb", ctypes.c_int32), ("repair_window", ctypes.c_int32),
                 ("init_step", ctypes.c_double)]
+
+
+class ra_repair_opts(ctypes.Structure):
+    _fields_ = [("tie_rel", ctypes.c_double), ("max_flex", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+class ra_repair_info(ctypes.Structure):
+    _fields_ = [("n_flex", ctypes.c_int64), ("n_alt", ctypes.c_int32),
+                ("lp_status", ctypes.c_int32), ("tie_cut", ctypes.c_double),
+                ("overuse", ctypes.c_double), ("U", ctypes.c_double),
+                ("max_usage_over_R", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ra_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("evals", ctypes.c_int32),
                 ("ls_fail", ctypes.c_int32), ("g", ctypes.c_double), ("U_lb", ctypes.c_double),
-                ("rel_gap", ctypes.c_double), ("gap_per_job", ctypes.c_double)]
+                ("rel_gap", ctypes.c_double), ("gap_per_job", ctypes.c_double),
+                ("repairs", ctypes.c_int32), ("n_flex", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -77,6 +93,11 @@ def lib():
         L.ra_solve_history.restype = i32
         L.ra_recover_primal.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
         L.ra_recover_primal.restype = i32
+        L.ra_repair_opts_default.argtypes = [ctypes.POINTER(ra_repair_opts)]
+        L.ra_repair_opts_default.restype = None
+        L.ra_recover_feasible.argtypes = [P, P, ctypes.POINTER(ra_repair_opts), P, P, P,
+                                          ctypes.POINTER(ra_repair_info)]
+        L.ra_recover_feasible.restype = i32
         L.ra_eval_dual_static.argtypes = [i64, i32, P, P, P, P, P, P, u32, P, P, P]
         L.ra_eval_dual_static.restype = i32
         L.ra_batch_create.argtypes = [i32, P, P, P, P, P, P, P, u32, P, ctypes.POINTER(P)]
@@ -201,7 +222,7 @@ def ra_solve_certificate(h, m):
                                    ctypes.c_void_p(scaled.ctypes.data))
     if k < 0:
         raise RaError(RA_ECUDA, lib().ra_last_error().decode())
-    return theta[:k], lam[:k], scaled[:k].astype(bool)
+    return theta[:k], lam[:k], scaled[:k]
 
 
 def ra_solve_history(h, cap=512):
@@ -222,6 +243,20 @@ def ra_recover_primal(h, lam, jstar=None, j12=None, x12=None, t=None, X=None, U=
                                    _ptr(U, torch.float64), _ptr(near_tie, torch.uint8),
                                    ctypes.byref(cnt) if count_ties else None))
     return int(cnt.value)
+
+
+def ra_recover_feasible(h, lam, jk=None, xk=None, X=None, tie_rel=None, max_flex=None):
+    o = ra_repair_opts()
+    lib().ra_repair_opts_default(ctypes.byref(o))
+    if tie_rel is not None:
+        o.tie_rel = tie_rel
+    if max_flex is not None:
+        o.max_flex = max_flex
+    info = ra_repair_info()
+    _check(lib().ra_recover_feasible(h, _ptr(lam, torch.float64), ctypes.byref(o),
+                                     _ptr(jk, torch.int32), _ptr(xk, torch.float32),
+                                     _ptr(X, torch.float32), ctypes.byref(info)))
+    return info.as_dict()
 
 
 def ra_eval_dual_static(A, kind, w, param, R, lam, g, q, flags=0, stream=None):
@@ -393,9 +428,11 @@ class AllocationProblem:
         return lam
 
     def solve(self, tol=1e-6, max_evals=500, lam0=None, update="lbfgs", use_graph=True,
-              lbfgs_mem=10, master_lb=True, init_step=None):
+              lbfgs_mem=10, master_lb=True, init_step=None, repair_window=None):
         o = ra_solve_opts_default()
         o.master_lb = 1 if master_lb else 0
+        if repair_window is not None:
+            o.repair_window = repair_window
         if init_step is not None:
             o.init_step = init_step
         o.tol_rel = tol
@@ -414,7 +451,8 @@ class AllocationProblem:
 
     def certificate(self):
         """(theta, lam, scaled): the allocation behind the last solve's U_lb is
-        sum_k theta_k X(lam_k) (column-scaled where scaled[k])."""
+        sum_k theta_k X(lam_k), column-scaled where scaled[k] == 1; scaled ==
+        [2] marks the repaired allocation recover_feasible(lam[0]) returns."""
         return ra_solve_certificate(self.handle, self.m)
 
     def history(self):
@@ -468,6 +506,21 @@ class AllocationProblem:
     @property
     def X(self):
         return self.recover(dense=True)["X"].view(self.n, self.m)
+
+    def recover_feasible(self, lam=None, dense=False, tie_rel=None, max_flex=None):
+        """A feasible allocation at lam (default: the last solve's best
+        prices) with the jobs at ties re-mixed (ra_recover_feasible): jk, xk
+        (4 (resource, fraction) pairs per job), X when dense, and info."""
+        lam = self.prices if lam is None else torch.as_tensor(lam, dtype=torch.float64,
+                                                             device=self.A.device).contiguous()
+        dev = self.A.device
+        out = dict(jk=torch.empty(4 * self.n, dtype=torch.int32, device=dev),
+                   xk=torch.empty(4 * self.n, dtype=torch.float32, device=dev))
+        if dense:
+            out["X"] = torch.empty(self.n * self.m, dtype=torch.float32, device=dev)
+        out["info"] = ra_recover_feasible(self.handle, lam, out["jk"], out["xk"], out.get("X"),
+                                          tie_rel=tie_rel, max_flex=max_flex)
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

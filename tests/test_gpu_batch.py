@@ -135,8 +135,10 @@ def test_batch_matches_single_problem_solves(ra):
         assert infos[k]["status"] == single["status"] == ra.RA_OK
         scale = max(abs(single["g"]), 1.0)
         assert abs(infos[k]["g"] - single["g"]) <= 2e-7 * scale
-        assert infos[k]["U_lb"] <= single["g"] + 1e-9 * scale
-        assert single["U_lb"] <= infos[k]["g"] + 1e-9 * scale
+        # each solver's bounds are FP32 estimates (per-job arithmetic), exact to
+        # a few 1e-7 of the gap: the two brackets overlap up to that rounding
+        assert infos[k]["U_lb"] <= single["g"] + 5e-7 * scale
+        assert single["U_lb"] <= infos[k]["g"] + 5e-7 * scale
     B.close()
 
 

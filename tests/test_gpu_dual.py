@@ -23,7 +23,8 @@ from paper_2104_00282_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TIE = 1e-5
+TIE = 1e-5          # allocation ambiguity: another cost-curve point this close to the segment
+TIE_ARGMIN = 1e-6   # argmin exemption: the two best effective prices this close
 
 
 @pytest.fixture(scope="module")
@@ -97,7 +98,7 @@ def compare_eval(ra, O, prob, lam, cap=True, fp64=False, check_lb=True):
     A = prob.A.astype(np.float64)
     kind, w, par = prob.kind, prob.w.astype(np.float64), prob.param.astype(np.float64)
     amb = (ora[:, 8] < TIE) | (ora[:, 9] < TIE)
-    amb_ratio = ora[:, 7] < TIE
+    amb_ratio = ora[:, 7] < TIE_ARGMIN
     # t within the FP32 arithmetic's reach of a hull vertex: one side may keep a
     # sliver (< 1e-4) of the neighbouring resource; compare x, not the index set
     sliver = (ora[:, 4] >= 0) & (np.minimum(ora[:, 5], ora[:, 6]) < 1e-4)
@@ -130,7 +131,9 @@ def compare_eval(ra, O, prob, lam, cap=True, fp64=False, check_lb=True):
     aP = A[rows[two], j1[two]]
     aQ = A[rows[two], j2[two]]
     kappa[two] = np.maximum(aP, aQ) / np.maximum(np.abs(aQ - aP), 1e-30)
-    cond = (1e-15 if fp64 else 2e-6) * kappa
+    # x = (t - a_P)/(a_Q - a_P) amplifies t's error by kappa; t's FP32 error
+    # reaches a few 1e-6 for power utilities (fast log/exp, exponent 1/(1-p))
+    cond = (1e-15 if fp64 else 5e-6) * kappa
     lim = rt + rt * np.abs(X_ora) + cond[:, None]
     for X in (X_rec, X_eval):
         err = np.abs(X - X_ora)
@@ -168,7 +171,11 @@ def compare_eval(ra, O, prob, lam, cap=True, fp64=False, check_lb=True):
             assert U == U_exp, (U, U_exp)
         else:
             assert abs(U - U_exp) <= (2e-7 if fp64 else 3e-6) * (np.abs(uu).sum() + 1.0), (U, U_exp)
-    return dict(n_amb=int(amb.sum()), g=g)
+    # the exempted argmin count is small (near ties of FP32-rounded ratios)
+    # unless prices are zero, where free resources tie by construction
+    if lam.min() > 0:
+        assert int(amb_ratio.sum()) <= 10 + n // 1000, int(amb_ratio.sum())
+    return dict(n_amb=int(amb.sum()), n_argmin_exempt=int(amb_ratio.sum()), g=g)
 
 
 SHAPES = [(1, 4), (255, 3), (256, 8), (257, 32), (100_003, 1), (100_003, 4), (100_003, 5),
@@ -206,6 +213,17 @@ def test_hetero_recipe_full_size(ra, oracle):
     lam = oracle.init_prices(prob)
     compare_eval(ra, oracle, prob, lam)
     compare_eval(ra, oracle, prob, lam * W.random_prices(8, seed=1, lo=0.7, hi=1.4))
+
+
+@pytest.mark.parametrize("cap", [False, True])
+def test_large_recipe_many_tiles_per_cta(ra, oracle, cap):
+    """The large recipe at m = 32 with about ten 256-job tiles per CTA (and a
+    ragged tail): every ring stage is reused and its mbarrier phase flips
+    several times within one evaluation, as at n = 1e7."""
+    prob = W.config_large(n=1_200_007, m=32, seed=12)
+    lam = oracle.init_prices(prob, cap=cap)
+    r = compare_eval(ra, oracle, prob, lam, cap=cap)
+    assert r["n_argmin_exempt"] <= 200
 
 
 def test_plain_small_recipe_fp64(ra, oracle):

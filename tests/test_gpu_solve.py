@@ -38,49 +38,48 @@ def oracle():
 def certify(O, prob, P, cap=True):
     """Oracle-side certificate of the GPU's result (FP64): g at the GPU's best
     prices, and the utility of the GPU's lower-bound allocation -- the mixture
-    sum_k theta_k X(lam_k) (column-scaled where flagged) rebuilt by the oracle,
-    scaled once more to exact feasibility against FP32 rounding in the GPU's
-    usage sums."""
-    lam = P.prices.cpu().numpy()
-    g, _, _ = O.dual(prob, lam, cap=cap)
+    sum_k theta_k X(lam_k) (column-scaled where flagged) rebuilt by the oracle
+    and scaled once more by min(1, R/usage) to exact feasibility in FP64."""
     theta, lams, scaled = P.certificate()
     assert len(theta) >= 1 and abs(theta.sum() - 1.0) < 1e-9 and np.all(theta >= 0)
-    Xbar = np.zeros((prob.n, prob.m))
-    for th, l, sc in zip(theta, lams, scaled):
-        if th <= 0:
-            continue
-        X, _ = O.allocation(prob, l, cap=cap)
-        if sc:
-            Xs = X.sum(0)
-            s, s_lin = O.column_scales(prob.R, Xs, X[prob.kind >= 2].sum(0), cap)
-            X *= np.where((prob.kind >= 2)[:, None], s_lin[None, :], s[None, :])
-        Xbar += th * X
-    usage = Xbar.sum(0)
-    assert np.all(usage <= prob.R * (1 + 3e-6) + 1e-9), (usage, prob.R)
-    Xbar *= O.column_scale(prob.R, usage)[None, :]
-    lb = O.utility_of(prob, (prob.A.astype(np.float64) * Xbar).sum(1))
-    return g, lb, O.rel_gap(g, lb)
+    repaired = None
+    if 2 in list(scaled):   # the bound is a repaired allocation at lams[0]
+        assert len(theta) == 1
+        out = P.recover_feasible(lams[0])
+        repaired = (out["jk"].cpu().numpy(), out["xk"].cpu().numpy())
+    c = O.certify(prob, P.prices.cpu().numpy(), theta, lams, scaled, cap, repaired=repaired)
+    # constraint violation of the GPU's allocation: <= 1e-6 R_j
+    assert c["max_usage_over_R"] <= 1 + 1e-6, c["usage_over_R"]
+    return c["g"], c["U_lb"], c["rel_gap"]
 
 
 def price_err(lam, ref):
     return float(np.max(np.abs(lam - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
 
+# prices: "unique" -- the dual optimum is unique and sharp at this gap, prices
+# within 1e-5; "sqrt" -- unique but smooth, error of order sqrt(gap); None --
+# not unique (jobs at kinks or idle resources leave g flat in some direction)
 @pytest.mark.parametrize("make,tol,fp64,prices,cap", [
-    (lambda: W.config_hetero(n=200_000, m=8, seed=3), 1e-6, False, True, True),
-    (lambda: W.config_large(n=200_000, m=32, seed=3), 1e-6, False, True, True),
-    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.1), 1e-6, False, True, True),
-    (lambda: W.config_plain_small(), 1e-9, True, False, True),
-    (lambda: W.paper_medium(n=200_000, utility="target", seed=1), 1e-6, False, False, True),
-    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.25), 1e-6, False, False, True),
+    (lambda: W.config_hetero(n=200_000, m=8, seed=3), 1e-6, False, "unique", True),
+    (lambda: W.config_large(n=200_000, m=32, seed=3), 1e-6, False, "unique", True),
+    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.1), 1e-6, False, "sqrt", True),
+    (lambda: W.config_plain_small(), 1e-9, True, None, True),
+    (lambda: W.paper_medium(n=200_000, utility="target", seed=1), 1e-6, False, "sqrt", True),
+    (lambda: W.random_small(100_000, 5, seed=8, r_scale=0.25), 1e-6, False, None, True),
     # without the cap: log, power and linear-with-cap jobs (the split column
     # scaling of the lower bound), FP32 and FP64 job math
-    (lambda: W.config_large(n=150_000, m=32, seed=4), 1e-6, False, False, False),
-    (lambda: W.config_large(n=200_000, m=8, seed=5), 1e-6, True, False, False),
-    (lambda: W.config_hetero(n=150_000, m=16, seed=6), 1e-6, False, False, False),
+    (lambda: W.config_large(n=150_000, m=32, seed=4), 1e-6, False, "sqrt", False),
+    (lambda: W.config_large(n=200_000, m=8, seed=5), 1e-6, True, "sqrt", False),
+    (lambda: W.config_hetero(n=150_000, m=16, seed=6), 1e-6, False, "sqrt", False),
+    # few jobs per resource without the cap: the optimum needs jobs split
+    # between tied resources, which only the repair of the lower bound finds
+    (lambda: W.config_hetero(n=20_000, m=16, seed=8), 1e-6, False, "sqrt", False),
+    (lambda: W.random_small(3_000, 8, seed=9, kinds=(0, 1, 2)), 1e-6, False, None, False),
 ], ids=["hetero-200k-m8", "large-200k-m32", "mixed-100k-m5", "plain-small-fp64",
         "paper-medium-target", "degenerate-100k-m5", "large-150k-m32-nocap",
-        "large-200k-m8-nocap-fp64", "hetero-150k-m16-nocap"])
+        "large-200k-m8-nocap-fp64", "hetero-150k-m16-nocap", "hetero-20k-m16-nocap",
+        "mixed-3k-m8-nocap"])
 def test_solve_matches_oracle(ra, oracle, make, tol, fp64, prices, cap):
     prob = make()
     P = ra.AllocationProblem.from_numpy(prob, "cuda", fp64_jobmath=fp64, job_cap=cap)
@@ -88,22 +87,28 @@ def test_solve_matches_oracle(ra, oracle, make, tol, fp64, prices, cap):
     assert info["status"] == ra.RA_OK, info
     assert info["rel_gap"] <= tol
     ref = oracle.solve(prob, cap=cap, tol=min(tol, 1e-8) * 0.1, max_evals=2000)
-    # the GPU's bounds bracket the oracle's optimum
-    slack = 3e-6 if not fp64 else 1e-11
+    # the GPU's own bounds bracket the oracle's optimum, up to the FP32
+    # rounding of its per-job arithmetic (1e-6) or FP64 rounding
+    slack = 1e-6 if not fp64 else 1e-11
     scale = max(abs(ref.g), 1.0)
     assert info["g"] >= ref.U_lb - slack * scale
     assert info["U_lb"] <= ref.g + slack * scale
-    # the oracle certifies the GPU's prices in FP64
+    # the oracle certifies the GPU's result in FP64: the gap meets the tolerance
+    # and the allocation's utility (the primal objective) is within the
+    # tolerance of the optimum
     g, lb, gap = certify(oracle, prob, P, cap)
-    assert gap <= tol + (3e-6 if not fp64 else 1e-12), (g, lb, gap)
-    assert lb >= info["U_lb"] - (3e-6 if not fp64 else 1e-11) * scale   # Jensen, in FP64
-    # prices: the dual optimum need not be unique (jobs sitting at kinks make g
-    # flat in some directions), so the GPU's prices must be dual-optimal --
-    # g(lambda_gpu) within the tolerance of the oracle's optimum -- and close
-    # to the oracle's where g is strictly convex.
-    assert g <= ref.g + (tol + slack) * scale
-    if prices:
-        assert price_err(P.prices.cpu().numpy(), ref.lam) <= 1e-3
+    assert gap <= tol, (g, lb, gap)
+    assert ref.U_lb <= g + tol * scale            # the oracle's feasible point vs the GPU's g
+    if ref.converged:
+        assert (ref.g - lb) / scale <= tol, (ref.g, lb)
+        assert g <= ref.g + tol * scale
+    # prices: within 1e-5 where the dual optimum is unique and g has curvature
+    # at this gap (with the cap, prices pinned by capped jobs); elsewhere the
+    # price error of a point with dual gap eps is of order sqrt(eps) (g is
+    # quadratic about a smooth minimiser) -- see the FP64 test below
+    err = price_err(P.prices.cpu().numpy(), ref.lam)
+    if prices is not None:
+        assert err <= (1e-5 if prices == "unique" else 5e-3), err
     P.close()
 
 
@@ -185,3 +190,28 @@ def test_not_converged_is_reported(ra):
     info = P.solve(tol=1e-14, max_evals=3)
     P.close()
     assert info["status"] == ra.RA_ENOTCONV and info["evals"] == 3
+
+
+@pytest.mark.parametrize("make,cap", [
+    (lambda: W.config_hetero(n=100_000, m=8, seed=31), False),
+    (lambda: W.config_hetero(n=60_000, m=16, seed=32), False),
+    (lambda: W.random_small(80_000, 6, seed=33, kinds=(0, 1), r_scale=0.3), False),
+    (lambda: W.config_hetero(n=100_000, m=8, seed=34), True),
+], ids=["hetero-100k-m8-nocap", "hetero-60k-m16-nocap", "logpow-80k-m6-nocap", "hetero-100k-m8-cap"])
+def test_prices_match_oracle_fp64(ra, oracle, make, cap):
+    """Prices within 1e-5 relative of the oracle's where the dual optimum is
+    unique (log and power utilities: strictly concave, so the prices of a
+    Fisher-type market are unique).  The price error of a point whose dual
+    value is eps above the minimum is of order sqrt(eps / curvature), so this
+    needs a gap near 1e-13: FP64 per-job arithmetic, whose dual values are
+    exact to about 1e-14."""
+    prob = make()
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", fp64_jobmath=True, job_cap=cap)
+    info = P.solve(tol=1e-13, max_evals=3000)
+    lam = P.prices.cpu().numpy()
+    P.close()
+    assert info["status"] == ra.RA_OK, info
+    ref = oracle.solve(prob, cap=cap, tol=1e-13, max_evals=4000)
+    big = ref.lam > 1e-3 * ref.lam.max()
+    rel = np.abs(lam - ref.lam) / np.where(big, ref.lam, ref.lam.max())
+    assert rel.max() <= 1e-5, (rel.max(), info, ref.gap)
