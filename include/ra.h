@@ -144,6 +144,10 @@ typedef struct {
                              0 = off.  Default 16                                               */
     double init_step;     /* length of the first price step (and of a restarted gradient step)
                              as a fraction of |lambda|; default 0.05, smaller from a close start */
+    int32_t init_scale;   /* without the per-job cap and lambda0: 1 (default) scales the prices
+                             of Eq. e-initialization by the minimiser of g along their ray (one
+                             pass); 0 starts from Eq. e-initialization itself                  */
+    int32_t pad_;
 } ra_solve_opts;
 
 typedef struct {

@@ -53,6 +53,8 @@ def lib():
         L.ora_jobs.restype = i32
         L.ora_cost.argtypes = [i32, P, P, d, P]
         L.ora_cost.restype = d
+        L.ora_dual_blocks.argtypes = [i64, i32, P, P, P, P, P, i32, i32, P, i32]
+        L.ora_dual_blocks.restype = i32
         L.ora_mixture_utility.argtypes = [i64, i32, P, P, P, P, i32, P, P, P, P, i32, i32, P, i32]
         L.ora_mixture_utility.restype = i32
         _lib = L
@@ -139,6 +141,23 @@ def dual(prob, lam, cap=True, method="hull", nthreads=0, split=False):
     if split:
         return float(g[0]), r, float(U[0]), r_lin
     return float(g[0]), r, float(U[0])
+
+
+BLOCK = 4096   # jobs per partial sum of the oracle's evaluation
+
+
+def dual_blocks(prob, lam, cap=True, method="hull", nthreads=0):
+    """Per-block sums of the dual evaluation, blocks of BLOCK jobs in job
+    order: rows (sum h_i, sum u_i(t_i), r[m], r_lin[m]).  ``dual`` adds these
+    rows in block order."""
+    A, kind, w, par, _ = _arrays(prob)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    nb = (prob.n + BLOCK - 1) // BLOCK
+    part = np.zeros((max(nb, 1), 2 * prob.m + 2))
+    rc = lib().ora_dual_blocks(prob.n, prob.m, _p(A), _p(kind), _p(w), _p(par), _p(lam),
+                               int(bool(cap)), 0 if method == "hull" else 1, _p(part), nthreads)
+    assert rc == 0
+    return part[:nb]
 
 
 def column_scale(R, r, cap=True):

@@ -400,6 +400,24 @@ int ora_max_threads(void) { return nthreads_of(0); }
  *   g = lam^T R + sum_i h_i,  r = sum_i x_i,  U = sum_i u_i(t_i) (unscaled X).
  * Sums are formed per block of ORA_BLOCK jobs and then added in block order,
  * so the result does not depend on the thread count. */
+/* Per-block sums of the dual evaluation: block b holds jobs [b ORA_BLOCK,
+ * (b+1) ORA_BLOCK); part is nb x (2m + 2): sum h, sum u(t), r[m], r_lin[m]
+ * (the usage of the linear-utility jobs). */
+static void dual_blocks(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
+                        const float *par, const double *lam, int cap, int method, double *part,
+                        int nthreads);
+
+int ora_dual_blocks(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
+                    const float *par, const double *lam, int cap, int method, double *part,
+                    int nthreads)
+{
+    if (m <= 0 || m > ORA_MAXM || n < 0) return 1;
+    int64_t nb = (n + ORA_BLOCK - 1) / ORA_BLOCK;
+    memset(part, 0, sizeof(double) * (size_t)nb * (2 * m + 2));
+    dual_blocks(n, m, A, kind, w, par, lam, cap, method, part, nthreads);
+    return 0;
+}
+
 int ora_dual(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
              const float *par, const double *R, const double *lam, int cap, int method,
              double *g, double *r, double *U, double *r_lin, int nthreads)
@@ -409,6 +427,32 @@ int ora_dual(int64_t n, int m, const float *A, const uint8_t *kind, const float 
     int W = 2 * m + 2;   /* h, U, r[m], r_lin[m] (usage of linear-utility jobs) */
     double *part = (double *)calloc((size_t)(nb > 0 ? nb : 1) * W, sizeof(double));
     if (!part) return 2;
+    dual_blocks(n, m, A, kind, w, par, lam, cap, method, part, nthreads);
+    double sh = 0.0, su = 0.0;
+    for (int j = 0; j < m; ++j) r[j] = 0.0;
+    if (r_lin)
+        for (int j = 0; j < m; ++j) r_lin[j] = 0.0;
+    for (int64_t b = 0; b < nb; ++b) {
+        sh += part[b * W];
+        su += part[b * W + 1];
+        for (int j = 0; j < m; ++j) r[j] += part[b * W + 2 + j];
+        if (r_lin)
+            for (int j = 0; j < m; ++j) r_lin[j] += part[b * W + 2 + m + j];
+    }
+    double lr = 0.0;
+    for (int j = 0; j < m; ++j) lr += lam[j] * R[j];
+    *g = lr + sh;
+    if (U) *U = su;
+    free(part);
+    return 0;
+}
+
+static void dual_blocks(int64_t n, int m, const float *A, const uint8_t *kind, const float *w,
+                        const float *par, const double *lam, int cap, int method, double *part,
+                        int nthreads)
+{
+    int64_t nb = (n + ORA_BLOCK - 1) / ORA_BLOCK;
+    int W = 2 * m + 2;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads))
     for (int64_t b = 0; b < nb; ++b) {
         double a[ORA_MAXM], o[ORA_NOUT];
@@ -427,23 +471,6 @@ int ora_dual(int64_t n, int m, const float *A, const uint8_t *kind, const float 
             }
         }
     }
-    double sh = 0.0, su = 0.0;
-    for (int j = 0; j < m; ++j) r[j] = 0.0;
-    if (r_lin)
-        for (int j = 0; j < m; ++j) r_lin[j] = 0.0;
-    for (int64_t b = 0; b < nb; ++b) {
-        sh += part[b * W];
-        su += part[b * W + 1];
-        for (int j = 0; j < m; ++j) r[j] += part[b * W + 2 + j];
-        if (r_lin)
-            for (int j = 0; j < m; ++j) r_lin[j] += part[b * W + 2 + m + j];
-    }
-    double lr = 0.0;
-    for (int j = 0; j < m; ++j) lr += lam[j] * R[j];
-    *g = lr + sh;
-    if (U) *U = su;
-    free(part);
-    return 0;
 }
 
 /* Utility of the column-scaled allocation X~ at prices lam (Section 5: scale

@@ -113,6 +113,8 @@ void ra_solve_opts_default(ra_solve_opts *o)
     o->lam_floor = -1.0;
     o->master_lb = 1;
     o->repair_window = 16;
+    o->init_scale = 1;
+    o->pad_ = 0;
     o->init_step = 0.05;
 }
 

@@ -388,6 +388,122 @@ __global__ void __launch_bounds__(kTile, 2)
     }
 }
 
+// Scale of the starting prices along their ray (no per-job cap).  Scaling
+// every price by s scales every job's cheapest effective price c_i by s
+// (Section 4.1: the first cost segment leaves the origin towards the point of
+// highest a_j / lambda_j, whatever the common scale), so
+//     g(s lambda) = s lambda^T R + sum_i h_i(s c_i),
+//     g'(s)       = lambda^T R - sum_i c_i t_i(s),
+// and the minimiser along the ray is where the spending at the unscaled
+// effective prices, sum_i c_i t_i(s), equals lambda^T R.  One pass sums that
+// spending on the grid s_k = 2^(k - 8), k < kRayK, per job in closed form:
+// c t = w / s for log utilities, c t_1 s^(-1/(1-p)) for power utilities (t_1
+// the throughput at s = 1), c T while w > s c for linear utilities; the last
+// CTA interpolates the crossing in log-log and rescales lambda in place.
+constexpr int kRayK = 16;
+template <int MT>
+__global__ void __launch_bounds__(kTile, 2)
+    ray_scale_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
+                     const double *R, long long n, int m, double *lam, int stages,
+                     long long num_full, double *partials, unsigned *ticket, int *status,
+                     uint64_t wait_ns)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t bars[kMaxStages];
+    __shared__ __align__(16) float mu_s[RA_MAX_M];
+    __shared__ double lamd_s[RA_MAX_M], Rd_s[RA_MAX_M];
+    __shared__ double lr_s;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool grouped = (m == MT);
+    constexpr int C = MT / 4;
+    const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
+    if (tid < RA_MAX_M) {
+        lamd_s[tid] = tid < m ? lam[tid] : 0.0;
+        Rd_s[tid] = tid < m ? R[tid] : 0.0;
+        mu_s[tid] = inv_price<float>(tid < m ? static_cast<float>(lamd_s[tid]) : Fn<float>::inf());
+    }
+    __syncthreads();
+    KahanF S[kRayK];
+    auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
+                   float *warp_rows, const unsigned char *) {
+        (void)i;
+        (void)warp_rows;
+        if (!valid) return;
+        float vb = 0.f;   // max_j a_j / lambda_j = 1 / c
+        if (grouped) {
+#pragma unroll
+            for (int c4 = 0; c4 < C; ++c4) {
+                const int q = (c4 + rot) & (C - 1);
+                const float4 av = reinterpret_cast<const float4 *>(row)[q];
+                const float4 mv = reinterpret_cast<const float4 *>(mu_s)[q];
+                vb = fmaxf(vb, fmaxf(fmaxf(av.x * mv.x, av.y * mv.y), fmaxf(av.z * mv.z, av.w * mv.w)));
+            }
+        } else {
+            for (int k = 0; k < m; ++k) vb = fmaxf(vb, row[k] * mu_s[k]);
+        }
+        if (!(vb > 0.f)) return;
+        const float c = 1.0f / vb;
+        if (kd <= RA_U_POWER) {
+            // spending at s_0 = 2^-8 and the factor between successive scales
+            float base, ratio;
+            if (kd == RA_U_LOG) {
+                base = wi * 256.0f;
+                ratio = 0.5f;
+            } else {
+                const float e = 1.0f / (1.0f - pi);
+                base = fminf(__expf(__logf(c) + e * (__logf(wi * pi / c) + 8.0f * 0.69314718f)), 1e30f);
+                ratio = exp2f(-e);
+            }
+#pragma unroll
+            for (int k = 0; k < kRayK; ++k) {
+                S[k].add(base);
+                base *= ratio;
+            }
+        } else {
+            const float spend = c * pi;
+            float sk = 1.0f / 256.0f;
+#pragma unroll
+            for (int k = 0; k < kRayK; ++k) {
+                S[k].add(wi > sk * c ? spend : 0.0f);
+                sk *= 2.0f;
+            }
+        }
+    };
+    unsigned char *smem = align128<MT>(smem_dyn);
+    stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
+                    wait_ns, job, [&] {
+                        if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
+                    });
+    // lane k of every warp takes the warp's total of S_k
+    FF mine = red_zero<FF>();
+#pragma unroll
+    for (int k = 0; k < kRayK; ++k) {
+        const FF v = warp_sum(ff_of(S[k]));
+        if (lane == k) mine = v;
+    }
+    const FF z = red_zero<FF>();
+    FF(*red)[kPartW] = ring_red(smem);
+    if (grid_reduce(z, z, z, mine, z, kRayK, false, true, partials, ticket, red) && tid == 0) {
+        if (ld_status(status) & kStatusTimeout) return;   // incomplete sums: keep the prices
+        const double T = lr_s;
+        double x = kRayK - 1;   // log2(s) + 8 of the crossing
+        if (!(to_double(red[0][4]) > T)) {
+            x = 0.0;
+        } else {
+            for (int k = 1; k < kRayK; ++k) {
+                const double a = to_double(red[0][4 + k - 1]), b = to_double(red[0][4 + k]);
+                if (b <= T) {
+                    x = (b > 0.0 && isfinite(a)) ? (k - 1) + (log2(a) - log2(T)) / (log2(a) - log2(b))
+                                                 : static_cast<double>(k);
+                    break;
+                }
+            }
+        }
+        const double sc = exp2(x - 8.0);
+        for (int j = 0; j < m; ++j) lam[j] *= sc;
+    }
+}
+
 // Dual values g(lambda_a) and g(lambda_b) in one pass over the data (the
 // two start points a warm start chooses between): each job is solved at both
 // price vectors from the same staged row; only the two sums of h are
@@ -1170,6 +1286,15 @@ cudaError_t configure_dual(ra_problem *p)
     RA_IATTR(16)
     RA_IATTR(32)
 #undef RA_IATTR
+#define RA_RATTR(MT)                                                                               \
+    if ((e = cudaFuncSetAttribute(ray_scale_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  kRingSmemMax)) != cudaSuccess)                                     \
+        return e;
+    RA_RATTR(4)
+    RA_RATTR(8)
+    RA_RATTR(16)
+    RA_RATTR(32)
+#undef RA_RATTR
 #define RA_GATTR(MT)                                                                               \
     if ((e = cudaFuncSetAttribute(dual_g2_kernel<MT, true>,                                       \
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemMax)) !=     \
@@ -1296,6 +1421,26 @@ cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long 
     default: RA_INIT(32); break;
     }
 #undef RA_INIT
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s)
+{
+    const long long num_full = p->n / kTile;
+    int grid = p->grid_dual;
+    if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
+#define RA_RAY(MT)                                                                                 \
+    ray_scale_kernel<MT><<<grid, kTile, p->smem_dual, s>>>(p->A, p->kind, p->w, p->param, p->R,     \
+                                                           p->n, p->m, lam, p->stages, num_full,   \
+                                                           p->partials, p->ticket + 6, p->status,  \
+                                                           wait_limit_ns())
+    switch (p->mt) {
+    case 4: RA_RAY(4); break;
+    case 8: RA_RAY(8); break;
+    case 16: RA_RAY(16); break;
+    default: RA_RAY(32); break;
+    }
+#undef RA_RAY
     return cudaGetLastError();
 }
 

@@ -258,6 +258,7 @@ cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t 
 cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
                                const EvalOut *src, double *U_lb, cudaStream_t s);
 cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all = 0);
+cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s);
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
                            double *g_out, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);

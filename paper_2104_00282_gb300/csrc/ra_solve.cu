@@ -670,6 +670,19 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
         }
     }
     __syncwarp();
+    // Without the per-job cap a price at the floor makes the dual unbounded
+    // (demand of log / power jobs has no limit), and a trial there is a
+    // wasted evaluation: the first trial of a line search lowers no price by
+    // more than half.
+    if (st->lam_floor > 0.0 && st->ls_iter == 0 && !st->sg_pending) {
+        const double dj = active ? st->d[j] : 0.0;
+        const double lim = (active && dj < 0.0) ? 0.5 * st->lam_cur[j] / -dj : __longlong_as_double(0x7ff0000000000000ll);
+        double smax = lim;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) smax = fmin(smax, __shfl_xor_sync(kFull, smax, off));
+        if (j == 0 && smax < st->step) st->step = smax;
+        __syncwarp();
+    }
     set_trial(st, j, active, st->lam_cur[j] + st->step * st->d[j]);
 }
 
@@ -1057,6 +1070,8 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if (!lambda0) {
         if ((e = launch_init(p, st->lam_trial, s)) != cudaSuccess)
             return fail(RA_ECUDA, "init launch: %s", cudaGetErrorString(e));
+        if (!cap && opts.init_scale && (e = launch_ray_scale(p, st->lam_trial, s)) != cudaSuccess)
+            return fail(RA_ECUDA, "ray-scale launch: %s", cudaGetErrorString(e));
     }
     solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, p->m,
                                          stop_tolerance(opts.tol_rel, p->flags), opts.max_evals,

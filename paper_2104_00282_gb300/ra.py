@@ -34,7 +34,8 @@ class ra_solve_opts(ctypes.Structure):
                 ("lbfgs_mem", ctypes.c_int32), ("update", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("lam_floor", ctypes.c_double),
                 ("master_lb", ctypes.c_int32), ("repair_window", ctypes.c_int32),
-                ("init_step", ctypes.c_double)]
+                ("init_step", ctypes.c_double), ("init_scale", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class ra_repair_opts(ctypes.Structure):
@@ -93,6 +94,14 @@ def lib():
         L.ra_solve_history.restype = i32
         L.ra_recover_primal.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
         L.ra_recover_primal.restype = i32
+        L.ra_eval_partial.argtypes = [P, P, P]
+        L.ra_eval_partial.restype = i32
+        L.ra_combine_partials.argtypes = [i32, i32, P, P, P, P, P, P]
+        L.ra_combine_partials.restype = i32
+        L.ra_solve_sharded.argtypes = [P, i64, i32, i32, P, P, ALLGATHER_FN, P,
+                                       ctypes.POINTER(ra_solve_opts), P, P,
+                                       ctypes.POINTER(ra_solve_info)]
+        L.ra_solve_sharded.restype = i32
         L.ra_repair_opts_default.argtypes = [ctypes.POINTER(ra_repair_opts)]
         L.ra_repair_opts_default.restype = None
         L.ra_recover_feasible.argtypes = [P, P, ctypes.POINTER(ra_repair_opts), P, P, P,
@@ -243,6 +252,36 @@ def ra_recover_primal(h, lam, jstar=None, j12=None, x12=None, t=None, X=None, U=
                                    _ptr(U, torch.float64), _ptr(near_tie, torch.uint8),
                                    ctypes.byref(cnt) if count_ties else None))
     return int(cnt.value)
+
+
+def RA_SHARD_WIDTH(m):
+    return 4 + 2 * m
+
+
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p)
+
+
+def ra_eval_partial(h, lam, part):
+    _check(lib().ra_eval_partial(h, _ptr(lam, torch.float64), _ptr(part, torch.float64)))
+
+
+def ra_combine_partials(parts, m, lam, R, g=None, q=None, stream=None):
+    S = parts.numel() // RA_SHARD_WIDTH(m)
+    _check(lib().ra_combine_partials(S, m, _ptr(parts, torch.float64), _ptr(lam, torch.float64),
+                                     _ptr(R, torch.float64), _ptr(g, torch.float64),
+                                     _ptr(q, torch.float64), _stream(stream)))
+
+
+def ra_solve_sharded(h, n_total, rank, world, send, recv, fn, lam_out, opts=None, lam0=None,
+                     allow_notconv=True):
+    o = opts or ra_solve_opts_default()
+    info = ra_solve_info()
+    ok = (RA_OK, RA_ENOTCONV) if allow_notconv else (RA_OK,)
+    _check(lib().ra_solve_sharded(h, n_total, rank, world, _ptr(send, torch.float64),
+                                  _ptr(recv, torch.float64), fn, None, ctypes.byref(o),
+                                  _ptr(lam0, torch.float64), _ptr(lam_out, torch.float64),
+                                  ctypes.byref(info)), ok)
+    return info.as_dict()
 
 
 def ra_recover_feasible(h, lam, jk=None, xk=None, X=None, tie_rel=None, max_flex=None):
@@ -428,8 +467,10 @@ class AllocationProblem:
         return lam
 
     def solve(self, tol=1e-6, max_evals=500, lam0=None, update="lbfgs", use_graph=True,
-              lbfgs_mem=10, master_lb=True, init_step=None, repair_window=None):
+              lbfgs_mem=10, master_lb=True, init_step=None, repair_window=None, init_scale=None):
         o = ra_solve_opts_default()
+        if init_scale is not None:
+            o.init_scale = 1 if init_scale else 0
         o.master_lb = 1 if master_lb else 0
         if repair_window is not None:
             o.repair_window = repair_window

@@ -149,8 +149,8 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
         A, kind, w, param, R = W.hetero_device(int(sizes[i]), M, seed, i, device)
         prob = ra.AllocationProblem(A, kind, w, param, R, job_cap=job_cap)
 
-        def cold():
-            return prob.solve(tol=tol, max_evals=max_evals)
+        def cold():   # the paper's Eq. e-initialization, unscaled
+            return prob.solve(tol=tol, max_evals=max_evals, init_scale=False)
 
         def warm():
             lam0, used = prob.warm_prices(net)
