@@ -332,6 +332,18 @@ def run_gpu(args):
         e1.synchronize()
         if k > 0:
             o_times.append(e0.elapsed_time(e1))
+    # the other mode's standalone evaluation (CUDA events, as the headline's)
+    lam_o = Po.init_prices()
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            ra.ra_eval_dual(Po.handle, lam_o)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ra.ra_eval_dual(Po.handle, lam_o)
+        e1.record(stream)
+    e1.synchronize()
+    o_eval_ms = e0.elapsed_time(e1) / reps
     Po.close()
     other = {"ms": statistics.median(o_times), "evals": o_info["evals"],
              "rel_gap": o_info["rel_gap"], "status": o_info["status"]}
@@ -364,6 +376,7 @@ def run_gpu(args):
                         "and price update FP64 in both; each result re-checked by the FP64 oracle"}
 
     batch = run_batch(args, dev, stream) if args.batch > 0 else None
+    medium = run_paper_medium(args, dev, stream) if args.paper_medium > 0 else None
     warm = run_warm(args) if args.warm > 0 else None
 
     if rank != 0:
@@ -375,8 +388,24 @@ def run_gpu(args):
         cpu = {"value": r["scaled"], "unit": "ms", "cores": r["threads"], "kind": "oracle",
                "converged": r["converged"], "gap": r["gap"], "sample": _sample_text(r)}
     evals = [i["evals"] for i in infos]
-    # per solve: initialisation + setup, then per evaluation: dual pass, solver step
-    launches = sum(2 + 2 * e for e in evals)
+    # per solve: initialisation (+ the ray scaling without the cap) and setup,
+    # then per evaluation: dual pass, solver step; per repair of the lower
+    # bound: scan, collect, gather, apply, FP64 evaluation, accept
+    launches = sum((2 if cap else 3) + 2 * i["evals"] + 6 * i["repairs"] for i in infos)
+    # the in-solve evaluation kernel: device time between price updates (the
+    # solver's own global-timer accounting), against the bytes of A, w,
+    # param and kind alone (the lower-bound records, 10 B/job written and 10
+    # read once the records are on, are left out: a lower bound on the rate)
+    ev_ms = statistics.median(i["eval_ms"] / max(i["evals"], 1) for i in infos)
+    st_ms = statistics.median(i["step_ms"] / max(i["evals"], 1) for i in infos)
+    in_solve = {"achieved": alg_bytes / (ev_ms * 1e-3) / 1e9, "frac": alg_bytes / (ev_ms * 1e-3) / 1e9 / peak,
+                "launch_ms": ev_ms, "step_ms": st_ms,
+                "kernel": f"dual_tma_kernel in the solve ({'with' if cap else 'no'} cap; lagged bound, records)",
+                "timing": "device global timer between solver steps (graph launch gaps included)"}
+    other_mode = {"achieved": alg_bytes / (o_eval_ms * 1e-3) / 1e9,
+                  "frac": alg_bytes / (o_eval_ms * 1e-3) / 1e9 / peak, "launch_ms": o_eval_ms,
+                  "kernel": f"dual_tma_kernel, {'no' if cap else 'with'} per-job cap (ra_eval_dual)",
+                  "timing": "CUDA events, 20 launches"}
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -396,7 +425,9 @@ def run_gpu(args):
                      "kernel": f"dual_tma_kernel, {'with' if cap else 'no'} per-job cap "
                                "(ra_eval_dual, no lower-bound record)",
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": eval_ms,
-                     "peak_source": f"{peak_src} hbm_gbs (burst copy)"},
+                     "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+                     "in_solve": in_solve,
+                     ("capped" if not cap else "uncapped"): other_mode},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -404,6 +435,7 @@ def run_gpu(args):
         ("no_job_cap" if cap else "with_job_cap"): other,
         "batched": batch,
         "warm_start": warm,
+        "paper_medium": medium,
     }
     print(json.dumps(line), flush=True)
 
@@ -538,6 +570,121 @@ def run_sharded(args):
     print(json.dumps(line), flush=True)
 
 
+def run_paper_medium(args, dev, stream):
+    """The paper's medium problem (Section 6.2: n = 1e6, m = 4, the per-job
+    cap, log utility and target-priority utility with t_des = 0.2, w in
+    {1, 2}) solved to 1e-6, with the statistics of the allocation the
+    library returns (ra_recover_feasible at the final prices) beside the
+    paper's: jobs on two resources, jobs with slack, jobs reaching the
+    target.  The paper's own times (GTX 1070, FP32 PyTorch, absolute gap
+    1e-3 n) are context only."""
+    import numpy as np
+    import torch
+    from paper_2104_00282_gb300 import ra
+    from paper_2104_00282_gb300 import workloads as W
+    out = {}
+    paper = {"log": {"gpu_s": 0.30, "two_resources": 0.17, "positive_slack": 0.18},
+             "target": {"gpu_s": 0.89, "two_resources": 0.67, "positive_slack": 0.50,
+                        "reach_target": ">0.95", "low_priority_miss": 0.10}}
+    for util in ("log", "target"):
+        prob = W.paper_medium(n=args.paper_medium, utility=util, seed=0)
+        with torch.cuda.stream(stream):
+            P = ra.AllocationProblem.from_numpy(prob, dev, stream=stream, job_cap=True)
+        times, info = [], None
+        for k in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            info = P.solve(tol=TOL, max_evals=args.max_evals)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                times.append(e0.elapsed_time(e1))
+        rec = P.recover_feasible()
+        jk = rec["jk"].cpu().numpy().reshape(-1, 4)
+        xk = rec["xk"].cpu().numpy().reshape(-1, 4).astype(np.float64)
+        P.close()
+        used = (jk >= 0) & (xk > 1e-9)
+        a = np.where(jk >= 0, prob.A[np.arange(prob.n)[:, None], np.maximum(jk, 0)], 0.0)
+        t = (a * np.where(jk >= 0, xk, 0.0)).sum(1)
+        st = {"ms": statistics.median(times), "evals": info["evals"], "rel_gap": info["rel_gap"],
+              "status": info["status"], "repairs": info["repairs"],
+              "two_resources": float(np.mean(used.sum(1) == 2)),
+              "positive_slack": float(np.mean(1.0 - np.where(jk >= 0, xk, 0.0).sum(1) > 1e-6)),
+              "max_usage_over_R": rec["info"]["max_usage_over_R"]}
+        if util == "target":
+            reach = t >= 0.2 - 1e-6
+            st["reach_target"] = float(reach.mean())
+            st["low_priority_miss"] = float((~reach[prob.w == 1]).mean())
+            st["high_priority_miss"] = float((~reach[prob.w == 2]).mean())
+        out[util] = {"gb300": st, "paper": paper[util]}
+    out["note"] = ("n = %d, m = 4, per-job cap; target-priority optima are not unique (a linear "
+                   "program): the two-resource fraction depends on which optimum a solver returns" % args.paper_medium)
+    return out
+
+
+def run_sweep(args):
+    """The scaling experiments of Section 6.4 (Fig. 10) and the large problem of
+    Section 6.3, on this GPU.  Dual evaluation time (CUDA events, the mean of
+    20 back-to-back ra_eval_dual launches at the Eq. e-initialization prices,
+    the per-job cap of the paper's experiments) against m at n = 1e5 and
+    against n at m = 4, reported as algorithmic GB/s (n (4m + 9) bytes per
+    evaluation) and as a fraction of the measured copy bandwidth; and the
+    n = 5e7, m = 4 log-utility problem solved to 1e-6.  Workloads: the
+    Section 6.1 code example generator (A ~ U[0, 1], R = U[0, 1] n + 1e3,
+    log utility).  Prints one JSON object."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_2104_00282_gb300 import ra
+    from paper_2104_00282_gb300 import workloads as W
+    peak = _peaks().get("hbm_gbs") or 6800.0
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+
+    def eval_point(n, m):
+        prob = W.paper_code_example(n=n, m=m, seed=0)
+        P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=True)
+        lam = P.init_prices()
+        for _ in range(3):
+            ra.ra_eval_dual(P.handle, lam)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            ra.ra_eval_dual(P.handle, lam)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        P.close()
+        b = n * (4 * m + 9)
+        return {"n": n, "m": m, "ms": ms, "GB_s": b / (ms * 1e-3) / 1e9,
+                "hbm_frac": b / (ms * 1e-3) / 1e9 / peak, "bytes": b,
+                "l2_resident": b < l2}
+
+    out = {"peak_gbs": peak, "peak_source": "measured hbm_gbs", "l2_bytes": l2,
+           "vs_m": [eval_point(100_000, m) for m in (2, 4, 8, 16, 32)],
+           "vs_n": [eval_point(n, 4) for n in (100, 1_000, 10_000, 100_000, 1_000_000,
+                                               10_000_000, 100_000_000)]}
+    # Section 6.3: n = 5e7, m = 4, log utility, solved with the per-job cap
+    prob = W.paper_code_example(n=50_000_000, m=4, seed=1)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=True)
+    ts, info = [], None
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        info = P.solve(tol=TOL, max_evals=args.max_evals)
+        e1.record()
+        e1.synchronize()
+        if k > 0:
+            ts.append(e0.elapsed_time(e1))
+    P.close()
+    out["large_5e7_m4"] = {"ms": statistics.median(ts), "evals": info["evals"],
+                           "rel_gap": info["rel_gap"], "status": info["status"],
+                           "paper": "228 s CPU (i7-6700K), about 7.9 s GPU (V100), FP32, absolute gap 1e-3 n"}
+    print(json.dumps(out), flush=True)
+
+
 def run_warm(args):
     """Learned warm start (the committed network, trained by
     paper_2104_00282_gb300.warmstart on 20000 solved problems): cold and warm
@@ -562,33 +709,49 @@ def run_warm(args):
 def run_batch(args, dev, stream):
     """Batched price discovery: P independent problems (n log-uniform in
     [100, 2e5], m in {4, 8, 16, 32}) solved together to the same tolerance,
-    cold start.  Reports problems/s over the whole batch and the percentiles
-    of the per-problem device time to tolerance."""
+    cold start.  The launch shape of the batched evaluation is chosen by the
+    package's autotuner on this workload (cached per GPU and workload).
+    Reports problems/s over the whole batch, the percentiles of the
+    per-problem device time to tolerance, and the bytes the batched passes
+    streamed (sum over problems of evaluations x n (4m + 29): the A rows,
+    w, param, kind and the 20-byte lower-bound records) per second."""
     import numpy as np
     import torch
+    from paper_2104_00282_gb300 import autotune
     from paper_2104_00282_gb300 import ra
     from paper_2104_00282_gb300 import workloads as W
 
     P = args.batch
     n, m = W.batched_shapes(P)
     probs = W.batched_workload(P)
-    with torch.cuda.stream(stream):
-        B = ra.AllocationBatch(probs, job_cap=True, device=dev, stream=stream)
+    tensors = [tuple(torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+                     for x in (p.A, p.kind, p.w, p.param, p.R)) for p in probs]
     del probs
-    times, secs, infos = [], None, None
-    for k in range(4):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        infos, secs = B.solve(tol=TOL, max_evals=BATCH_MAX_EVALS)
-        e1.record(stream)
-        e1.synchronize()
-        if k > 0:
-            times.append(e0.elapsed_time(e1))
-    B.close()
-    ms = statistics.median(times)
+    torch.cuda.synchronize()
+    shape, tuned = autotune.tune(tensors, job_cap=True, tol=TOL, max_evals=BATCH_MAX_EVALS)
+
+    def timed(shape):
+        with torch.cuda.stream(stream):
+            B = ra.AllocationBatch.from_tensors(tensors, job_cap=True, stream=stream, shape=shape)
+        times, secs, infos = [], None, None
+        for k in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            infos, secs = B.solve(tol=TOL, max_evals=BATCH_MAX_EVALS)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                times.append(e0.elapsed_time(e1))
+        B.close()
+        return statistics.median(times), times, infos, np.asarray(secs)
+
+    ms, times, infos, secs = timed(shape)
+    ms_default, _, _, secs_default = timed(None)
     evals = np.array([i["evals"] for i in infos])
     status = np.array([i["status"] for i in infos])
+    bytes_streamed = float(np.sum(evals * n * (4 * m + 29)))
+    peak = _peaks().get("hbm_gbs") or 6800.0
     return {"problems": P, "jobs": int(n.sum()), "A_bytes": int((n * m).sum() * 4),
             "ms": ms, "problems_per_s": P / (ms * 1e-3),
             "jobs_per_s": float(n.sum()) / (ms * 1e-3),
@@ -598,55 +761,17 @@ def run_batch(args, dev, stream):
             "evals": {"p50": float(np.median(evals)), "p99": float(np.percentile(evals, 99)),
                       "max": int(evals.max())},
             "converged": int((status == 0).sum()), "step_ms_all": times,
+            "streamed_GB_s": bytes_streamed / (ms * 1e-3) / 1e9,
+            "streamed_hbm_frac": bytes_streamed / (ms * 1e-3) / 1e9 / peak,
+            "shape": {"chunk_tiles": shape[0], "whole_tiles": shape[1], "ctas_per_sm": shape[2],
+                      "chosen_by": "autotune over " + str(len(tuned.get("trials", []))) +
+                                   " shapes (0 = cached)"},
+            "default_shape": {"shape": [16, 0, 0], "ms": ms_default,
+                              "p50": float(np.percentile(secs_default, 50) * 1e3),
+                              "p99": float(np.percentile(secs_default, 99) * 1e3)},
             "workload": "n log-uniform in [100, 2e5], m uniform in {4, 8, 16, 32}, "
                         "heterogeneous-hardware recipe, per-job cap 1^T x_i <= 1 (problem "
                         "e-res-alloc), cold start to 1e-6 relative gap, at most 500 evaluations"}
-
-
-def run_profile(args):
-    """Small, self-contained workloads for a profiler (ncu), one per kind of
-    launch: ``eval`` runs --reps standalone dual evaluations (ra_eval_dual) at
-    the Eq. e-initialization prices of the large recipe (n = --n, m = --m);
-    ``solve`` one solve with the host-driven loop, so that every launch is a
-    separate kernel the profiler can see (inside a CUDA graph's conditional
-    node it cannot); ``batch`` one batched solve of the batched workload's
-    first --problems problems with the host loop; ``warm`` one warm-started
-    solve (statistics, network, start prices, solve) of a held-out problem of
-    the warm-start recipe (n = --n, m = 16)."""
-    import torch
-    import __graft_entry__ as G
-    G.build()
-    from paper_2104_00282_gb300 import ra
-    from paper_2104_00282_gb300 import workloads as W
-    what = args.profile
-    if what in ("eval", "solve"):
-        prob = W.config_large(n=args.n, m=args.m, seed=0)
-        P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=args.job_cap)
-        if what == "eval":
-            lam = P.init_prices()
-            for _ in range(args.reps):
-                ra.ra_eval_dual(P.handle, lam)
-            out = f"{args.reps} evaluations"
-        else:
-            out = P.solve(tol=TOL, max_evals=args.max_evals, use_graph=False)
-        P.close()
-    elif what == "batch":
-        probs = W.batched_workload(args.problems)
-        B = ra.AllocationBatch(probs, job_cap=True)
-        infos, _ = B.solve(tol=TOL, max_evals=BATCH_MAX_EVALS, use_graph=False)
-        out = f"{sum(i['status'] == 0 for i in infos)} of {len(infos)} converged"
-        B.close()
-    else:
-        from paper_2104_00282_gb300 import warmstart as WS
-        net = WS.load()
-        A, kind, w, param, R = W.hetero_device(args.n, 16, WS.EVAL_SEED, 5, "cuda")
-        P = ra.AllocationProblem(A, kind, w, param, R, job_cap=False)
-        lam0, used = P.warm_prices(net)
-        out = P.solve(tol=TOL, max_evals=BATCH_MAX_EVALS, lam0=lam0, use_graph=False)
-        P.close()
-        net.close()
-    torch.cuda.synchronize()
-    print("profile", what, out, flush=True)
 
 
 def main():
@@ -668,8 +793,10 @@ def main():
                     help="headline with the paper's per-job cap 1^T x_i <= 1 (default: X >= 0 only)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven solver loop (same kernels; lets ncu see every launch)")
-    ap.add_argument("--warm", type=int, default=200,
+    ap.add_argument("--warm", type=int, default=1000,
                     help="held-out problems in the warm-start comparison (0 = skip)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the Section 6.3-6.4 scaling experiments instead of the benchmark")
     ap.add_argument("--shard", action="store_true",
                     help="use the job-range sharded solve even on one rank (it is the default "
                          "with more than one rank)")
@@ -677,10 +804,14 @@ def main():
                     help="skip the FP64 oracle re-check of the headline solve")
     ap.add_argument("--fp64-study", type=int, default=1,
                     help="1 = also solve the workload with FP64 per-job arithmetic (precision study)")
+    ap.add_argument("--paper-medium", type=int, default=1_000_000,
+                    help="jobs of the paper's medium problem solved beside the headline (0 = skip)")
     ap.add_argument("--batch", type=int, default=4096,
                     help="problems in the batched solve reported beside the headline (0 = skip)")
     args = ap.parse_args()
-    if args.profile:
+    if args.sweep:
+        run_sweep(args)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -24,7 +24,8 @@
  *    unspecified; ra_last_error() returns a thread-local message.
  *  - Utility kinds (per job, uint8):
  *      RA_U_LOG     u(t) = w log t                 (Eq. e-log-util, weighted)
- *      RA_U_POWER   u(t) = w t^p, 0 < p < 1        (Section 2.2, power utility)
+ *      RA_U_POWER   u(t) = w t^p, 0 < p < 1, or    (Section 2.2, power utility;
+ *                   u(t) = -w t^p, -64 <= p < 0     alpha-fair with alpha = 1 - p)
  *      RA_U_LINCAP  u(t) = w min(t, T)             (target-priority + w T)
  *      RA_U_TARGET  u(t) = w min(t - T, 0)         (Eq. e-target-priority-util)
  *    param[i] holds p (power) or T (lincap, target) and is ignored for log.
@@ -70,7 +71,7 @@ typedef struct ra_problem ra_problem; /* opaque; owns its device workspace */
  *   A      n*m FP32 efficiencies, A_ij >= 0                       (borrowed)
  *   kind   n uint8 utility kinds                                   (borrowed)
  *   w      n FP32 weights, w > 0                                   (borrowed)
- *   param  n FP32 utility parameters (p in (0,1) or T > 0)         (borrowed)
+ *   param  n FP32 utility parameters (p in (0,1) or [-64,0), or T > 0) (borrowed)
  *   R      m FP64 resource limits, R_j >= 0                        (borrowed)
  *   flags  RA_JOB_CAP or RA_NO_JOB_CAP, | RA_FP64_JOBMATH, | RA_VALIDATE
  *   stream cudaStream_t used by every call on this problem (NULL = legacy)
@@ -161,6 +162,10 @@ typedef struct {
     double gap_per_job;   /* (g - U_lb) / n, the paper's absolute measure (Algorithm 2)         */
     int32_t repairs;      /* repairs of the lower bound run (see repair_window)                 */
     int32_t n_flex;       /* jobs the last repair re-mixed                                      */
+    double eval_ms;       /* device time (global timer) in dual evaluations, from the end of one
+                             price update to the start of the next (launch gaps included)      */
+    double step_ms;       /* device time in the solver steps (master LP and price update);
+                             neither counts the host-side repairs                               */
 } ra_solve_info;
 
 /* Fill *opts with the defaults (tol 1e-6, 500 evals, memory 10, L-BFGS, graph,
@@ -237,9 +242,10 @@ ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jst
  * the jobs whose optimum is within tie_rel of a tie -- two effective prices
  * lambda_j / A_ij, two hull segments, or (linear utilities) w and a segment
  * slope -- are re-mixed: each job's optimal extreme allocations are listed and
- * a small LP (FP64, on the host) picks convex weights that first minimise the
- * total relative overuse sum_j max(r_j - R_j, 0) / R_j and then maximise the
- * weighted utility.  Overuse the LP cannot remove is taken out by the column
+ * a small LP (FP64, on the host) picks convex weights that maximise the
+ * weighted utility minus the overuse max(r_j - R_j, 0) priced at lambda_j
+ * (about the utility that scaling it away would cost).  Overuse the LP leaves
+ * is taken out by the column
  * scaling of Section 5 (without the per-job cap, under-used columns are also
  * scaled up).  The paper is silent on this step; at optimal prices the
  * re-mixed allocation closes the duality gap that column scaling alone
@@ -389,6 +395,26 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
                           const float *const *param, const double *const *R, uint32_t flags,
                           void *stream, ra_batch **out);
 
+/*
+ * ra_batch_create_shaped -- ra_batch_create with the launch shape of the
+ * batched evaluation given (chosen by the package's autotuner): a problem of
+ * at most whole_tiles 256-job tiles is one chunk (one CTA visits all of it
+ * in an evaluation, so small problems never wait for other CTAs), a larger
+ * one is cut into chunks of chunk_tiles tiles; the persistent grid of each
+ * width class runs ctas_per_sm CTAs per SM (0: as many as fit).  shape NULL
+ * gives the defaults {16, 0, 0}.
+ */
+typedef struct {
+    int32_t chunk_tiles;  /* 1..4096, default 16 */
+    int32_t whole_tiles;  /* >= 0, default 0 */
+    int32_t ctas_per_sm;  /* 0..8, default 0 */
+    int32_t pad_;
+} ra_batch_shape;
+ra_status ra_batch_create_shaped(int32_t P, const int64_t *n, const int32_t *m, const float *const *A,
+                                 const uint8_t *const *kind, const float *const *w,
+                                 const float *const *param, const double *const *R, uint32_t flags,
+                                 const ra_batch_shape *shape, void *stream, ra_batch **out);
+
 /* Waits for the batch's stream, then frees its workspace. */
 void ra_batch_destroy(ra_batch *b);
 
@@ -413,6 +439,25 @@ int64_t ra_batch_prices(const ra_batch *b);
  */
 ra_status ra_batch_solve(ra_batch *b, const ra_solve_opts *opts, const double *lambda0,
                          double *lambda_out, ra_solve_info *infos, double *seconds);
+
+/*
+ * ra_batch_rebalance -- price coordination of M shards of one problem
+ * (Section 7: shards solved independently with budgets R_k, resources then
+ * moved from shards with lower prices to shards with higher prices; it
+ * converges to the solution of the whole problem).  The batch's problems
+ * are the shards (every one with the same m); their R arrays are the budgets
+ * and are overwritten in place:
+ *     R_kj <- Pi( R_kj + step (lambda_kj - pbar_j) / pbar_j * R_total_j / M ),
+ * pbar_j the mean price of resource j over the shards and Pi the Euclidean
+ * projection onto {R_kj >= f_j, sum_k R_kj = R_total_j} with the floor
+ * f_j = 1e-3 R_total_j / M: a shard with none of a resource would price it
+ * at infinity without the per-job cap (and its jobs that only use it would
+ * get no throughput).
+ *   lambda   device, the shards' prices concatenated (as ra_batch_solve returns)
+ *   R_total  device, m FP64: the whole problem's limits
+ * Enqueued on the batch's stream; allocates nothing.
+ */
+ra_status ra_batch_rebalance(ra_batch *b, const double *lambda, const double *R_total, double step);
 
 /*
  * Learned warm start (not in the paper; the cold start it competes with is

@@ -485,7 +485,7 @@ def utility_of(prob, t):
         m0 = k == 0
         u[m0] = w[m0] * np.log(t[m0])
         m1 = k == 1
-        u[m1] = w[m1] * np.power(t[m1], par[m1])
+        u[m1] = np.sign(par[m1]) * w[m1] * np.power(t[m1], par[m1])
         m2 = k == 2
         u[m2] = w[m2] * np.minimum(t[m2], par[m2])
         m3 = k == 3
@@ -500,7 +500,7 @@ def _u_vec(kind, w, par, t):
         if kind == 0:
             return w * np.log(t)
         if kind == 1:
-            return w * np.power(t, par)
+            return np.sign(par) * w * np.power(t, par)
         if kind == 2:
             return w * np.minimum(t, par)
         return w * np.minimum(t - par, 0.0)
@@ -529,7 +529,7 @@ def job_alternatives(a, lam, kind, w, par, cap=True, rel=1e-9):
                 if alpha <= 0:
                     ts = [hi]
                 else:
-                    t = w / alpha if kind == 0 else (w * par / alpha) ** (1.0 / (1.0 - par))
+                    t = w / alpha if kind == 0 else (w * abs(par) / alpha) ** (1.0 / (1.0 - par))
                     ts = [min(max(t, aP), hi)]
             else:
                 if w < alpha * (1 - rel):

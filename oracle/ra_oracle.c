@@ -14,7 +14,8 @@
  *
  * Utility kinds (Section 2.2):
  *   0 log     u(t) = w log t                  (Eq. e-log-util, with a weight)
- *   1 power   u(t) = w t^par, 0 < par < 1     ("Power utilities")
+ *   1 power   u(t) = w t^par, 0 < par < 1, or -w t^par, par < 0
+ *             ("Power utilities"; alpha-fair with alpha = 1 - par)
  *   2 lincap  u(t) = w min(t, par)            (Eq. e-target-priority-util + w par)
  *   3 target  u(t) = w min(t - par, 0)        (Eq. e-target-priority-util)
  *
@@ -67,7 +68,7 @@ static double util(int kind, double w, double par, double t)
 {
     switch (kind) {
     case K_LOG:    return w * log(t);
-    case K_POWER:  return w * pow(t, par);
+    case K_POWER:  return par > 0.0 ? w * pow(t, par) : -w * pow(t, par);
     case K_LINCAP: return w * fmin(t, par);
     default:       return w * fmin(t - par, 0.0);
     }
@@ -79,15 +80,16 @@ static double util_deriv(int kind, double w, double par, double t)
 {
     switch (kind) {
     case K_LOG:   return w / t;
-    case K_POWER: return w * par * pow(t, par - 1.0);
+    case K_POWER: return w * fabs(par) * pow(t, par - 1.0);
     default:      return t < par ? w : 0.0;
     }
 }
 
 /* Smallest maximiser of u(t) - alpha t over [lo, hi] (hi may be +inf).
  * Strictly concave kinds: t = Pi_[lo,hi] (u')^{-1}(alpha)   (Eq. e-opt-t-log),
- *   (u')^{-1}(alpha) = w/alpha for log, (w par/alpha)^{1/(1-par)} for power;
- *   alpha <= 0 makes the objective increasing, so t = hi.
+ *   (u')^{-1}(alpha) = w/alpha for log, (w |par|/alpha)^{1/(1-par)} for power;
+ *   alpha <= 0 makes the objective increasing, so t = hi.  For power utilities
+ *   u'(t) = w |par| t^(par - 1), so (u')^{-1}(alpha) = (w |par| / alpha)^{1/(1-par)}.
  * Kinds 2/3: slope w - alpha below par and -alpha above it (Eq. e-opt-t-target):
  *   w <= alpha -> lo; otherwise par clamped to [lo, hi] (hi when alpha < 0). */
 static double argmax_interval(int kind, double w, double par, double alpha, double lo, double hi)
@@ -95,7 +97,7 @@ static double argmax_interval(int kind, double w, double par, double alpha, doub
     double t;
     if (kind == K_LOG || kind == K_POWER) {
         if (!(alpha > 0.0)) return hi;
-        t = (kind == K_LOG) ? w / alpha : pow(w * par / alpha, 1.0 / (1.0 - par));
+        t = (kind == K_LOG) ? w / alpha : pow(w * fabs(par) / alpha, 1.0 / (1.0 - par));
     } else {
         if (w <= alpha) return lo;
         if (alpha < 0.0) return hi;

@@ -53,8 +53,9 @@ static ra_status validate(const ra_problem *p)
     for (int64_t i = 0; i < n; ++i) {
         if (kind[i] > RA_U_TARGET) return fail(RA_EINVAL, "kind[%lld] = %d is not a utility kind", (long long)i, kind[i]);
         if (!(std::isfinite(w[i]) && w[i] > 0.f)) return fail(RA_EINVAL, "w[%lld] = %g must be finite and > 0", (long long)i, w[i]);
-        if (kind[i] == RA_U_POWER && !(par[i] > 0.f && par[i] < 1.f))
-            return fail(RA_EINVAL, "param[%lld] = %g: power exponent must lie in (0, 1)", (long long)i, par[i]);
+        if (kind[i] == RA_U_POWER && !((par[i] > 0.f && par[i] < 1.f) || (par[i] < 0.f && par[i] >= -64.f)))
+            return fail(RA_EINVAL, "param[%lld] = %g: power exponent must lie in (0, 1) or [-64, 0)",
+                        (long long)i, par[i]);
         if (kind[i] >= RA_U_LINCAP && !(std::isfinite(par[i]) && par[i] > 0.f))
             return fail(RA_EINVAL, "param[%lld] = %g: target throughput must be finite and > 0", (long long)i, par[i]);
         bool any = false;
@@ -369,6 +370,12 @@ ra_status ra_solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t
     return s;
 }
 
+ra_status ra_batch_rebalance(ra_batch *b, const double *lambda, const double *R_total, double step)
+{
+    if (!b || !lambda || !R_total) return fail(RA_EINVAL, "NULL argument");
+    return ra::batch_rebalance(b, lambda, R_total, step);
+}
+
 void ra_repair_opts_default(ra_repair_opts *o)
 {
     if (!o) return;
@@ -432,6 +439,20 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
                           const float *const *param, const double *const *R, uint32_t flags,
                           void *stream, ra_batch **out)
 {
+    return ra_batch_create_shaped(P, n, m, A, kind, w, param, R, flags, nullptr, stream, out);
+}
+
+ra_status ra_batch_create_shaped(int32_t P, const int64_t *n, const int32_t *m, const float *const *A,
+                                 const uint8_t *const *kind, const float *const *w,
+                                 const float *const *param, const double *const *R, uint32_t flags,
+                                 const ra_batch_shape *shape, void *stream, ra_batch **out)
+{
+    ra_batch_shape sh{ra::kChunkTiles, 0, 0, 0};
+    if (shape) sh = *shape;
+    if (sh.chunk_tiles < 1 || sh.chunk_tiles > 4096)
+        return fail(RA_EINVAL, "chunk_tiles = %d must lie in [1, 4096]", sh.chunk_tiles);
+    if (sh.whole_tiles < 0 || sh.ctas_per_sm < 0 || sh.ctas_per_sm > 8)
+        return fail(RA_EINVAL, "whole_tiles must be >= 0 and ctas_per_sm in [0, 8]");
     ra::g_err[0] = 0;
     if (!out) return fail(RA_EINVAL, "out is NULL");
     *out = nullptr;
@@ -491,11 +512,13 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
         q.cls = m[p] <= 4 ? 0 : m[p] <= 8 ? 1 : m[p] <= 16 ? 2 : 3;
         const int c = q.cls;
         const long long tiles = (n[p] + ra::kTile - 1) / ra::kTile;
+        // a problem of at most whole_tiles tiles is one chunk: one CTA visits all of it
+        const long long ck = tiles <= sh.whole_tiles ? tiles : sh.chunk_tiles;
         q.chunk_begin = static_cast<int>(cp[c].size());
-        for (long long t0 = 0; t0 < tiles; t0 += ra::kChunkTiles) {
+        for (long long t0 = 0; t0 < tiles; t0 += ck) {
             cp[c].push_back(p);
             ct0[c].push_back(static_cast<int32_t>(t0));
-            cnt[c].push_back(static_cast<int32_t>(tiles - t0 < ra::kChunkTiles ? tiles - t0 : ra::kChunkTiles));
+            cnt[c].push_back(static_cast<int32_t>(tiles - t0 < ck ? tiles - t0 : ck));
         }
         q.chunk_end = static_cast<int>(cp[c].size());
         q.lbt[0] = q.lbt[1] = nullptr;
@@ -554,6 +577,7 @@ ra_status ra_batch_create(int32_t P, const int64_t *n, const int32_t *m, const f
         e = ra::batch_configure(4 << c, !(flags & RA_NO_JOB_CAP), &per_sm);
         if (e != cudaSuccess) break;
         if (per_sm < 1) per_sm = 1;
+        if (sh.ctas_per_sm > 0 && sh.ctas_per_sm < per_sm) per_sm = sh.ctas_per_sm;
         const long long g = static_cast<long long>(b->num_sms) * per_sm;
         b->grid[c] = static_cast<int>(g < b->nchunks[c] ? g : b->nchunks[c]);
         const long long gi = static_cast<long long>(b->num_sms) * 4;

@@ -248,6 +248,8 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         lbj_out = P.lbj_buf[q ^ 1];
     }
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
+    // records (and the linear jobs' usage that scales them) of this evaluation
+    const bool rec_w = REC && (P.rec_on == nullptr || *P.rec_on != 0);
     constexpr int C = MT / 4;
     const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
 
@@ -293,12 +295,12 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                 if (jp.y != 255) tt += sc[jp.y] * tp.y;
                 lbsum.add(util<float>(kind, w, p, tt));
             }
-            if (REC) {
+            if (rec_w) {
                 lbt_out[i] = make_float2(s.tP, s.tQ);
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
             }
         }
-        if (!CAP && REC)
+        if (!CAP && rec_w)
             warp_rsum_lin<MT, KahanF>(warp_rows, m, lane, grouped, rot, s,
                                       valid && kind >= RA_U_LINCAP, racc, rlin);
         else
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                         if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
                     });
     reduce_and_finalize(ff_of(hsum), ff_of(uxsum), ff_of(lbsum), ff_of(racc), ff_of(rlin), m,
-                        !CAP && REC, grouped ? (lane / MT == 0) : true, P, ring_red(smem), &lr_s);
+                        !CAP && rec_w, grouped ? (lane / MT == 0) : true, P, ring_red(smem), &lr_s);
 }
 
 // Initial prices, Eq. e-initialization:
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kTile, 2)
         float d = 0.0f;
         if (valid) {
             if (kd == RA_U_LOG) d = wi / t;
-            else if (kd == RA_U_POWER) d = wi * pi * exp2f((pi - 1.0f) * log2f(t));
+            else if (kd == RA_U_POWER) d = wi * fabsf(pi) * exp2f((pi - 1.0f) * log2f(t));
             else d = t < pi ? wi : 0.0f;  // supergradient of w min(t, T) (+ const)
         }
         // own row <- d * a, in column order, then warp column sums
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(kTile, 2)
                 ratio = 0.5f;
             } else {
                 const float e = 1.0f / (1.0f - pi);
-                base = fminf(__expf(__logf(c) + e * (__logf(wi * pi / c) + 8.0f * 0.69314718f)), 1e30f);
+                base = fminf(__expf(__logf(c) + e * (__logf(wi * fabsf(pi) / c) + 8.0f * 0.69314718f)), 1e30f);
                 ratio = exp2f(-e);
             }
 #pragma unroll
@@ -881,7 +883,7 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
                 const int kd = P.kind[i];
                 const float wi = P.w[i], pi = P.param[i];
                 if (kd == RA_U_LOG) d = wi / t;
-                else if (kd == RA_U_POWER) d = wi * pi * exp2f((pi - 1.0f) * log2f(t));
+                else if (kd == RA_U_POWER) d = wi * fabsf(pi) * exp2f((pi - 1.0f) * log2f(t));
                 else d = t < pi ? wi : 0.0f;
             }
             float *own = rows + tid * m;
@@ -958,6 +960,7 @@ __global__ void __launch_bounds__(kTile)
         lbj_out = P.lbj_buf[q ^ 1];
     }
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
+    const bool rec = REC && (P.rec_on == nullptr || *P.rec_on != 0);
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<Real>(P.lam[tid]) : Fn<Real>::inf();
         s_s[tid] = (lag && tid < m) ? static_cast<Real>(P.s_prev[tid]) : Real(1);
@@ -1007,7 +1010,7 @@ __global__ void __launch_bounds__(kTile)
                 if (jp.y != 255) tt += sc[jp.y] * static_cast<Real>(tp.y);
                 lbsum += static_cast<double>(util<Real>(kind, w, p, tt));
             }
-            if (REC) {
+            if (rec) {
                 lbt_out[i] = RecOf<Real>::make(s.tP, s.tQ);
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
             }
@@ -1345,6 +1348,33 @@ cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t 
     case 8: return cap ? launch_dual_mt<8, true>(p, dp, s) : launch_dual_mt<8, false>(p, dp, s);
     case 16: return cap ? launch_dual_mt<16, true>(p, dp, s) : launch_dual_mt<16, false>(p, dp, s);
     default: return cap ? launch_dual_mt<32, true>(p, dp, s) : launch_dual_mt<32, false>(p, dp, s);
+    }
+}
+
+// g(lambda) with FP64 per-job arithmetic whatever the problem's flags (no
+// records, no lagged bound): the exact check of a gap that FP32 arithmetic
+// can only estimate.
+cudaError_t launch_dual_exact(const ra_problem *p, const double *lam, EvalOut *out, cudaStream_t s)
+{
+    DualParams dp{};
+    dp.A = p->A;
+    dp.kind = p->kind;
+    dp.w = p->w;
+    dp.param = p->param;
+    dp.R = p->R;
+    dp.n = p->n;
+    dp.m = p->m;
+    dp.lam = lam;
+    dp.partials = p->partials;
+    dp.ticket = p->ticket + 7;
+    dp.status = p->status;
+    dp.out = out;
+    const bool cap = !(p->flags & RA_NO_JOB_CAP);
+    switch (p->mt) {
+    case 4: return cap ? launch_simple<4, true, double, false, false>(p, dp, s) : launch_simple<4, false, double, false, false>(p, dp, s);
+    case 8: return cap ? launch_simple<8, true, double, false, false>(p, dp, s) : launch_simple<8, false, double, false, false>(p, dp, s);
+    case 16: return cap ? launch_simple<16, true, double, false, false>(p, dp, s) : launch_simple<16, false, double, false, false>(p, dp, s);
+    default: return cap ? launch_simple<32, true, double, false, false>(p, dp, s) : launch_simple<32, false, double, false, false>(p, dp, s);
     }
 }
 

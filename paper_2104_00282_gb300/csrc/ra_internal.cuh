@@ -143,6 +143,10 @@ struct SolverState {
     int32_t stall_window;   // 0 = never leave for a repair
     int32_t mark_evals;     // evaluation at which gap_mark was set
     double gap_mark;
+    // device time (globaltimer) of the loop: evaluations (from the end of one
+    // solver step to the start of the next, launch gaps included) and steps
+    unsigned long long t_last;
+    double eval_ns, step_ns;
 };
 
 // Internal solver status: the loop stopped for a repair of the lower bound.
@@ -214,6 +218,7 @@ struct DualParams {
     uchar2 *lbj_buf[2];
     const int32_t *pingpong;
     const int32_t *lag_on;
+    const int32_t *rec_on;    // device flag: write the records (and r_lin) (NULL = always)
     uint64_t wait_ns;         // bound of the mbarrier waits (set by the launchers)
 };
 
@@ -259,6 +264,7 @@ cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uch
                                const EvalOut *src, double *U_lb, cudaStream_t s);
 cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all = 0);
 cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s);
+cudaError_t launch_dual_exact(const ra_problem *p, const double *lam, EvalOut *out, cudaStream_t s);
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
                            double *g_out, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);
@@ -307,6 +313,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
                         double *recv, ra_allgather_fn fn, void *ctx, const ra_solve_opts *o,
                         const double *lambda0, double *lambda_out, ra_solve_info *info);
 ra_status eval_partial(ra_problem *p, const double *lambda, double *part);
+ra_status batch_rebalance(ra_batch *b, const double *lambda, const double *R_total, double step);
 ra_status combine_partials(int32_t S, int32_t m, const double *parts, const double *lambda,
                            const double *R, double *g, double *q, void *stream);
 

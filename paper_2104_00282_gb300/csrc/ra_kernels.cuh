@@ -125,12 +125,18 @@ template <> __device__ __forceinline__ double inv_price<double>(double lam)
     return lam > 0.0 ? 1.0 / lam : (lam == 0.0 ? 0x1p960 : 0.0);
 }
 
-// u(t), Section 2.2.
+// u(t), Section 2.2.  Power utilities: w t^p for 0 < p < 1, -w t^p for
+// p < 0 (the alpha-fair utilities with alpha = 1 - p > 1); the latter is
+// -inf at t = 0 like the logarithm.
 template <typename Real>
 __device__ __forceinline__ Real util(int kind, Real w, Real p, Real t)
 {
     if (kind == RA_U_LOG) return w * Fn<Real>::log(t);
-    if (kind == RA_U_POWER) return t > Real(0) ? w * Fn<Real>::exp2(p * Fn<Real>::log2(t)) : Real(0);
+    if (kind == RA_U_POWER) {
+        if (!(t > Real(0))) return p > Real(0) ? Real(0) : -Fn<Real>::inf();
+        const Real v = w * Fn<Real>::exp2(p * Fn<Real>::log2(t));
+        return p > Real(0) ? v : -v;
+    }
     if (kind == RA_U_LINCAP) return w * fmin(t, p);
     return w * fmin(t - p, Real(0));
 }
@@ -144,7 +150,8 @@ __device__ __forceinline__ float util<float>(int kind, float w, float p, float t
 {
     const float L = __logf(t);
     const float ul = w * L;
-    const float up = t > 0.0f ? w * __expf(p * L) : 0.0f;
+    const float pw = w * __expf(p * L);          // +inf at t = 0 when p < 0
+    const float up = p > 0.0f ? (t > 0.0f ? pw : 0.0f) : -pw;
     const float uc = w * fminf(t, p);
     const float ut = w * fminf(t - p, 0.0f);
     return kind == RA_U_LOG ? ul : kind == RA_U_POWER ? up : kind == RA_U_LINCAP ? uc : ut;
@@ -160,7 +167,7 @@ __device__ __forceinline__ Real topt(int kind, Real w, Real p, Real alpha, Real 
     if (kind <= RA_U_POWER) {
         if (!(alpha > Real(0))) return hi;
         if (kind == RA_U_LOG) t = w / alpha;
-        else t = Fn<Real>::exp2(Fn<Real>::log2(w * p / alpha) / (Real(1) - p));
+        else t = Fn<Real>::exp2(Fn<Real>::log2(w * fabs(p) / alpha) / (Real(1) - p));
     } else {
         if (w <= alpha) return lo;
         if (alpha < Real(0)) return hi;
@@ -170,13 +177,14 @@ __device__ __forceinline__ Real topt(int kind, Real w, Real p, Real alpha, Real 
 }
 
 // FP32 variant of topt with the same selection structure: log w/alpha,
-// power exp(log(w p / alpha) / (1 - p)), both through the fast intrinsics.
+// power exp(log(w |p| / alpha) / (1 - p)) (u'(t) = w |p| t^(p-1) for either
+// sign of p), both through the fast intrinsics.
 template <>
 __device__ __forceinline__ float topt<float>(int kind, float w, float p, float alpha, float lo,
                                              float hi)
 {
     const float tl = __fdividef(w, alpha);
-    const float tp = __expf(__fdividef(__logf(__fdividef(w * p, alpha)), 1.0f - p));
+    const float tp = __expf(__fdividef(__logf(__fdividef(w * fabsf(p), alpha)), 1.0f - p));
     float t;
     if (kind <= RA_U_POWER) {
         if (!(alpha > 0.0f)) return hi;
@@ -225,6 +233,7 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
     // independent chains (ILP); ties go to the lower column.
     Real bv[4] = {Real(0), Real(0), Real(0), Real(0)};
     int bk[4] = {-1, -1, -1, -1};
+    Real amax = Real(0);   // right end of the hull's domain (cap only)
 #pragma unroll
     for (int k = 0; k < MT; ++k) {
         const Real v = a[k] * mu[k];
@@ -232,6 +241,7 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
             bv[k & 3] = v;
             bk[k & 3] = k;
         }
+        if (CAP) amax = a[k] > amax ? a[k] : amax;
     }
     Real vb = bv[0];
     int kb = bk[0];
@@ -285,6 +295,10 @@ __device__ __forceinline__ void solve_job(const Real (&a)[MT], const Real (&lam)
         for (int step = 0; step < MT; ++step) {
             t = topt<Real>(kind, w, p, alpha, aP, aQ);
             if (t < aQ) break;
+            if (aQ >= amax) {  // no vertex to the right: the scan would find none
+                t = aQ;
+                break;
+            }
             // next vertex: minimum slope (lam_k - lQ)/(a_k - aQ) over a_k > aQ,
             // compared division-free, in four independent chains
             Real cdl[4] = {Real(1), Real(1), Real(1), Real(1)};
@@ -376,6 +390,7 @@ __device__ __forceinline__ void solve_job_sm(const float *row, const float *mu_s
     constexpr int C = MT / 4;
     float bv[4] = {0.f, 0.f, 0.f, 0.f};
     int bc[4] = {-1, -1, -1, -1};    // column of each chain's best
+    float amax = 0.f;                // right end of the hull's domain (cap only)
     if (grouped) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -387,6 +402,7 @@ __device__ __forceinline__ void solve_job_sm(const float *row, const float *mu_s
             if (v1 > bv[1]) { bv[1] = v1; bc[1] = 4 * q + 1; }
             if (v2 > bv[2]) { bv[2] = v2; bc[2] = 4 * q + 2; }
             if (v3 > bv[3]) { bv[3] = v3; bc[3] = 4 * q + 3; }
+            if (CAP) amax = fmaxf(amax, fmaxf(fmaxf(av.x, av.y), fmaxf(av.z, av.w)));
         }
     } else {
 #pragma unroll
@@ -397,6 +413,7 @@ __device__ __forceinline__ void solve_job_sm(const float *row, const float *mu_s
                     bv[k & 3] = v;
                     bc[k & 3] = k;
                 }
+                if (CAP) amax = fmaxf(amax, row[k]);
             }
         }
     }
@@ -438,6 +455,10 @@ __device__ __forceinline__ void solve_job_sm(const float *row, const float *mu_s
         for (int step = 0; step < MT; ++step) {
             t = topt<float>(kind, w, p, alpha, aP, aQ);
             if (t < aQ) break;
+            if (aQ >= amax) {  // no vertex to the right: the scan would find none
+                t = aQ;
+                break;
+            }
             // next vertex: minimum slope (lam_k - lQ)/(a_k - aQ) over a_k > aQ,
             // compared division-free, in four independent chains
             float cdl[4] = {1.f, 1.f, 1.f, 1.f};

@@ -15,9 +15,10 @@
 //   2. picks the jobs closest to a tie (at most max_flex, margins below
 //      tie_rel) from a histogram of the margins;
 //   3. on the host, in FP64, lists each picked job's optimal extreme
-//      allocations and solves a small LP for convex weights that first
-//      minimise the overuse sum_j max(r_j - R_j, 0) / R_j and then maximise
-//      the weighted utility (ra_lp.cpp);
+//      allocations and solves a small LP for convex weights that maximise
+//      their weighted utility minus the overuse sum_j max(r_j - R_j, 0)
+//      priced at lambda_j -- about the utility that scaling the overuse away
+//      would cost (ra_lp.cpp);
 //   4. applies the column scaling of Section 5 to what is left of any
 //      overuse (and, without the cap, scales under-used columns up), and
 //      writes the allocation with its utility U -- a lower bound on U*.
@@ -369,7 +370,9 @@ double util_h(int kind, double w, double p, double t)
 {
     switch (kind) {
     case RA_U_LOG: return w * std::log(t);
-    case RA_U_POWER: return t > 0.0 ? w * std::pow(t, p) : 0.0;
+    case RA_U_POWER:
+        if (!(t > 0.0)) return p > 0.0 ? 0.0 : -INFINITY;
+        return p > 0.0 ? w * std::pow(t, p) : -w * std::pow(t, p);
     case RA_U_LINCAP: return w * std::fmin(t, p);
     default: return w * std::fmin(t - p, 0.0);
     }
@@ -407,7 +410,7 @@ void job_alternatives(int m, const double *a, const double *lam, int kind, doubl
             if (kind <= RA_U_POWER) {
                 double t;
                 if (!(al > 0.0)) t = hi;
-                else t = kind == RA_U_LOG ? w / al : std::pow(w * par / al, 1.0 / (1.0 - par));
+                else t = kind == RA_U_LOG ? w / al : std::pow(w * std::fabs(par) / al, 1.0 / (1.0 - par));
                 ts[nt++] = std::fmin(std::fmax(t, aP), hi);
             } else {
                 const double T = std::fmin(std::fmax(par, aP), hi);
@@ -649,6 +652,9 @@ ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_op
     const int rows = m + G, cols = V + 2 * m + G;
     std::vector<double> theta(V, 0.0);
     int lp_status = -1;
+    double lam_floor_w = 0.0;
+    for (int j = 0; j < m; ++j) lam_floor_w = std::fmax(lam_floor_w, lam_h[j]);
+    lam_floor_w *= 1e-6;
     double overuse = 0.0;
     if (V > 0) {
         std::vector<double> A(static_cast<size_t>(rows) * cols, 0.0), b(rows, 0.0), c(cols, 0.0),
@@ -671,28 +677,19 @@ ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_op
             } else {
                 basis[j] = V + j;
             }
-            c[V + m + j] = 1.0 / std::fmax(R[j], 1e-300);
+            // overuse costs its price: scaling a column down by v_j gives up
+            // about lambda_j v_j of utility, so the LP trades overuse against
+            // the alternatives' utility in one objective (Lagrangian weights)
+            c[V + m + j] = std::fmax(lam_h[j], lam_floor_w);
         }
         for (int g = 0; g < G; ++g) {
             A[static_cast<size_t>(m + g) * cols + V + 2 * m + g] = 1.0;
             b[m + g] = 1.0;
             basis[m + g] = V + 2 * m + g;
         }
+        for (int v = 0; v < V; ++v) c[v] = -(alts[vjob[v]][valt[v]].u - alts[vjob[v]][0].u);
         lp::Simplex S(rows, cols, A, b, c, ub, basis);
         lp::Result r = S.solve(20000);
-        if (r == lp::kOptimal) {
-            std::vector<double> x = S.x();
-            // phase 2: keep the overuse, maximise the weighted utility
-            double umax = 0.0;
-            for (int v = 0; v < V; ++v)
-                umax = std::fmax(umax, std::fabs(alts[vjob[v]][valt[v]].u - alts[vjob[v]][0].u));
-            std::vector<double> c2(cols, 0.0);
-            for (int v = 0; v < V; ++v)
-                c2[v] = umax > 0.0 ? -(alts[vjob[v]][valt[v]].u - alts[vjob[v]][0].u) / umax : 0.0;
-            for (int j = 0; j < m; ++j) S.set_upper(V + m + j, x[V + m + j] * (1.0 + 1e-12) + 1e-300);
-            S.set_cost(c2);
-            r = S.solve(20000);
-        }
         lp_status = static_cast<int>(r);
         if (r == lp::kOptimal || r == lp::kIterLimit) {
             std::vector<double> x = S.x();
@@ -743,8 +740,9 @@ ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_op
     ApplyArgs ap{p->kind, p->w, p->param, p->lbt[0], p->lbt[1], p->lbj[0], W->tie, n, m, bin_cut,
                  W->flex_idx, F, W->flex_x, W->flex_ax, W->fac, jk, xk, X, p->status, p->partials,
                  p->ticket + 5, W->out};
-    if (p->flags & RA_FP64_JOBMATH) repair_apply_kernel<double><<<nb, kTile, 0, s>>>(ap);
-    else repair_apply_kernel<float><<<nb, kTile, 0, s>>>(ap);
+    // the utility of the returned allocation in FP64 (an exact lower bound on
+    // U*, whichever per-job arithmetic the evaluations use)
+    repair_apply_kernel<double><<<nb, kTile, 0, s>>>(ap);
     RA_CHECK(cudaGetLastError(), "repair apply");
     std::vector<double> res(1 + m);
     int kst = 0;

@@ -103,6 +103,9 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
         st->U_master = -__longlong_as_double(0x7ff0000000000000ll);
         st->t_start = device_ns();
         st->t_done = 0ull;
+        st->t_last = st->t_start;
+        st->eval_ns = 0.0;
+        st->step_ns = 0.0;
         st->stall_window = stall_window;
         st->mark_evals = 0;
         st->gap_mark = __longlong_as_double(0x7ff0000000000000ll);
@@ -126,7 +129,9 @@ __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const d
 // decide whether the solve is done; otherwise let the loop resume without a
 // stall exit.  The repair used the lower-bound record buffers, so the next
 // evaluation carries no lagged bound.
-__global__ void repair_accept_kernel(SolverState *st, double U_rep, int32_t *lag_on, int next_window)
+__global__ void repair_accept_kernel(SolverState *st, double U_rep, const EvalOut *exact,
+                                     double tol_exact, int32_t *lag_on, int32_t *rec_on,
+                                     int next_window)
 {
     const int j = threadIdx.x;
     const int m = st->m;
@@ -145,14 +150,23 @@ __global__ void repair_accept_kernel(SolverState *st, double U_rep, int32_t *lag
             st->master_ok = 0;
         }
         const double den = fmax(fmax(fabs(st->U_best), fabs(st->g_best)), 1.0);
-        const double gap = (st->g_best - st->U_best) / den;
+        double gap = (st->g_best - st->U_best) / den;
+        // the repaired utility is exact (FP64), and so is g at lam_best from
+        // the FP64 pass: their gap needs no allowance for FP32 rounding
+        const double g64 = exact->g;
+        const double den64 = fmax(fmax(fabs(U_rep), fabs(g64)), 1.0);
+        const bool exact_ok = better && isfinite(g64) && (g64 - U_rep) / den64 <= tol_exact;
+        if (exact_ok) {
+            st->g_best = g64;
+            gap = (g64 - U_rep) / den64;
+        }
         st->gap = gap;
         const int h = st->hist_len;
         if (better && h > 0) {
             st->hist[h - 1][2] = st->U_best;
             st->hist[h - 1][3] = gap;
         }
-        if (gap <= st->tol) {
+        if (gap <= st->tol || exact_ok) {
             st->done = 1;
             st->status = RA_OK;
         } else if (st->evals >= st->max_evals) {
@@ -167,6 +181,8 @@ __global__ void repair_accept_kernel(SolverState *st, double U_rep, int32_t *lag
         }
         st->have_lb_prev = 0;
         *lag_on = 0;
+        *rec_on = 1;
+        st->t_last = device_ns();   // the repair's time counts as neither
     }
 }
 
@@ -688,8 +704,8 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
 
 // One update after the evaluation of st->lam_trial (results in *ev).
 __device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
-                            const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
-                            int32_t *done_host_flag)
+                            int32_t *rec_on, const int *kstatus, cudaGraphConditionalHandle cond,
+                            int use_cond, int32_t *done_host_flag)
 {
     const int j = threadIdx.x;
     st += blockIdx.x;  // block b: problem b of a batch (one block for a single solve)
@@ -762,6 +778,7 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpon
         st->r_lin_prev[j] = ev->r_lin[j];
     }
     double g_best = st->g_best;
+    const double g_best_old = g_best;
     const bool improved = g_t < g_best;
     if (improved) {
         g_best = g_t;
@@ -855,8 +872,21 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpon
             st->t_done = device_ns();
         }
         *pingpong = *pingpong ^ 1;  // this evaluation's records become "previous"
-        *lag_on = 1;
-        st->have_lb_prev = 1;
+        if (rec_on) {
+            // The lagged bound of the next evaluation needs this one's records.
+            // Far from the optimum that bound is useless, so the records are
+            // written only once the dual is in its local regime: the best g
+            // improved by less than 1 % in this evaluation, or the gap is
+            // below 1 % (and from then on).
+            const int wrote = *rec_on != 0;   // set bytewise by a memset
+            *lag_on = wrote;
+            st->have_lb_prev = wrote;
+            const double dec = isfinite(g_best_old) ? (g_best_old - g_best) / fmax(fabs(g_best), 1.0) : 1.0;
+            *rec_on = (wrote || dec < 1e-2 || gap < 1e-2) ? 1 : 0;
+        } else {
+            *lag_on = 1;
+            st->have_lb_prev = 1;
+        }
         const int fin = st->done;
         if (done_host_flag) *done_host_flag = fin;
         if (use_cond) cudaGraphSetConditional(cond, fin ? 0u : 1u);
@@ -887,6 +917,8 @@ __global__ void batch_finish_kernel(const SolverState *st, const BatchProblem *p
         r.gap_per_job = (S->g_best - S->U_best) / static_cast<double>(probs[p].n);
         r.repairs = 0;
         r.n_flex = 0;
+        r.eval_ms = S->eval_ns * 1e-6;   // the batched passes it waited for
+        r.step_ms = S->step_ns * 1e-6;
         info[p] = r;
         secs[p] = S->t_done > *t0 ? static_cast<double>(S->t_done - *t0) * 1e-9 : 0.0;
     }
@@ -897,13 +929,22 @@ __global__ void batch_finish_kernel(const SolverState *st, const BatchProblem *p
 // b serves problem b of a batch.
 __global__ void __launch_bounds__(kLpThreads)
     step_kernel(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
-                const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
+                int32_t *rec_on, const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
                 int32_t *done_host_flag)
 {
+    SolverState *S = st + blockIdx.x;
+    const unsigned long long t0 = device_ns();
+    const bool live = !S->done;
     master_body(st, ev);
     __syncthreads();
     if (threadIdx.x < 32)
-        update_body(st, ev, pingpong, lag_on, kstatus, cond, use_cond, done_host_flag);
+        update_body(st, ev, pingpong, lag_on, rec_on, kstatus, cond, use_cond, done_host_flag);
+    if (threadIdx.x == 0 && live) {
+        const unsigned long long t1 = device_ns();
+        if (t0 > S->t_last) S->eval_ns += static_cast<double>(t0 - S->t_last);
+        if (t1 > t0) S->step_ns += static_cast<double>(t1 - t0);
+        S->t_last = t1;
+    }
 }
 
 // The relative gap the loop stops at.  With FP32 per-job arithmetic the
@@ -1002,6 +1043,73 @@ __global__ void shard_sum_kernel(const double *recv, int world, int count, doubl
     }
 }
 
+// ---------------------------------------------------------------------------- price coordination
+
+// Budgets of M shards of one problem (Section 7: each shard solved on its
+// own with budget R_k, the resources then moved from shards with lower
+// prices to those with higher prices).  Block j, one warp: the mean price
+// pbar_j of resource j over the shards, the step
+//     R_kj + step (lambda_kj - pbar_j) / pbar_j * R_j / M,
+// then the Euclidean projection onto {R_kj >= 0, sum_k R_kj = R_j}
+// (threshold tau with sum_k max(y_k - tau, 0) = R_j, found by bisection).
+// Smallest share of a resource a shard keeps, as a fraction of R_j / M.
+constexpr double kRebalanceFloor = 1e-3;
+
+__global__ void rebalance_kernel(const BatchProblem *probs, int P, int m, const double *lam,
+                                 const double *R_tot, double step, double *y)
+{
+    const int j = blockIdx.x, lane = threadIdx.x;
+    double sum = 0.0;
+    for (int k = lane; k < P; k += 32) sum += lam[static_cast<size_t>(k) * m + j];
+    const double pbar = wsum(sum) / P;
+    const double Rj = R_tot[j];
+    double ymin = INFINITY, ymax = -INFINITY;
+    for (int k = lane; k < P; k += 32) {
+        const double Rk = probs[k].R[j];
+        const double dk = pbar > 0.0 ? (lam[static_cast<size_t>(k) * m + j] - pbar) / pbar : 0.0;
+        const double v = Rk + step * dk * (Rj / P);
+        y[static_cast<size_t>(k) * m + j] = v;
+        ymin = fmin(ymin, v);
+        ymax = fmax(ymax, v);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        ymin = fmin(ymin, __shfl_xor_sync(kFull, ymin, off));
+        ymax = fmax(ymax, __shfl_xor_sync(kFull, ymax, off));
+    }
+    __syncwarp();
+    // projection onto {R_k >= fl, sum_k R_k = R_j}: R_k = max(y_k - tau, fl)
+    const double fl = kRebalanceFloor * Rj / P;
+    double lo = ymin - Rj / P, hi = ymax;   // f(lo) >= Rj >= f(hi) = P fl
+    for (int it = 0; it < 100; ++it) {
+        const double tau = 0.5 * (lo + hi);
+        double f = 0.0;
+        for (int k = lane; k < P; k += 32) f += fmax(y[static_cast<size_t>(k) * m + j] - tau, fl);
+        f = wsum(f);
+        if (f > Rj) lo = tau;
+        else hi = tau;
+    }
+    const double tau = 0.5 * (lo + hi);
+    // write max(y - tau, fl), then restore sum = R_j exactly on the largest entry
+    double tot = 0.0;
+    for (int k = lane; k < P; k += 32) {
+        const double v = fmax(y[static_cast<size_t>(k) * m + j] - tau, fl);
+        const_cast<double *>(probs[k].R)[j] = v;
+        tot += v;
+    }
+    tot = wsum(tot);
+    __syncwarp();
+    if (lane == 0) {
+        int kbig = 0;
+        double vbig = -1.0;
+        for (int k = 0; k < P; ++k)
+            if (probs[k].R[j] > vbig) {
+                vbig = probs[k].R[j];
+                kbig = k;
+            }
+        const_cast<double *>(probs[kbig].R)[j] = fmax(vbig + (Rj - tot), fl);
+    }
+}
+
 constexpr int kMaxRepairs = 5;   // lower-bound repairs per solve (the last at max_evals)
 
 double stop_tolerance(double tol, uint32_t flags)
@@ -1064,8 +1172,13 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     int32_t *pingpong = p->graph_flag;
     int32_t *lag_on = p->graph_flag + 1;
     int32_t *done_flag = p->graph_flag + 2;
+    int32_t *rec_on = p->graph_flag + 3;   // the evaluation in flight writes lower-bound records
     const int cap = !(p->flags & RA_NO_JOB_CAP);
-    if ((e = cudaMemsetAsync(p->status, 0, sizeof(int), s)) != cudaSuccess)
+    // A cold start writes no records until the dual is in its local regime;
+    // prices the caller supplies may already be near the optimum, so the
+    // first evaluation at them writes its records.
+    if ((e = cudaMemsetAsync(p->status, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(rec_on, lambda0 ? 1 : 0, sizeof(int32_t), s)) != cudaSuccess)
         return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     if (!lambda0) {
         if ((e = launch_init(p, st->lam_trial, s)) != cudaSuccess)
@@ -1105,6 +1218,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     dp.lbj_buf[1] = p->lbj[1];
     dp.pingpong = pingpong;
     dp.lag_on = lag_on;
+    dp.rec_on = rec_on;
     dp.partials = p->partials;
     dp.ticket = p->ticket;
     dp.status = p->status;
@@ -1133,7 +1247,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 cudaError_t e1 = launch_dual(p, dp, s);
-                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, cond,
+                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, cond,
                                                       1, nullptr);
                 cudaError_t e2 = cudaGetLastError();
                 cudaError_t e3 = cudaStreamEndCapture(s, &body);
@@ -1173,7 +1287,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             for (int k = 0; k < 8; ++k) {
                 if ((e = launch_dual(p, dh, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
-                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
+                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, 0, 0,
                                                       done_flag);
             }
             if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
@@ -1185,13 +1299,14 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     };
     struct {
         int32_t done, status, k, evals, ls_fail;
-        double g, U, gap;
+        double g, U, gap, eval_ns, step_ns;
     } h;
     auto read_state = [&]() -> ra_status {
         int32_t ints[8];
         double dbl[8];
         e = cudaMemcpyAsync(ints, &st->phase, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dbl, &st->tol, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h.eval_ns, &st->eval_ns, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(RA_ECUDA, "solver result: %s", cudaGetErrorString(e));
         h.done = ints[1];
@@ -1225,7 +1340,9 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         // while the prices are still moving a repair may fall short: exit again
         // after twice as many evaluations without the gap halving
         const int next = repairs + 1 < kMaxRepairs ? opts.repair_window << repairs : 0;
-        repair_accept_kernel<<<1, 32, 0, s>>>(st, ri.U, lag_on, next);
+        if ((e = launch_dual_exact(p, st->lam_best, p->ev + 1, s)) != cudaSuccess)
+            return fail(RA_ECUDA, "exact evaluation: %s", cudaGetErrorString(e));
+        repair_accept_kernel<<<1, 32, 0, s>>>(st, ri.U, p->ev + 1, opts.tol_rel, lag_on, rec_on, next);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return fail(RA_ECUDA, "repair accept: %s", cudaGetErrorString(e));
         if ((rs = read_state()) != RA_OK) return rs;
@@ -1249,6 +1366,8 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         info->gap_per_job = (h.g - h.U) / static_cast<double>(p->n);
         info->repairs = repairs;
         info->n_flex = static_cast<int32_t>(n_flex);
+        info->eval_ms = h.eval_ns * 1e-6;
+        info->step_ms = h.step_ns * 1e-6;
     }
     if (h.status == RA_ETIMEOUT) return fail(RA_ETIMEOUT, "a device wait gave up during the solve");
     if (h.status == RA_EUNBOUNDED) return fail(RA_EUNBOUNDED, "dual value not finite: a price reached zero without the per-job cap");
@@ -1330,7 +1449,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
             cudaError_t e1 = launch_batch_dual(4 << c, args[c], b->grid[c], batch_smem(4 << c, cap), s);
             if (e1 != cudaSuccess) return e1;
         }
-        step_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, b->status, cond,
+        step_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, nullptr, b->status, cond,
                                               0, nullptr);
         batch_any_active_kernel<<<1, 1024, 0, s>>>(b->st, P, cond, use_cond, b->active);
         return cudaGetLastError();
@@ -1490,7 +1609,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
         ra_status rs = exchange(W);
         if (rs != RA_OK) return rs;
         shard_combine_kernel<<<1, 32, 0, s>>>(recv, world, m, st->lam_trial, p->R, p->ev, p->status);
-        step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, p->status, 0, 0,
+        step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, nullptr, p->status, 0, 0,
                                                           done_flag);
         if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1500,6 +1619,8 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
     double dbl[8];
     e = cudaMemcpyAsync(ints, &st->phase, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dbl, &st->tol, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+    double tm[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tm, &st->eval_ns, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(lambda_out, st->lam_best, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(RA_ECUDA, "sharded result: %s", cudaGetErrorString(e));
@@ -1514,6 +1635,8 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
         info->gap_per_job = (dbl[4] - dbl[5]) / static_cast<double>(n_total);
         info->repairs = 0;
         info->n_flex = 0;
+        info->eval_ms = tm[0] * 1e-6;   // evaluation and exchange of the sums
+        info->step_ms = tm[1] * 1e-6;
     }
     if (ints[2] == RA_ETIMEOUT) return fail(RA_ETIMEOUT, "a device wait gave up on some shard");
     if (ints[2] == RA_EUNBOUNDED) return fail(RA_EUNBOUNDED, "dual value not finite");
@@ -1553,4 +1676,17 @@ ra_status combine_partials(int32_t S, int32_t m, const double *parts, const doub
     if (e != cudaSuccess) return fail(RA_ECUDA, "combine: %s", cudaGetErrorString(e));
     return RA_OK;
 }
+ra_status batch_rebalance(ra_batch *b, const double *lambda, const double *R_total, double step)
+{
+    const int m = b->m_h[0];
+    for (int k = 1; k < b->P; ++k)
+        if (b->m_h[k] != m) return fail(RA_EINVAL, "rebalancing needs every problem to have the same m");
+    if (!(step >= 0.0)) return fail(RA_EINVAL, "step = %g must be >= 0", step);
+    // the batch's price scratch (sum_p m_p = P m doubles) holds the proposed budgets
+    rebalance_kernel<<<m, 32, 0, b->stream>>>(b->probs, b->P, m, lambda, R_total, step, b->lam_tmp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RA_ECUDA, "rebalance: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
 }  // namespace ra

@@ -38,6 +38,11 @@ class ra_solve_opts(ctypes.Structure):
                 ("pad_", ctypes.c_int32)]
 
 
+class ra_batch_shape(ctypes.Structure):
+    _fields_ = [("chunk_tiles", ctypes.c_int32), ("whole_tiles", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
 class ra_repair_opts(ctypes.Structure):
     _fields_ = [("tie_rel", ctypes.c_double), ("max_flex", ctypes.c_int32),
                 ("pad_", ctypes.c_int32)]
@@ -57,7 +62,8 @@ class ra_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("evals", ctypes.c_int32),
                 ("ls_fail", ctypes.c_int32), ("g", ctypes.c_double), ("U_lb", ctypes.c_double),
                 ("rel_gap", ctypes.c_double), ("gap_per_job", ctypes.c_double),
-                ("repairs", ctypes.c_int32), ("n_flex", ctypes.c_int32)]
+                ("repairs", ctypes.c_int32), ("n_flex", ctypes.c_int32),
+                ("eval_ms", ctypes.c_double), ("step_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,6 +100,8 @@ def lib():
         L.ra_solve_history.restype = i32
         L.ra_recover_primal.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
         L.ra_recover_primal.restype = i32
+        L.ra_batch_rebalance.argtypes = [P, P, P, ctypes.c_double]
+        L.ra_batch_rebalance.restype = i32
         L.ra_eval_partial.argtypes = [P, P, P]
         L.ra_eval_partial.restype = i32
         L.ra_combine_partials.argtypes = [i32, i32, P, P, P, P, P, P]
@@ -111,6 +119,9 @@ def lib():
         L.ra_eval_dual_static.restype = i32
         L.ra_batch_create.argtypes = [i32, P, P, P, P, P, P, P, u32, P, ctypes.POINTER(P)]
         L.ra_batch_create.restype = i32
+        L.ra_batch_create_shaped.argtypes = [i32, P, P, P, P, P, P, P, u32,
+                                             ctypes.POINTER(ra_batch_shape), P, ctypes.POINTER(P)]
+        L.ra_batch_create_shaped.restype = i32
         L.ra_batch_destroy.argtypes = [P]
         L.ra_batch_destroy.restype = None
         L.ra_batch_prices.argtypes = [P]
@@ -261,6 +272,11 @@ def RA_SHARD_WIDTH(m):
 ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p)
 
 
+def ra_batch_rebalance(h, lam, R_total, step):
+    _check(lib().ra_batch_rebalance(h, _ptr(lam, torch.float64), _ptr(R_total, torch.float64),
+                                    float(step)))
+
+
 def ra_eval_partial(h, lam, part):
     _check(lib().ra_eval_partial(h, _ptr(lam, torch.float64), _ptr(part, torch.float64)))
 
@@ -309,17 +325,21 @@ def ra_eval_dual_static(A, kind, w, param, R, lam, g, q, flags=0, stream=None):
                                      _ptr(q, torch.float64, m)))
 
 
-def ra_batch_create(n, m, A_ptrs, kind_ptrs, w_ptrs, param_ptrs, R_ptrs, flags=0, stream=None):
+def ra_batch_create(n, m, A_ptrs, kind_ptrs, w_ptrs, param_ptrs, R_ptrs, flags=0, stream=None,
+                    shape=None):
     """n, m: P sizes; *_ptrs: P device addresses (ints) laid out as for
-    ra_problem_create."""
+    ra_problem_create; shape: optional (chunk_tiles, whole_tiles, ctas_per_sm)."""
     P = len(n)
     arr = lambda ctype, vals: (ctype * P)(*vals)
     h = ctypes.c_void_p()
-    _check(lib().ra_batch_create(P, arr(ctypes.c_int64, n), arr(ctypes.c_int32, m),
-                                 arr(ctypes.c_void_p, A_ptrs), arr(ctypes.c_void_p, kind_ptrs),
-                                 arr(ctypes.c_void_p, w_ptrs), arr(ctypes.c_void_p, param_ptrs),
-                                 arr(ctypes.c_void_p, R_ptrs), flags, _stream(stream),
-                                 ctypes.byref(h)))
+    sh = None
+    if shape is not None:
+        sh = ctypes.byref(ra_batch_shape(int(shape[0]), int(shape[1]), int(shape[2]), 0))
+    _check(lib().ra_batch_create_shaped(P, arr(ctypes.c_int64, n), arr(ctypes.c_int32, m),
+                                        arr(ctypes.c_void_p, A_ptrs), arr(ctypes.c_void_p, kind_ptrs),
+                                        arr(ctypes.c_void_p, w_ptrs), arr(ctypes.c_void_p, param_ptrs),
+                                        arr(ctypes.c_void_p, R_ptrs), flags, sh, _stream(stream),
+                                        ctypes.byref(h)))
     return h
 
 
@@ -594,7 +614,8 @@ class AllocationBatch:
     Each problem's arrays live in one packed device buffer per field, every
     segment 16-byte aligned."""
 
-    def __init__(self, problems, job_cap=True, device="cuda", stream=None, pinned=False):
+    def __init__(self, problems, job_cap=True, device="cuda", stream=None, pinned=False,
+                 shape=None):
         import numpy as np
         self.P = len(problems)
         self.n = [int(p.A.shape[0]) for p in problems]
@@ -614,14 +635,15 @@ class AllocationBatch:
         ptrs = {f: [self.dev[f].data_ptr() + o * esz[f] for o in self.offs[f]] for f in esz}
         self.flags = 0 if job_cap else RA_NO_JOB_CAP
         self.stream = stream
+        self.shape = shape
         self.handle = ra_batch_create(self.n, self.m, ptrs["A"], ptrs["kind"], ptrs["w"],
-                                      ptrs["param"], ptrs["R"], self.flags, stream)
+                                      ptrs["param"], ptrs["R"], self.flags, stream, shape)
         self.m_total = ra_batch_prices(self.handle)
         self.lam_off = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
         self.prices = None
 
     @classmethod
-    def from_tensors(cls, tensors, job_cap=True, stream=None):
+    def from_tensors(cls, tensors, job_cap=True, stream=None, shape=None):
         """Batch over device tensors (A, kind, w, param, R) per problem, used in
         place (they must stay alive with the batch; each is kept referenced)."""
         import numpy as np
@@ -635,7 +657,8 @@ class AllocationBatch:
         self.stream = stream
         cols = list(zip(*self.tensors))
         ptrs = [[x.data_ptr() for x in col] for col in cols]
-        self.handle = ra_batch_create(self.n, self.m, *ptrs, self.flags, stream)
+        self.shape = shape
+        self.handle = ra_batch_create(self.n, self.m, *ptrs, self.flags, stream, shape)
         self.m_total = ra_batch_prices(self.handle)
         self.lam_off = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
         self.prices = None

@@ -45,16 +45,22 @@ def _torch():
 
 
 def label_corpus(P, seed=TRAIN_SEED, device="cuda", group_jobs=150_000_000, tol=1e-6,
-                 max_evals=500, job_cap=False, log=print):
+                 max_evals=300, job_cap=False, log=print):
     """Features (rows x 26) and targets (rows) of P generated problems, labelled
-    by batched GPU solves; problems that do not reach the tolerance are left
-    out.  Returns (X, Y, info) with X, Y FP32 device tensors."""
+    by batched GPU solves; a problem the batch leaves above the tolerance is
+    solved once more on its own from the batch's prices (ra_solve, whose
+    repair of the lower bound closes the gaps that few jobs per resource
+    leave), so that every problem is labelled.  Returns (X, Y, info) with X,
+    Y FP32 device tensors; info counts the problems the second solve needed
+    and any that still missed the tolerance (labelled with their best
+    prices)."""
     torch = _torch()
     from . import ra
     from . import workloads as W
     sizes = W.warmstart_sizes(P, seed)
     Xs, Ys = [], []
     converged, solve_s, t0, k = 0, 0.0, time.time(), 0
+    resolved = missed = 0
     while k < P:
         grp, jobs = [], 0
         while k < P and (not grp or jobs + sizes[k] <= group_jobs):
@@ -66,19 +72,30 @@ def label_corpus(P, seed=TRAIN_SEED, device="cuda", group_jobs=150_000_000, tol=
         feats = B.features()
         t1 = time.time()
         infos, _ = B.solve(tol=tol, max_evals=max_evals)
+        prices = B.prices.clone()
+        for j, info in enumerate(infos):
+            if info["status"] == ra.RA_OK:
+                continue
+            resolved += 1
+            Pj = ra.AllocationProblem(*tensors[j], job_cap=job_cap)
+            o = M * j
+            sj = Pj.solve(tol=tol, max_evals=1000, lam0=prices[o:o + M], init_step=WARM_INIT_STEP)
+            prices[o:o + M] = Pj.prices
+            Pj.close()
+            missed += sj["status"] != ra.RA_OK
         solve_s += time.time() - t1
-        ok = torch.tensor([i["status"] == ra.RA_OK for i in infos], device=device)
-        rows = ok.repeat_interleave(M)
-        Xs.append(feats[rows].clone())
-        Ys.append(torch.log(B.prices[rows] + ra.RA_MLP_PRICE_OFFSET).float())
-        converged += int(ok.sum().item())
+        Xs.append(feats.clone())
+        Ys.append(torch.log(prices + ra.RA_MLP_PRICE_OFFSET).float())
+        converged += len(infos)
         B.close()
         del tensors, B, feats
         if log:
-            log(f"labelled {k}/{P} problems ({converged} converged), {time.time() - t0:.0f} s")
+            log(f"labelled {k}/{P} problems ({resolved} solved again, {missed} above the "
+                f"tolerance), {time.time() - t0:.0f} s")
     X = torch.cat(Xs)
     Y = torch.cat(Ys)
-    return X, Y, {"problems": P, "converged": converged, "rows": int(X.shape[0]),
+    return X, Y, {"problems": P, "labelled": converged, "solved_again": resolved,
+                  "missed_tolerance": missed, "rows": int(X.shape[0]),
                   "solve_s": solve_s, "total_s": time.time() - t0}
 
 
@@ -174,17 +191,24 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
 
 
 def summarize(rec):
-    med = lambda key: statistics.median(r[key] for r in rec)
+    med = lambda key, rs: statistics.median(r[key] for r in rs)
+    both = [r for r in rec if r["cold_status"] == 0 and r["warm_status"] == 0]
     out = {
         "problems": len(rec),
-        "cold": {"median_ms": med("cold_ms"), "median_evals": med("cold_evals"),
+        "cold": {"median_ms": med("cold_ms", rec), "median_evals": med("cold_evals", rec),
                  "converged": sum(r["cold_status"] == 0 for r in rec)},
-        "warm": {"median_ms": med("warm_ms"), "median_evals": med("warm_evals"),
+        "warm": {"median_ms": med("warm_ms", rec), "median_evals": med("warm_evals", rec),
                  "converged": sum(r["warm_status"] == 0 for r in rec),
                  "used_network_prices": sum(r["used_warm"] for r in rec)},
     }
     out["speedup_median_time"] = out["cold"]["median_ms"] / out["warm"]["median_ms"]
     out["speedup_median_evals"] = out["cold"]["median_evals"] / out["warm"]["median_evals"]
+    if both:
+        out["both_converged"] = {
+            "problems": len(both),
+            "speedup_median_time": med("cold_ms", both) / med("warm_ms", both),
+            "median_ratio_time": statistics.median(r["cold_ms"] / r["warm_ms"] for r in both),
+            "speedup_median_evals": med("cold_evals", both) / med("warm_evals", both)}
     return out
 
 
@@ -202,14 +226,16 @@ def main(argv=None):
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--report", default=None, help="write a JSON summary here")
     ap.add_argument("--job-cap", action="store_true", help="problems with 1^T x_i <= 1")
-    ap.add_argument("--max-evals", type=int, default=500)
+    ap.add_argument("--max-evals", type=int, default=None,
+                    help="evaluation limit (default: 300 for the batched labelling, 500 per "
+                         "held-out solve)")
     args = ap.parse_args(argv)
     torch = _torch()
     from . import build
     build.build()
     if args.cmd == "train":
         X, Y, info = label_corpus(args.problems or 20000, job_cap=args.job_cap,
-                                  max_evals=args.max_evals)
+                                  max_evals=args.max_evals or 300)
         print(json.dumps(info), flush=True)
         t0 = time.time()
         net, hist = train(X, Y, epochs=args.epochs)
@@ -220,7 +246,7 @@ def main(argv=None):
     else:
         net = load(args.weights)
         rec = evaluate(net, P=args.problems or 1000, job_cap=args.job_cap,
-                       max_evals=args.max_evals)
+                       max_evals=args.max_evals or 500)
         report = summarize(rec)
         report["per_problem"] = rec
     print(json.dumps({k: v for k, v in report.items() if k not in ("per_problem", "history")}),

@@ -10,7 +10,8 @@ A problem is (Section 2.4, problem (e-res-alloc)):
                (Section 2.1, "Throughput").
 * ``kind``  -- n uint8 utility kinds:
                0 = log        u(t) = w log t            (Eq. e-log-util, weighted)
-               1 = power      u(t) = w t^p, 0 < p < 1   (Section 2.2, "Power utilities")
+               1 = power      u(t) = w t^p, 0 < p < 1, or -w t^p, p < 0
+                                (Section 2.2, "Power utilities"; alpha-fair)
                2 = lin-cap    u(t) = w min(t, T)        (target-priority plus w T)
                3 = target     u(t) = w min(t - T, 0)    (Eq. e-target-priority-util)
 * ``w``     -- n FP32 weights (priorities), w > 0.
@@ -212,6 +213,23 @@ def random_small(n: int, m: int, seed: int, kinds=(0, 1, 2, 3), r_scale: float =
     param = np.where(kind == U_POWER, p, np.where(kind >= U_LINCAP, T, 0)).astype(np.float32)
     R = rng.uniform(0.5, 1.5, size=m) * r_scale * n
     return Problem(A, kind, w, param, R.astype(np.float64), f"random-small n={n} m={m}")
+
+
+def alpha_fair(n: int, m: int = 8, seed: int = 0, alpha_lo: float = 1.5,
+               alpha_hi: float = 5.0) -> Problem:
+    """Alpha-fair utilities (Section 2.2): A_ij = s_j exp(0.5 z), s_j ~ U[0.5, 4];
+    30 % log utilities (alpha = 1), 70 % t^(1-alpha) / (1-alpha) with alpha ~
+    U[alpha_lo, alpha_hi] (kind 1 with p = 1 - alpha < 0 and weight 1/|p|),
+    each times a priority ~ U[0.5, 2]; R_j ~ U[0.1, 0.4] n."""
+    rng = _rng(12, seed)
+    A = _lognormal_columns(rng, n, m, 0.5, 0.5, 4.0)
+    kind = _utility_mix(rng, n, (0.3, 0.7))
+    prio = rng.uniform(0.5, 2.0, size=n)
+    p = 1.0 - rng.uniform(alpha_lo, alpha_hi, size=n)
+    w = np.where(kind == U_POWER, prio / np.abs(p), prio).astype(np.float32)
+    param = np.where(kind == U_POWER, p, 0.0).astype(np.float32)
+    R = rng.uniform(0.1, 0.4, size=m) * n
+    return Problem(A, kind, w, param, R.astype(np.float64), f"alpha-fair n={n} m={m}")
 
 
 def random_prices(m: int, seed: int, lo: float = 0.2, hi: float = 3.0) -> np.ndarray:

@@ -118,8 +118,13 @@ def test_batch_graph_and_host_loop_agree_bitwise(ra):
     c, _ = B.solve(tol=1e-7, use_graph=True)
     lc = B.prices.cpu().numpy().copy()
     B.close()
-    assert a == b == c
+    assert _results(a) == _results(b) == _results(c)
     assert np.array_equal(la, lb) and np.array_equal(la, lc)
+
+
+def _results(infos):
+    """The solve results without the device timings."""
+    return [{k: v for k, v in i.items() if k not in ("eval_ms", "step_ms")} for i in infos]
 
 
 def test_batch_matches_single_problem_solves(ra):
@@ -187,3 +192,37 @@ def test_batch_full_size_sampled(ra, oracle):
         assert infos[k]["U_lb"] <= ref.g + 3e-6 * scale
         assert g <= ref.g + 4e-6 * scale
     B.close()
+
+
+def test_launch_shape_changes_order_not_results(ra):
+    """The batched evaluation's launch shape (chunk size, whole small problems
+    per CTA, CTAs per SM) changes which CTA adds which tiles, not the
+    optimum each problem reaches."""
+    probs = [W.batched_problem(k, n, m, seed=11) for k, (n, m) in
+             enumerate([(300, 4), (5000, 8), (70_000, 16), (1000, 32), (20_000, 32), (257, 8)])]
+    out = []
+    for shape in (None, (4, 16, 2), (64, 0, 1)):
+        B = ra.AllocationBatch(probs, shape=shape)
+        infos, _ = B.solve(tol=1e-7, max_evals=800)
+        B.close()
+        assert all(i["status"] == ra.RA_OK for i in infos), infos
+        out.append(infos)
+    for infos in out[1:]:
+        for a, b in zip(out[0], infos):
+            scale = max(abs(a["g"]), 1.0)
+            assert abs(a["g"] - b["g"]) <= 2e-7 * scale
+            assert b["U_lb"] <= a["g"] + 5e-7 * scale and a["U_lb"] <= b["g"] + 5e-7 * scale
+
+
+def test_autotune_picks_and_caches_a_shape(ra, tmp_path, monkeypatch):
+    from paper_2104_00282_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "shapes.json"))
+    monkeypatch.setattr(autotune, "CANDIDATES", [(16, 0, 0), (8, 16, 2)])
+    probs = [W.batched_problem(k, n, m, seed=12) for k, (n, m) in
+             enumerate([(400, 4), (9000, 8), (30_000, 16), (2000, 32)])]
+    tensors = [tuple(torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+                     for x in (p.A, p.kind, p.w, p.param, p.R)) for p in probs]
+    shape, entry = autotune.tune(tensors, job_cap=True, tol=1e-6)
+    assert shape in autotune.CANDIDATES and len(entry["trials"]) == 2
+    shape2, entry2 = autotune.tune(tensors, job_cap=True, tol=1e-6)
+    assert shape2 == shape and entry2["ms"] == entry["ms"]      # from the cache

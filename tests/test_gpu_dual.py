@@ -48,7 +48,7 @@ def oracle():
 def _u(kind, w, p, t):
     with np.errstate(divide="ignore", invalid="ignore"):
         return np.where(kind == 0, w * np.log(t),
-               np.where(kind == 1, w * np.power(np.maximum(t, 0), p),
+               np.where(kind == 1, np.sign(p) * w * np.power(np.maximum(t, 0), p),
                np.where(kind == 2, w * np.minimum(t, p), w * np.minimum(t - p, 0.0))))
 
 
@@ -224,6 +224,17 @@ def test_large_recipe_many_tiles_per_cta(ra, oracle, cap):
     lam = oracle.init_prices(prob, cap=cap)
     r = compare_eval(ra, oracle, prob, lam, cap=cap)
     assert r["n_argmin_exempt"] <= 200
+
+
+@pytest.mark.parametrize("cap", [False, True])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_alpha_fair_utilities(ra, oracle, cap, fp64):
+    """Power utilities with p < 0 (-w t^p, alpha-fair with alpha = 1 - p in
+    [1.5, 5]) beside log utilities."""
+    prob = W.alpha_fair(n=60_011, m=8, seed=3)
+    lam = oracle.init_prices(prob, cap=cap)
+    compare_eval(ra, oracle, prob, lam * W.random_prices(8, seed=4, lo=0.7, hi=1.4), cap=cap,
+                 fp64=fp64)
 
 
 def test_plain_small_recipe_fp64(ra, oracle):

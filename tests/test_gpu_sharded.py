@@ -94,8 +94,12 @@ def test_sharded_solve_two_shards_on_one_gpu(ra, oracle, cap):
     for o in out:
         assert not isinstance(o, Exception), o
     (l0, i0, c0), (l1, i1, c1) = out
-    # every shard ran the same update on the same combined sums
-    assert np.array_equal(l0, l1) and i0 == i1
+    # every shard ran the same update on the same combined sums (only the
+    # device timings differ)
+    timing = ("eval_ms", "step_ms")
+    assert np.array_equal(l0, l1)
+    assert {k: v for k, v in i0.items() if k not in timing} == \
+        {k: v for k, v in i1.items() if k not in timing}
     assert i0["status"] == ra.RA_OK and i0["rel_gap"] <= 1e-6, i0
     # the whole problem's certificate, rebuilt by the oracle
     theta, lams, scaled = c0
