@@ -523,6 +523,11 @@ ra_status ra_batch_features(ra_batch *b, float *feats);
  * the cold start's pass; both g values come from one pass over the data.
  */
 ra_status ra_warmstart_prices(ra_problem *prob, ra_mlp *net, double *lambda0, int32_t *used_warm);
+/* The choice of the problem's last ra_warmstart_prices call: *used_warm (host)
+ * receives 1 when the network's prices were kept, 0 when the cold start was,
+ * after the problem's stream has finished that call (synchronises the
+ * stream).  RA_EINVAL when the problem has made no such call. */
+ra_status ra_warmstart_used(ra_problem *prob, int32_t *used_warm);
 
 /*
  * ra_set_wait_timeout -- bound of every device-side wait of the library's

@@ -180,6 +180,7 @@ ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t 
     alloc(reinterpret_cast<void **>(&p->graph_flag), sizeof(int32_t) * 8);
     alloc(reinterpret_cast<void **>(&p->tmp), sizeof(double) * (RA_MAX_M + 8));
     alloc(reinterpret_cast<void **>(&p->warm), ra::kWarmBytes);
+    if (ok && cudaHostAlloc(&p->host_state, 256, cudaHostAllocDefault) != cudaSuccess) ok = false;
     if (!ok) {
         (void)cudaGetLastError();
         ra_problem_destroy(p);
@@ -214,6 +215,8 @@ void ra_problem_destroy(ra_problem *p)
     cudaFree(p->graph_flag);
     cudaFree(p->tmp);
     cudaFree(p->warm);
+    if (p->host_state) cudaFreeHost(p->host_state);
+    ra::release_loop_graph(p);
     ra::release_repair_work(p);
     if (p->side) cudaStreamDestroy(p->side);
     if (p->fork) cudaEventDestroy(p->fork);
@@ -753,6 +756,17 @@ ra_status ra_batch_features(ra_batch *b, float *feats)
     cudaError_t e = ra::launch_features(b->feat_probs, none, b->P, b->m_max, b->feat_stats, feats,
                                         b->stream);
     if (e != cudaSuccess) return fail(RA_ECUDA, "features launch: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
+
+ra_status ra_warmstart_used(ra_problem *p, int32_t *used_warm)
+{
+    if (!p || !used_warm) return fail(RA_EINVAL, "NULL argument");
+    if (!p->side) return fail(RA_EINVAL, "no ra_warmstart_prices call on this problem");
+    const int32_t *used = reinterpret_cast<const int32_t *>(p->warm + kWsUsed);
+    cudaError_t e = cudaMemcpyAsync(used_warm, used, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start flag: %s", cudaGetErrorString(e));
     return RA_OK;
 }
 

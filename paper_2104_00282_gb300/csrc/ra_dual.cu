@@ -124,10 +124,11 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
         unsigned char *base = smem + st * st_bytes;
         const long long j0 = tile * kTile;
         mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(core_bytes + (recs ? kRecBytes : 0)));
-        bulk_load(base, A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
-        bulk_load(base + a_bytes, W + j0, kTile * 4, &bars[st]);
-        bulk_load(base + a_bytes + kTile * 4, Par + j0, kTile * 4, &bars[st]);
-        bulk_load(base + a_bytes + kTile * 8, Kind + j0, kTile, &bars[st]);
+        const uint64_t pol = policy_evict_first();
+        bulk_load_stream(base, A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st], pol);
+        bulk_load_stream(base + a_bytes, W + j0, kTile * 4, &bars[st], pol);
+        bulk_load_stream(base + a_bytes + kTile * 4, Par + j0, kTile * 4, &bars[st], pol);
+        bulk_load_stream(base + a_bytes + kTile * 8, Kind + j0, kTile, &bars[st], pol);
         if (recs) {
             bulk_load(base + core_bytes, rec_t + j0, kTile * sizeof(float2), &bars[st]);
             bulk_load(base + core_bytes + kTile * sizeof(float2), rec_j + j0, kTile * sizeof(uchar2),
@@ -662,10 +663,11 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
         const int st = static_cast<int>(issued % stages);
         unsigned char *base = smem + st * StageLayout<MT>::bytes(MT);
         mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
-        bulk_load(base, P.A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st]);
-        bulk_load(base + a_bytes, P.w + j0, kTile * 4, &bars[st]);
-        bulk_load(base + a_bytes + kTile * 4, P.param + j0, kTile * 4, &bars[st]);
-        bulk_load(base + a_bytes + kTile * 8, P.kind + j0, kTile, &bars[st]);
+        const uint64_t pol = policy_evict_first();
+        bulk_load_stream(base, P.A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st], pol);
+        bulk_load_stream(base + a_bytes, P.w + j0, kTile * 4, &bars[st], pol);
+        bulk_load_stream(base + a_bytes + kTile * 4, P.param + j0, kTile * 4, &bars[st], pol);
+        bulk_load_stream(base + a_bytes + kTile * 8, P.kind + j0, kTile, &bars[st], pol);
         ++issued;
         cursor_next(B, prod);
     };

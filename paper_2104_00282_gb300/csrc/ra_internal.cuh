@@ -90,6 +90,10 @@ struct SolverState {
     double U_best;
     double gap;
     double sg_a0;         // subgradient step scale
+    // device time (globaltimer) of the loop: evaluations (from the end of one
+    // solver step to the start of the next, launch gaps included) and steps;
+    // here so that one copy of the state's first 144 bytes reads the results
+    double eval_ns, step_ns;
     double init_step;     // first step length / |lambda|
     double g_bt;          // best trial value of the current line search
     double last_step;     // norm of the last accepted price step
@@ -133,20 +137,22 @@ struct SolverState {
     double s_lin_lag[RA_MAX_M];   // the same for its linear-utility jobs
     double r_lin_prev[RA_MAX_M];  // r_lin of the previous evaluation
     double R[RA_MAX_M];
-    double S[kMaxLbfgsMem][RA_MAX_M];
-    double Y[kMaxLbfgsMem][RA_MAX_M];
-    double rho[kMaxLbfgsMem];
-    double hist[kHist][kHistCols];
+    // L-BFGS pairs in FP32: they only shape the search direction (prices,
+    // dual values and the gap stay FP64)
+    float S[kMaxLbfgsMem][RA_MAX_M];
+    float Y[kMaxLbfgsMem][RA_MAX_M];
+    float rho[kMaxLbfgsMem];
     // stall exit for the tie-aware repair (single-problem solves): the loop
     // leaves the device when the gap has not halved within stall_window
     // evaluations, so that the host can re-mix the jobs at ties
     int32_t stall_window;   // 0 = never leave for a repair
     int32_t mark_evals;     // evaluation at which gap_mark was set
     double gap_mark;
-    // device time (globaltimer) of the loop: evaluations (from the end of one
-    // solver step to the start of the next, launch gaps included) and steps
-    unsigned long long t_last;
-    double eval_ns, step_ns;
+    unsigned long long t_last;   // end of the last solver step (global timer, ns)
+    // verbose history, one row per evaluation; kept last: a single solve's
+    // step stages everything before it in shared memory and writes back only
+    // the rows it appended
+    double hist[kHist][kHistCols];
 };
 
 // Internal solver status: the loop stopped for a repair of the lower bound.
@@ -186,6 +192,12 @@ struct ra_problem {
     cudaStream_t side;   // warm start: statistics and network beside the cold-start pass
     cudaEvent_t fork, join;
     void *rep;           // allocation-repair workspace (ra_repair.cu), made on first use
+    // the solve loop's CUDA graph, built on the first graph solve and kept
+    // (it depends only on the problem's buffers and the wait limit)
+    cudaGraph_t loop_graph;
+    cudaGraphExec_t loop_exec;
+    uint64_t loop_wait_ns;
+    void *host_state;    // pinned host copy of the solver's result fields
 };
 
 namespace ra {
@@ -265,6 +277,7 @@ cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uch
 cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all = 0);
 cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s);
 cudaError_t launch_dual_exact(const ra_problem *p, const double *lam, EvalOut *out, cudaStream_t s);
+void release_loop_graph(ra_problem *p);
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
                            double *g_out, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);

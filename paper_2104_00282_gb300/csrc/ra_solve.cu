@@ -29,6 +29,13 @@ __device__ __forceinline__ double wsum(double v)
     return v;
 }
 
+__device__ __forceinline__ float wsumf(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
 __device__ __forceinline__ double wmax(double v)
 {
 #pragma unroll
@@ -218,40 +225,55 @@ __global__ void __launch_bounds__(1024)
 
 // Projected L-BFGS direction at the current point (two-loop recursion on the
 // free coordinates; lane j owns coordinate j).
+// Search direction d = -H q_cur by the two-loop recursion over the stored
+// pairs, lane j holding coordinate j; coordinates at the price floor with a
+// positive subgradient are held fixed (the projection).  The recursion is a
+// chain of dependent warp sums, so it runs in FP32 (FP64 arithmetic is slow
+// on this GPU and a direction needs no more): all pairs are loaded at once,
+// and the loops are unrolled over the largest memory so that the
+// coefficients stay in registers.
 __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
 {
     const double q = active ? st->q_cur[j] : 0.0;
     const double l = active ? st->lam_cur[j] : 0.0;
     const bool fixed = !active || (l <= st->lam_floor && q > 0.0);
-    double v = fixed ? 0.0 : q;
-    double alph[kMaxLbfgsMem];
     const int cnt = st->mem_count, mem = st->mem, head = st->mem_head;
-    for (int c = 0; c < cnt; ++c) {  // newest first
-        const int idx = (head - 1 - c + mem) % mem;
-        const double sj = fixed ? 0.0 : st->S[idx][j];
-        const double yj = fixed ? 0.0 : st->Y[idx][j];
-        const double a = st->rho[idx] * wsum(sj * v);
-        alph[c] = a;
-        v -= a * yj;
+    float sr[kMaxLbfgsMem], yr[kMaxLbfgsMem], rr[kMaxLbfgsMem], alph[kMaxLbfgsMem];
+#pragma unroll
+    for (int c = 0; c < kMaxLbfgsMem; ++c) {   // newest first
+        const bool in = c < cnt;
+        const int idx = in ? (head - 1 - c + mem) % mem : 0;   // >= 0 since c < cnt <= mem
+        sr[c] = (in && !fixed) ? st->S[idx][j] : 0.0f;
+        yr[c] = (in && !fixed) ? st->Y[idx][j] : 0.0f;
+        rr[c] = in ? st->rho[idx] : 0.0f;
     }
-    double gamma;
+    float v = fixed ? 0.0f : static_cast<float>(q);
+#pragma unroll
+    for (int c = 0; c < kMaxLbfgsMem; ++c) {
+        if (c < cnt) {
+            const float a = rr[c] * wsumf(sr[c] * v);
+            alph[c] = a;
+            v -= a * yr[c];
+        }
+    }
+    float gamma;
     if (cnt > 0) {
         const int idx = (head - 1 + mem) % mem;
-        const double sj = active ? st->S[idx][j] : 0.0, yj = active ? st->Y[idx][j] : 0.0;
-        gamma = wsum(sj * yj) / fmax(wsum(yj * yj), 1e-300);
+        const float sj = active ? st->S[idx][j] : 0.0f, yj = active ? st->Y[idx][j] : 0.0f;
+        gamma = wsumf(sj * yj) / fmaxf(wsumf(yj * yj), 1e-37f);
     } else {
         const double ln = sqrt(wsum(l * l)), qn = sqrt(wsum(fixed ? 0.0 : q * q));
-        gamma = qn > 0.0 ? st->init_step * fmax(ln, 1e-300) / qn : 0.0;
+        gamma = qn > 0.0 ? static_cast<float>(st->init_step * fmax(ln, 1e-300) / qn) : 0.0f;
     }
     v *= gamma;
-    for (int c = cnt - 1; c >= 0; --c) {  // oldest first
-        const int idx = (head - 1 - c + mem) % mem;
-        const double sj = fixed ? 0.0 : st->S[idx][j];
-        const double yj = fixed ? 0.0 : st->Y[idx][j];
-        const double b = st->rho[idx] * wsum(yj * v);
-        v += sj * (alph[c] - b);
+#pragma unroll
+    for (int c = kMaxLbfgsMem - 1; c >= 0; --c) {   // oldest first
+        if (c < cnt) {
+            const float b = rr[c] * wsumf(yr[c] * v);
+            v += sr[c] * (alph[c] - b);
+        }
     }
-    double d = fixed ? 0.0 : -v;
+    double d = fixed ? 0.0 : -static_cast<double>(v);
     // not a descent direction: drop the memory and take a scaled gradient step
     if (wsum(d * (active ? q : 0.0)) >= 0.0) {
         const double ln = sqrt(wsum(l * l)), qn = sqrt(wsum(fixed ? 0.0 : q * q));
@@ -550,11 +572,12 @@ __device__ void accept_point(SolverState *st, int j, bool active, double g_t, do
                              double lam_t, bool store_pair)
 {
     if (store_pair && st->phase == 1) {
-        const double sv = active ? lam_t - st->lam_cur[j] : 0.0;
-        const double yv = active ? q_t - st->q_cur[j] : 0.0;
-        const double sy = wsum(sv * yv);
-        const double ss = wsum(sv * sv), yy = wsum(yv * yv);
-        if (sy > 1e-12 * sqrt(ss * yy) && sy > 0.0) {
+        // the differences in FP64, the pair and its products in FP32
+        const float sv = active ? static_cast<float>(lam_t - st->lam_cur[j]) : 0.0f;
+        const float yv = active ? static_cast<float>(q_t - st->q_cur[j]) : 0.0f;
+        const float sy = wsumf(sv * yv);
+        const float ss = wsumf(sv * sv), yy = wsumf(yv * yv);
+        if (sy > 1e-12f * sqrtf(ss) * sqrtf(yy) && sy > 0.0f && isfinite(1.0f / sy)) {
             const int idx = st->mem_head;
             if (active) {
                 st->S[idx][j] = sv;
@@ -562,12 +585,12 @@ __device__ void accept_point(SolverState *st, int j, bool active, double g_t, do
             }
             __syncwarp();
             if (j == 0) {
-                st->rho[idx] = 1.0 / sy;
+                st->rho[idx] = 1.0f / sy;
                 st->mem_head = (idx + 1) % st->mem;
                 st->mem_count = min(st->mem_count + 1, st->mem);
             }
         }
-        if (j == 0) st->last_step = sqrt(ss);
+        if (j == 0) st->last_step = sqrt(static_cast<double>(ss));
     }
     __syncwarp();
     if (active) {
@@ -927,12 +950,65 @@ __global__ void batch_finish_kernel(const SolverState *st, const BatchProblem *p
 // One solver step after an evaluation: the master LP (all threads of the
 // CTA, when it runs), then the bookkeeping and price update (warp 0).  Block
 // b serves problem b of a batch.
+// Bytes of the solver state before the history table, and where a staged
+// copy of the state sits in the step kernel's dynamic shared memory.
+constexpr size_t kStateHot = offsetof(SolverState, hist);
+// the fields a solve reports (phase .. step_ns) lie at the start of the state
+constexpr size_t kResultBytes = offsetof(SolverState, step_ns) + sizeof(double);
+static_assert(kResultBytes <= 256, "result fields fit the pinned host buffer");
+constexpr size_t kStageOff = (sizeof(LpShared) + 15) / 16 * 16;
+constexpr size_t kStepSmemStaged = kStageOff + sizeof(SolverState);
+static_assert(kStateHot % 8 == 0, "state copy works in 8-byte words");
+
+// dst[0, bytes) <- src[0, bytes) by all threads of the CTA (16-byte words
+// where both sides allow, 8-byte words for the rest)
+__device__ void copy_state(void *__restrict__ dst, const void *__restrict__ src, size_t bytes)
+{
+    const bool v16 = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0;
+    size_t done = 0;
+    if (v16) {
+        // four loads in flight per thread before their stores
+        const size_t n16 = bytes / 16;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        const size_t step = blockDim.x;
+        size_t i = threadIdx.x;
+        for (; i + 3 * step < n16; i += 4 * step) {
+            const uint4 a = s4[i], b = s4[i + step], c = s4[i + 2 * step], d = s4[i + 3 * step];
+            d4[i] = a;
+            d4[i + step] = b;
+            d4[i + 2 * step] = c;
+            d4[i + 3 * step] = d;
+        }
+        for (; i < n16; i += step) d4[i] = s4[i];
+        done = n16 * 16;
+    }
+    const size_t n8 = (bytes - done) / 8;
+    for (size_t i = threadIdx.x; i < n8; i += blockDim.x)
+        reinterpret_cast<uint2 *>(static_cast<char *>(dst) + done)[i] =
+            reinterpret_cast<const uint2 *>(static_cast<const char *>(src) + done)[i];
+}
+
+// STAGE (a single solve, one CTA): the step works on a copy of the solver
+// state in shared memory -- its chains of dependent reads would otherwise
+// each wait for L2 or DRAM (the evaluation in between streams the problem
+// through L2) -- and writes the copy back, with the history rows it added.
+template <bool STAGE>
 __global__ void __launch_bounds__(kLpThreads)
     step_kernel(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
                 int32_t *rec_on, const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
                 int32_t *done_host_flag)
 {
+    extern __shared__ __align__(16) unsigned char lp_dyn[];
+    SolverState *const glob = st;
+    if (STAGE) {
+        SolverState *sh = reinterpret_cast<SolverState *>(lp_dyn + kStageOff);
+        copy_state(sh, glob, kStateHot);
+        __syncthreads();
+        st = sh;
+    }
     SolverState *S = st + blockIdx.x;
+    const int hist0 = S->hist_len;
     const unsigned long long t0 = device_ns();
     const bool live = !S->done;
     master_body(st, ev);
@@ -944,6 +1020,13 @@ __global__ void __launch_bounds__(kLpThreads)
         if (t0 > S->t_last) S->eval_ns += static_cast<double>(t0 - S->t_last);
         if (t1 > t0) S->step_ns += static_cast<double>(t1 - t0);
         S->t_last = t1;
+    }
+    if (STAGE) {
+        __syncthreads();
+        copy_state(glob, S, kStateHot);
+        const int h1 = S->hist_len;
+        for (int i = hist0 * kHistCols + threadIdx.x; i < h1 * kHistCols; i += blockDim.x)
+            glob->hist[i / kHistCols][i % kHistCols] = S->hist[i / kHistCols][i % kHistCols];
     }
 }
 
@@ -1110,6 +1193,18 @@ __global__ void rebalance_kernel(const BatchProblem *probs, int P, int m, const 
     }
 }
 
+}  // namespace
+
+void release_loop_graph(ra_problem *p)
+{
+    if (p->loop_exec) cudaGraphExecDestroy(p->loop_exec);
+    if (p->loop_graph) cudaGraphDestroy(p->loop_graph);
+    p->loop_exec = nullptr;
+    p->loop_graph = nullptr;
+}
+
+namespace {
+
 constexpr int kMaxRepairs = 5;   // lower-bound repairs per solve (the last at max_evals)
 
 double stop_tolerance(double tol, uint32_t flags)
@@ -1194,7 +1289,9 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
-    if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kStepSmemStaged))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
         return fail(RA_ECUDA, "master kernel attribute: %s", cudaGetErrorString(e));
     DualParams dp{};
@@ -1226,50 +1323,52 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     dp.skip = nullptr;
 
     // the loop as one CUDA graph: a conditional while node whose body is
-    // {dual evaluation, solver step}; kept until the solve returns, since a
-    // repair of the lower bound may resume it
-    cudaGraph_t graph = nullptr;
+    // {dual evaluation, solver step}.  It depends only on the problem's
+    // buffers and the wait limit, so it is built once and kept with the
+    // problem (a repair of the lower bound resumes it too).
     cudaGraphExec_t exec = nullptr;
     if (opts.use_graph) {
-        cudaGraphConditionalHandle cond;
-        bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
-        ok = ok && cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) ==
-                       cudaSuccess;
-        cudaGraphNode_t node;
-        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-        cp.conditional.handle = cond;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
-        if (ok) {
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        const uint64_t wns = wait_limit_ns();
+        if (p->loop_exec && p->loop_wait_ns != wns) release_loop_graph(p);
+        if (!p->loop_exec) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            cudaGraphConditionalHandle cond;
+            bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+            ok = ok && cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) ==
+                           cudaSuccess;
+            cudaGraphNode_t node;
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
             if (ok) {
-                cudaError_t e1 = launch_dual(p, dp, s);
-                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, cond,
-                                                      1, nullptr);
-                cudaError_t e2 = cudaGetLastError();
-                cudaError_t e3 = cudaStreamEndCapture(s, &body);
-                ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    cudaError_t e1 = launch_dual(p, dp, s);
+                    step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(
+                        st, p->ev, pingpong, lag_on, rec_on, p->status, cond, 1, nullptr);
+                    cudaError_t e2 = cudaGetLastError();
+                    cudaError_t e3 = cudaStreamEndCapture(s, &body);
+                    ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
+                }
+            }
+            ok = ok && cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess;
+            if (ok) {
+                p->loop_graph = graph;
+                p->loop_exec = ex;
+                p->loop_wait_ns = wns;
+            } else {   // the host-driven loop below does the same work
+                (void)cudaGetLastError();
+                if (ex) cudaGraphExecDestroy(ex);
+                if (graph) cudaGraphDestroy(graph);
             }
         }
-        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
-        if (!ok) {
-            (void)cudaGetLastError();
-            if (exec) cudaGraphExecDestroy(exec);
-            exec = nullptr;
-        }
+        exec = p->loop_exec;
     }
-    struct GraphGuard {
-        cudaGraph_t &g;
-        cudaGraphExec_t &x;
-        ~GraphGuard()
-        {
-            if (x) cudaGraphExecDestroy(x);
-            if (g) cudaGraphDestroy(g);
-        }
-    } guard{graph, exec};
     // run the loop until its while node (or the host-driven fallback) stops
     auto run_loop = [&]() -> ra_status {
         if (exec) {
@@ -1287,7 +1386,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             for (int k = 0; k < 8; ++k) {
                 if ((e = launch_dual(p, dh, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
-                step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, 0, 0,
+                step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, 0, 0,
                                                       done_flag);
             }
             if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
@@ -1301,30 +1400,45 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         int32_t done, status, k, evals, ls_fail;
         double g, U, gap, eval_ns, step_ns;
     } h;
+    // the result fields lie in the state's first kResultBytes: one copy into
+    // the problem's pinned buffer, then one synchronisation
     auto read_state = [&]() -> ra_status {
-        int32_t ints[8];
-        double dbl[8];
-        e = cudaMemcpyAsync(ints, &st->phase, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dbl, &st->tol, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h.eval_ns, &st->eval_ns, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(p->host_state, st, kResultBytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(RA_ECUDA, "solver result: %s", cudaGetErrorString(e));
-        h.done = ints[1];
-        h.status = ints[2];
-        h.k = ints[3];
-        h.evals = ints[4];
-        h.ls_fail = ints[6];
-        h.g = dbl[4];
-        h.U = dbl[5];
-        h.gap = dbl[6];
+        const SolverState *hs = static_cast<const SolverState *>(p->host_state);
+        h.done = hs->done;
+        h.status = hs->status;
+        h.k = hs->k;
+        h.evals = hs->evals;
+        h.ls_fail = hs->ls_fail;
+        h.g = hs->g_best;
+        h.U = hs->U_best;
+        h.gap = hs->gap;
+        h.eval_ns = hs->eval_ns;
+        h.step_ns = hs->step_ns;
+        return RA_OK;
+    };
+    // the best prices go out before the results are read (the usual case has
+    // no repair after that read, so nothing is left to enqueue after it)
+    auto copy_prices = [&]() -> ra_status {
+        if ((e = cudaMemcpyAsync(lambda_out, st->lam_best, sizeof(double) * p->m,
+                                 cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return fail(RA_ECUDA, "copy prices: %s", cudaGetErrorString(e));
+        if (lambda_lb && (e = cudaMemcpyAsync(lambda_lb, st->lam_lb, sizeof(double) * p->m,
+                                              cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return fail(RA_ECUDA, "copy prices: %s", cudaGetErrorString(e));
         return RA_OK;
     };
     int repairs = 0;
     int64_t n_flex = 0;
+    bool copied = false;
     for (;;) {
         ra_status rs = run_loop();
+        if (rs == RA_OK) rs = copy_prices();
         if (rs == RA_OK) rs = read_state();
         if (rs != RA_OK) return rs;
+        copied = true;
         // the lower bound stalled (or the evaluations ran out): re-mix the jobs
         // at ties at the best prices (ra_repair.cu), then stop or resume
         const bool want = opts.repair_window > 0 && repairs < kMaxRepairs &&
@@ -1345,16 +1459,15 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         repair_accept_kernel<<<1, 32, 0, s>>>(st, ri.U, p->ev + 1, opts.tol_rel, lag_on, rec_on, next);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return fail(RA_ECUDA, "repair accept: %s", cudaGetErrorString(e));
+        copied = false;
         if ((rs = read_state()) != RA_OK) return rs;
         if (h.done) break;   // closed the gap, or out of evaluations: otherwise resume
     }
     if (h.status == kStatusStalled) h.status = RA_ENOTCONV;  // defensive: never leaves the library
-    if ((e = cudaMemcpyAsync(lambda_out, st->lam_best, sizeof(double) * p->m,
-                             cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return fail(RA_ECUDA, "copy prices: %s", cudaGetErrorString(e));
-    if (lambda_lb && (e = cudaMemcpyAsync(lambda_lb, st->lam_lb, sizeof(double) * p->m,
-                                          cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return fail(RA_ECUDA, "copy prices: %s", cudaGetErrorString(e));
+    if (!copied) {
+        const ra_status rs = copy_prices();
+        if (rs != RA_OK) return rs;
+    }
     if (info) {
         info->status = h.status;
         info->iters = h.k;
@@ -1439,7 +1552,9 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
                                         b->lag_on);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "batched setup launch: %s", cudaGetErrorString(e));
-    if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kStepSmemStaged))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
         return fail(RA_ECUDA, "master kernel attribute: %s", cudaGetErrorString(e));
 
@@ -1449,7 +1564,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
             cudaError_t e1 = launch_batch_dual(4 << c, args[c], b->grid[c], batch_smem(4 << c, cap), s);
             if (e1 != cudaSuccess) return e1;
         }
-        step_kernel<<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, nullptr, b->status, cond,
+        step_kernel<false><<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, nullptr, b->status, cond,
                                               0, nullptr);
         batch_any_active_kernel<<<1, 1024, 0, s>>>(b->st, P, cond, use_cond, b->active);
         return cudaGetLastError();
@@ -1572,7 +1687,9 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
     solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, m, stop_tolerance(opts.tol_rel, p->flags),
                                          opts.max_evals, opts.lbfgs_mem, opts.update, opts.lam_floor,
                                          cap, opts.master_lb, opts.init_step, pingpong, lag_on, 0);
-    if ((e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kStepSmemStaged))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(LpShared)))) != cudaSuccess)
         return fail(RA_ECUDA, "step attribute: %s", cudaGetErrorString(e));
     DualParams dp{};
@@ -1609,7 +1726,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
         ra_status rs = exchange(W);
         if (rs != RA_OK) return rs;
         shard_combine_kernel<<<1, 32, 0, s>>>(recv, world, m, st->lam_trial, p->R, p->ev, p->status);
-        step_kernel<<<1, kLpThreads, sizeof(LpShared), s>>>(st, p->ev, pingpong, lag_on, nullptr, p->status, 0, 0,
+        step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(st, p->ev, pingpong, lag_on, nullptr, p->status, 0, 0,
                                                           done_flag);
         if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)

@@ -115,7 +115,20 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
         }
         return;
     }
-    for (int k = tid; k < S; k += blockDim.x) key[k] = fkey(P.A[sample_row(k, n, S) * P.m + j]);
+    {
+        // the sampled rows are scattered over A: eight loads in flight per
+        // thread before their keys are stored
+        constexpr int kB = 8;
+        int k = tid;
+        for (; k + (kB - 1) * static_cast<int>(blockDim.x) < S; k += kB * blockDim.x) {
+            float v[kB];
+#pragma unroll
+            for (int b = 0; b < kB; ++b) v[b] = P.A[sample_row(k + b * blockDim.x, n, S) * P.m + j];
+#pragma unroll
+            for (int b = 0; b < kB; ++b) key[k + b * blockDim.x] = fkey(v[b]);
+        }
+        for (; k < S; k += blockDim.x) key[k] = fkey(P.A[sample_row(k, n, S) * P.m + j]);
+    }
     if (tid < kQuant) {
         pref[tid] = 0u;
         rank[tid] = static_cast<unsigned>(((2 * tid + 1) * S) / 16);
@@ -301,6 +314,38 @@ __global__ void __launch_bounds__(256)
     H[static_cast<long long>(r) * N + c] = gelu(z);
 }
 
+// Inference on one problem's resources (few rows), the whole network in one
+// launch: CTA r computes row r, thread c hidden unit c of both layers with the
+// fused multiply-adds and order of rows_bias_gelu_kernel, then warp 0 the head
+// as head_kernel does -- the same bits as the three-kernel path.
+__global__ void __launch_bounds__(kHid) infer_rows_kernel(const float *X, const float *theta, float *y)
+{
+    __shared__ float xr[kFeatIn];
+    __shared__ float h1[kHid];
+    __shared__ float h2[kHid];
+    const int r = blockIdx.x, c = threadIdx.x;
+    if (c < kFeatIn) xr[c] = X[static_cast<long long>(r) * kFeatIn + c];
+    __syncthreads();
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kFeatIn; ++k) acc = fmaf(xr[k], theta[oW1 + k * kHid + c], acc);
+    h1[c] = gelu(acc + theta[ob1 + c]);
+    __syncthreads();
+    acc = 0.0f;
+#pragma unroll 16
+    for (int k = 0; k < kHid; ++k) acc = fmaf(h1[k], theta[oW2 + k * kHid + c], acc);
+    h2[c] = gelu(acc + theta[ob2 + c]);
+    __syncthreads();
+    if (c < 32) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kHid / 32; ++k) s = fmaf(h2[c + 32 * k], theta[oW3 + c + 32 * k], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (c == 0) y[r] = s + theta[ob3];
+    }
+}
+
 // y_r = h2_r . W3 + b3, one warp per row, lanes in a fixed butterfly.
 __global__ void head_kernel(int rows, const float *h2, const float *theta, float *y)
 {
@@ -469,6 +514,10 @@ cudaError_t mlp_forward(ra_mlp *net, const float *X, int rows, float *y_out, cud
     float *z1, *h1, *z2, *h2, *dz2, *dz1, *y, *dy;
     mlp_buffers(net, rows, &z1, &h1, &z2, &h2, &dz2, &dz1, &y, &dy);
     const float *th = net->theta;
+    if (rows <= 64 && y_out) {   // inference on one problem's resources
+        infer_rows_kernel<<<rows, kHid, 0, s>>>(X, th, y_out);
+        return cudaGetLastError();
+    }
     if (rows <= 64) {   // one problem's resources: one CTA per row
         rows_bias_gelu_kernel<<<rows, kHid, kFeatIn * 4, s>>>(kFeatIn, kHid, X, th + oW1, th + ob1, z1, h1);
         rows_bias_gelu_kernel<<<rows, kHid, kHid * 4, s>>>(kHid, kHid, h1, th + oW2, th + ob2, z2, h2);

@@ -145,6 +145,8 @@ def lib():
         L.ra_batch_features.restype = i32
         L.ra_warmstart_prices.argtypes = [P, P, P, ctypes.POINTER(i32)]
         L.ra_warmstart_prices.restype = i32
+        L.ra_warmstart_used.argtypes = [P, ctypes.POINTER(i32)]
+        L.ra_warmstart_used.restype = i32
         L.ra_status_string.argtypes = [i32]
         L.ra_status_string.restype = ctypes.c_char_p
         L.ra_last_error.argtypes = []
@@ -540,12 +542,20 @@ class AllocationProblem:
         ra_warmstart_features(self.handle, f)
         return f
 
-    def warm_prices(self, net):
+    def warm_prices(self, net, sync=True):
         """(lambda0, used_warm): the network's prices if their dual value is not
-        larger than the cold start's, else Eq. e-initialization."""
+        larger than the cold start's, else Eq. e-initialization.  With
+        sync=False nothing waits for the choice (used_warm is None; ask
+        warm_used() later)."""
         lam0 = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
-        used = ra_warmstart_prices(self.handle, net.handle, lam0)
-        return lam0, bool(used)
+        used = ra_warmstart_prices(self.handle, net.handle, lam0, sync)
+        return lam0, (bool(used) if sync else None)
+
+    def warm_used(self):
+        """Whether the last warm_prices kept the network's prices (synchronises)."""
+        v = ctypes.c_int32(0)
+        _check(lib().ra_warmstart_used(self.handle, ctypes.byref(v)))
+        return bool(v.value)
 
     def recover(self, lam=None, dense=False):
         lam = self.prices if lam is None else torch.as_tensor(lam, dtype=torch.float64,

@@ -169,17 +169,17 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
         def cold():   # the paper's Eq. e-initialization, unscaled
             return prob.solve(tol=tol, max_evals=max_evals, init_scale=False)
 
-        def warm():
-            lam0, used = prob.warm_prices(net)
-            step = WARM_INIT_STEP if used else None
-            return prob.solve(tol=tol, max_evals=max_evals, lam0=lam0, init_step=step), used
+        def warm():   # nothing waits for the start-price choice
+            lam0, _ = prob.warm_prices(net, sync=False)
+            return prob.solve(tol=tol, max_evals=max_evals, lam0=lam0, init_step=WARM_INIT_STEP)
 
         if i % 2 == 0:
             ci, ct = timed(cold)
-            (wi, used), wt = timed(warm)
+            wi, wt = timed(warm)
         else:
-            (wi, used), wt = timed(warm)
+            wi, wt = timed(warm)
             ci, ct = timed(cold)
+        used = prob.warm_used()
         rec.append({"n": int(sizes[i]), "cold_ms": ct, "warm_ms": wt, "cold_evals": ci["evals"],
                     "warm_evals": wi["evals"], "cold_status": ci["status"],
                     "warm_status": wi["status"], "cold_gap": ci["rel_gap"], "warm_gap": wi["rel_gap"],

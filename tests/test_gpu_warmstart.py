@@ -10,7 +10,10 @@ start-price choice) against the FP64 oracle in oracle/warmstart.py.
 * Gradient: every parameter tensor of one training step against the
   oracle's back-propagation, relative to the tensor's largest entry.
 * Adam: parameters after several steps against the oracle's Adam run on the
-  oracle's own gradients.
+  oracle's own gradients, and each step entry by entry against the oracle's
+  Adam applied to the gradient the GPU step used.
+* The committed network: on held-out problems its prices are kept and warm
+  solves take at most 0.6 times the cold evaluations (median).
 * Start prices: the choice between the network's prices and Eq.
   e-initialization follows the oracle's dual values.
 """
@@ -146,6 +149,61 @@ def test_adam_steps_match_oracle(ra, WS):
     assert L_gpu == pytest.approx(L_ora, rel=1e-3)
 
 
+def test_adam_update_is_elementwise(ra, WS):
+    """Each Adam step, applied by the oracle to the gradient the GPU step used
+    (ra_mlp_get_grads) and to the GPU's parameters before the step, gives the
+    GPU's parameters after it, entry by entry, up to FP32 rounding."""
+    theta0 = W.mlp_init(seed=5)
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(192, 26)).astype(np.float32)
+    t = (np.tanh(X[:, 2]) + 0.3 * X[:, 5]).astype(np.float32)
+    lr, steps = 3e-3, 6
+    net = ra.WarmStartMLP(theta0)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    before = theta0.astype(np.float64)
+    m = np.zeros_like(before)
+    v = np.zeros_like(before)
+    for k in range(1, steps + 1):
+        net.train_step(Xd, td, lr)
+        g = net.grads().astype(np.float64)
+        after = net.params().astype(np.float64)
+        want, m, v = WS.adam(before, g, m, v, k, lr)
+        err = np.abs(after - want)
+        bound = 1e-5 * lr + 2.5e-7 * np.abs(want)
+        assert np.all(err <= bound), (k, int(np.argmax(err - bound)), float(err.max()))
+        # and the step really moved the parameters where the gradient is not zero
+        moved = np.abs(after - before)
+        assert np.median(moved[np.abs(g) > 0]) > 0.1 * lr
+        before = after
+    net.close()
+
+
+def test_committed_network_beats_the_cold_start(ra, WS):
+    """The trained network shipped with the package, on held-out problems of
+    its recipe (seed 1, never in the training corpus; no per-job cap): its
+    prices beat Eq. e-initialization on g, and warm solves need far fewer
+    evaluations than cold ones."""
+    from paper_2104_00282_gb300 import warmstart
+    net = warmstart.load()
+    held_out = [(i, int(x)) for i, x in enumerate(W.warmstart_sizes(16, warmstart.EVAL_SEED))
+                if x >= 30_000][:10]
+    cold_e, warm_e, used_n = [], [], 0
+    for i, n in held_out:
+        A, kind, w, par, R = W.hetero_device(n, 16, warmstart.EVAL_SEED, i, "cuda")
+        P = ra.AllocationProblem(A, kind, w, par, R, job_cap=False)
+        cold = P.solve(tol=1e-6, max_evals=500, init_scale=False)
+        lam0, used = P.warm_prices(net)
+        warm = P.solve(tol=1e-6, max_evals=500, lam0=lam0, init_step=warmstart.WARM_INIT_STEP)
+        P.close()
+        assert cold["status"] == ra.RA_OK and warm["status"] == ra.RA_OK, (n, cold, warm)
+        cold_e.append(cold["evals"])
+        warm_e.append(warm["evals"])
+        used_n += used
+    net.close()
+    assert used_n == len(held_out)
+    assert np.median(warm_e) <= 0.6 * np.median(cold_e), (cold_e, warm_e)
+
+
 def constant_net(ra, WS, log_price):
     """A network whose output is log_price for every input (W3 = 0, b3)."""
     P = {name: np.zeros(shape) for name, shape in WS.SHAPES}
@@ -164,6 +222,9 @@ def test_start_price_choice_follows_oracle(ra, WS, oracle, cap):
     for price in (1e3, float(np.median(ref.lam[ref.lam > 0])) + 1e-3, float(lam_c.mean()) + 1e-3):
         net = constant_net(ra, WS, float(np.log(price)))
         lam0, used = P.warm_prices(net)
+        lam0b, none = P.warm_prices(net, sync=False)   # the same choice, asked for later
+        assert none is None and P.warm_used() == used
+        assert torch.equal(lam0, lam0b)
         net.close()
         y = np.float64(np.float32(np.log(price)))
         lam_w = np.full(prob.m, max(np.exp(y) - 1e-3, 0.0))
