@@ -116,7 +116,7 @@ class ClockSampler:
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("ra_dual.cu", "ra_internal.cuh"):
+    for f in ("ra_dual.cu", "ra_kernels.cuh", "ra_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2104_00282_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -772,6 +772,52 @@ def run_batch(args, dev, stream):
             "workload": "n log-uniform in [100, 2e5], m uniform in {4, 8, 16, 32}, "
                         "heterogeneous-hardware recipe, per-job cap 1^T x_i <= 1 (problem "
                         "e-res-alloc), cold start to 1e-6 relative gap, at most 500 evaluations"}
+
+
+def run_profile(args):
+    """Small, self-contained workloads for a profiler (ncu), one per kind of
+    launch: ``eval`` runs --reps standalone dual evaluations (ra_eval_dual) at
+    the Eq. e-initialization prices of the large recipe (n = --n, m = --m);
+    ``solve`` one solve with the host-driven loop, so that every launch is a
+    separate kernel the profiler can see (inside a CUDA graph's conditional
+    node it cannot); ``batch`` one batched solve of the batched workload's
+    first --problems problems with the host loop; ``warm`` one warm-started
+    solve (statistics, network, start prices, solve) of a held-out problem of
+    the warm-start recipe (n = --n, m = 16)."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_2104_00282_gb300 import ra
+    from paper_2104_00282_gb300 import workloads as W
+    what = args.profile
+    if what in ("eval", "solve"):
+        prob = W.config_large(n=args.n, m=args.m, seed=0)
+        P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=args.job_cap)
+        if what == "eval":
+            lam = P.init_prices()
+            for _ in range(args.reps):
+                ra.ra_eval_dual(P.handle, lam)
+            out = f"{args.reps} evaluations"
+        else:
+            out = P.solve(tol=TOL, max_evals=args.max_evals, use_graph=False)
+        P.close()
+    elif what == "batch":
+        probs = W.batched_workload(args.problems)
+        B = ra.AllocationBatch(probs, job_cap=True)
+        infos, _ = B.solve(tol=TOL, max_evals=BATCH_MAX_EVALS, use_graph=False)
+        out = f"{sum(i['status'] == 0 for i in infos)} of {len(infos)} converged"
+        B.close()
+    else:
+        from paper_2104_00282_gb300 import warmstart as WS
+        net = WS.load()
+        A, kind, w, param, R = W.hetero_device(args.n, 16, WS.EVAL_SEED, 5, "cuda")
+        P = ra.AllocationProblem(A, kind, w, param, R, job_cap=False)
+        lam0, used = P.warm_prices(net)
+        out = P.solve(tol=TOL, max_evals=BATCH_MAX_EVALS, lam0=lam0, use_graph=False)
+        P.close()
+        net.close()
+    torch.cuda.synchronize()
+    print("profile", what, out, flush=True)
 
 
 def main():

@@ -51,3 +51,19 @@ def test_traffic_figure_is_tied_to_the_kernel_source():
         assert 1.0 <= t / 1.37e9 < 1.05
     else:
         assert t is None
+
+
+def test_every_mode_of_main_is_defined():
+    """main() dispatches to one function per mode (--sweep, --profile, the
+    reference arm, the sharded and the single-GPU runs); each must exist."""
+    sys.path.insert(0, ROOT)
+    import ast
+    import bench
+
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    main = next(n for n in tree.body if isinstance(n, ast.FunctionDef) and n.name == "main")
+    called = {c.func.id for c in ast.walk(main)
+              if isinstance(c, ast.Call) and isinstance(c.func, ast.Name) and c.func.id.startswith("run_")}
+    assert {"run_sweep", "run_profile", "run_reference", "run_sharded", "run_gpu"} <= called
+    for name in called:
+        assert callable(getattr(bench, name, None)), name
