@@ -179,6 +179,7 @@ ra_status ra_problem_create(int64_t n, int32_t m, const float *A, const uint8_t 
     alloc(reinterpret_cast<void **>(&p->st), sizeof(ra::SolverState));
     alloc(reinterpret_cast<void **>(&p->graph_flag), sizeof(int32_t) * 8);
     alloc(reinterpret_cast<void **>(&p->tmp), sizeof(double) * (RA_MAX_M + 8));
+    alloc(reinterpret_cast<void **>(&p->lb_slot), sizeof(double) * 2);
     alloc(reinterpret_cast<void **>(&p->warm), ra::kWarmBytes);
     if (ok && cudaHostAlloc(&p->host_state, 256, cudaHostAllocDefault) != cudaSuccess) ok = false;
     if (!ok) {
@@ -214,6 +215,7 @@ void ra_problem_destroy(ra_problem *p)
     cudaFree(p->st);
     cudaFree(p->graph_flag);
     cudaFree(p->tmp);
+    cudaFree(p->lb_slot);
     cudaFree(p->warm);
     if (p->host_state) cudaFreeHost(p->host_state);
     ra::release_loop_graph(p);
@@ -221,6 +223,9 @@ void ra_problem_destroy(ra_problem *p)
     if (p->side) cudaStreamDestroy(p->side);
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
+    if (p->lb_side) cudaStreamDestroy(p->lb_side);
+    if (p->lb_fork) cudaEventDestroy(p->lb_fork);
+    if (p->lb_join) cudaEventDestroy(p->lb_join);
     delete p;
 }
 

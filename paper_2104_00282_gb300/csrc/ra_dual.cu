@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     const uchar2 *lbj_prev = P.lbj_prev;
     float2 *lbt_out = P.lbt_out;
     uchar2 *lbj_out = P.lbj_out;
+    const int q = P.pingpong != nullptr ? (*P.pingpong & 1) : 0;
     if (P.pingpong != nullptr) {
-        const int q = *P.pingpong & 1;
         lbt_prev = P.lbt_buf[q];
         lbj_prev = P.lbj_buf[q];
         lbt_out = P.lbt_buf[q ^ 1];
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
     // records (and the linear jobs' usage that scales them) of this evaluation
     const bool rec_w = REC && (P.rec_on == nullptr || *P.rec_on != 0);
+    if (P.pingpong != nullptr && blockIdx.x == 0 && tid == 0) P.out->rec_buf = rec_w ? (q ^ 1) : -1;
     constexpr int C = MT / 4;
     const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
 
@@ -954,8 +955,8 @@ __global__ void __launch_bounds__(kTile)
     const uchar2 *lbj_prev = P.lbj_prev;
     Rec *lbt_out = reinterpret_cast<Rec *>(P.lbt_out);
     uchar2 *lbj_out = P.lbj_out;
+    const int q = P.pingpong != nullptr ? (*P.pingpong & 1) : 0;
     if (P.pingpong != nullptr) {
-        const int q = *P.pingpong & 1;
         lbt_prev = reinterpret_cast<const Rec *>(P.lbt_buf[q]);
         lbj_prev = P.lbj_buf[q];
         lbt_out = reinterpret_cast<Rec *>(P.lbt_buf[q ^ 1]);
@@ -963,6 +964,7 @@ __global__ void __launch_bounds__(kTile)
     }
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
     const bool rec = REC && (P.rec_on == nullptr || *P.rec_on != 0);
+    if (P.pingpong != nullptr && blockIdx.x == 0 && tid == 0) P.out->rec_buf = rec ? (q ^ 1) : -1;
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<Real>(P.lam[tid]) : Fn<Real>::inf();
         s_s[tid] = (lag && tid < m) ? static_cast<Real>(P.s_prev[tid]) : Real(1);
@@ -1028,10 +1030,11 @@ __global__ void __launch_bounds__(kTile)
 // U(X~) = sum_i u_i(s_P t_P + s_Q t_Q), s the column scaling of an evaluation's
 // r and r_lin (Section 5; see column_scales), from the compact per-job records.
 template <typename Real>
-__global__ void __launch_bounds__(kTile)
-    lower_bound_kernel(const uint8_t *kind, const float *w, const float *param, const void *lbt_v,
-                       const uchar2 *lbj, long long n, int m, const EvalOut *src, const double *R,
-                       int cap, double *partials, unsigned *ticket, double *U_lb)
+__device__ __forceinline__ void lower_bound_body(const uint8_t *kind, const float *w,
+                                                 const float *param, const void *lbt_v,
+                                                 const uchar2 *lbj, long long n, int m,
+                                                 const EvalOut *src, const double *R, int cap,
+                                                 double *partials, unsigned *ticket, double *U_lb)
 {
     using Rec = typename RecOf<Real>::type;
     const Rec *lbt = static_cast<const Rec *>(lbt_v);
@@ -1053,16 +1056,81 @@ __global__ void __launch_bounds__(kTile)
     }
     __syncthreads();
     typename std::conditional<sizeof(Real) == 8, double, KahanF>::type acc{};
-    for (long long i = static_cast<long long>(blockIdx.x) * kTile + tid; i < n;
-         i += static_cast<long long>(gridDim.x) * kTile) {
-        const Rec tp = lbt[i];
-        const uchar2 jp = lbj[i];
-        const int kd = kind[i];
+    auto add_job = [&](int kd, float wi, float pi, uchar2 jp, Real tP, Real tQ) {
         const Real *sc = kd >= RA_U_LINCAP ? sl_s : s_s;
         Real tt = Real(0);
-        if (jp.x != 255) tt += sc[jp.x] * static_cast<Real>(tp.x);
-        if (jp.y != 255) tt += sc[jp.y] * static_cast<Real>(tp.y);
-        acc_add(acc, util<Real>(kd, static_cast<Real>(w[i]), static_cast<Real>(param[i]), tt));
+        if (jp.x != 255) tt += sc[jp.x] * tP;
+        if (jp.y != 255) tt += sc[jp.y] * tQ;
+        acc_add(acc, util<Real>(kd, static_cast<Real>(wi), static_cast<Real>(pi), tt));
+    };
+    const long long nthr = static_cast<long long>(gridDim.x) * kTile;
+    const long long gtid = static_cast<long long>(blockIdx.x) * kTile + tid;
+    if constexpr (sizeof(Real) == 4) {
+        // FP32 records: a thread takes four consecutive jobs at a time with
+        // 16-, 8- and 4-byte loads (records, their columns, kinds, weights,
+        // parameters: 76 bytes), two such groups in flight; all five arrays
+        // are at least 16-byte aligned
+        const long long ng = n >> 2;
+        const float4 *t4 = reinterpret_cast<const float4 *>(lbt);
+        const uint2 *j4 = reinterpret_cast<const uint2 *>(lbj);
+        const uint32_t *k4 = reinterpret_cast<const uint32_t *>(kind);
+        const float4 *w4 = reinterpret_cast<const float4 *>(w);
+        const float4 *p4 = reinterpret_cast<const float4 *>(param);
+        constexpr int kG = 2;
+        for (long long g0 = gtid; g0 < ng; g0 += kG * nthr) {
+            float4 ta[kG], tb[kG], wv[kG], pv[kG];
+            uint2 jj[kG];
+            uint32_t kk[kG];
+#pragma unroll
+            for (int u = 0; u < kG; ++u) {
+                const long long gi = g0 + u * nthr;
+                if (gi < ng) {
+                    ta[u] = t4[2 * gi];
+                    tb[u] = t4[2 * gi + 1];
+                    jj[u] = j4[gi];
+                    kk[u] = k4[gi];
+                    wv[u] = w4[gi];
+                    pv[u] = p4[gi];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kG; ++u) {
+                if (g0 + u * nthr >= ng) continue;
+                const uchar2 c0 = make_uchar2(jj[u].x & 255u, (jj[u].x >> 8) & 255u);
+                const uchar2 c1 = make_uchar2((jj[u].x >> 16) & 255u, jj[u].x >> 24);
+                const uchar2 c2 = make_uchar2(jj[u].y & 255u, (jj[u].y >> 8) & 255u);
+                const uchar2 c3 = make_uchar2((jj[u].y >> 16) & 255u, jj[u].y >> 24);
+                add_job(kk[u] & 255u, wv[u].x, pv[u].x, c0, ta[u].x, ta[u].y);
+                add_job((kk[u] >> 8) & 255u, wv[u].y, pv[u].y, c1, ta[u].z, ta[u].w);
+                add_job((kk[u] >> 16) & 255u, wv[u].z, pv[u].z, c2, tb[u].x, tb[u].y);
+                add_job(kk[u] >> 24, wv[u].w, pv[u].w, c3, tb[u].z, tb[u].w);
+            }
+        }
+        // the last n mod 4 jobs
+        const long long i = (ng << 2) + gtid;
+        if (i < n) add_job(kind[i], w[i], param[i], lbj[i], lbt[i].x, lbt[i].y);
+    } else {
+        // FP64 records: one job per thread and trip, kU trips in flight
+        constexpr int kU = 4;
+        for (long long i0 = gtid; i0 < n; i0 += kU * nthr) {
+            Rec tp[kU];
+            uchar2 jp[kU];
+            int kd[kU];
+            float wv[kU], pv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const long long i = i0 + u * nthr;
+                const bool in = i < n;
+                tp[u] = in ? lbt[i] : Rec{};
+                jp[u] = in ? lbj[i] : make_uchar2(255, 255);
+                kd[u] = in ? static_cast<int>(kind[i]) : -1;
+                wv[u] = in ? w[i] : 0.f;
+                pv[u] = in ? param[i] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (kd[u] >= 0) add_job(kd[u], wv[u], pv[u], jp[u], tp[u].x, tp[u].y);
+        }
     }
     const double accd = warp_sum_d(acc_value(acc));
     if ((tid & 31) == 0) red[tid >> 5] = accd;
@@ -1075,13 +1143,50 @@ __global__ void __launch_bounds__(kTile)
         is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (is_last && tid == 0) {
-        __threadfence();
-        double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[b]);
-        *U_lb = isnan(src->sumh) ? src->sumh : v;   // the evaluation it scales was incomplete
+    if (!is_last) return;
+    // grid stage, all threads of the last CTA: thread t adds partials t,
+    // t + 256, ... in order, then the warps' butterflies and warp order --
+    // a fixed order, so the bound is deterministic
+    __threadfence();
+    double v = 0.0;
+    for (unsigned b = tid; b < gridDim.x; b += kTile) v += __ldcg(&partials[b]);
+    v = warp_sum_d(v);
+    __syncthreads();   // red[] is reused
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kWarps; ++k) t += red[k];
+        *U_lb = isnan(src->sumh) ? src->sumh : t;   // the evaluation it scales was incomplete
         *ticket = 0u;
     }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kTile)
+    lower_bound_kernel(const uint8_t *kind, const float *w, const float *param, const void *lbt_v,
+                       const uchar2 *lbj, long long n, int m, const EvalOut *src, const double *R,
+                       int cap, double *partials, unsigned *ticket, double *U_lb)
+{
+    lower_bound_body<Real>(kind, w, param, lbt_v, lbj, n, m, src, R, cap, partials, ticket, U_lb);
+}
+
+// The solver's lower-bound pass: the records the evaluation `src` wrote (the
+// buffer it names in src->rec_buf; nothing when it wrote none) into slot
+// U_slot[src->rec_buf].  It runs beside the price update of the same
+// evaluation, which reads the other slot (the previous evaluation's bound).
+template <typename Real>
+__global__ void __launch_bounds__(kTile)
+    lagged_bound_kernel(const uint8_t *kind, const float *w, const float *param,
+                        const void *lbt0, const void *lbt1, const uchar2 *lbj0, const uchar2 *lbj1,
+                        long long n, int m, const EvalOut *src, const double *R, int cap,
+                        double *partials, unsigned *ticket, double *U_slot, const int32_t *skip)
+{
+    if (skip != nullptr && *skip != 0) return;
+    const int b = src->rec_buf;
+    if (b < 0) return;
+    lower_bound_body<Real>(kind, w, param, b ? lbt1 : lbt0, b ? lbj1 : lbj0, n, m, src, R, cap,
+                           partials, ticket, U_slot + b);
 }
 
 // ---------------------------------------------------------------------------- recovery
@@ -1393,6 +1498,24 @@ cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uch
         lower_bound_kernel<float><<<static_cast<int>(blocks), kTile, 0, s>>>(
             p->kind, p->w, p->param, lbt, lbj, p->n, p->m, src, p->R, !(p->flags & RA_NO_JOB_CAP),
             p->partials, p->ticket + 1, U_lb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lagged_bound(const ra_problem *p, const int32_t *skip, cudaStream_t s)
+{
+    // two CTAs per SM: the solver step (one CTA, ~110 registers a thread)
+    // launched beside this pass must still find room on an SM
+    long long blocks = (p->n + kTile - 1) / kTile;
+    if (blocks > 2LL * p->num_sms) blocks = 2LL * p->num_sms;
+    const int cap = !(p->flags & RA_NO_JOB_CAP);
+    if (p->flags & RA_FP64_JOBMATH)
+        lagged_bound_kernel<double><<<static_cast<int>(blocks), kTile, 0, s>>>(
+            p->kind, p->w, p->param, p->lbt[0], p->lbt[1], p->lbj[0], p->lbj[1], p->n, p->m, p->ev,
+            p->R, cap, p->partials, p->ticket + 1, p->lb_slot, skip);
+    else
+        lagged_bound_kernel<float><<<static_cast<int>(blocks), kTile, 0, s>>>(
+            p->kind, p->w, p->param, p->lbt[0], p->lbt[1], p->lbj[0], p->lbj[1], p->n, p->m, p->ev,
+            p->R, cap, p->partials, p->ticket + 1, p->lb_slot, skip);
     return cudaGetLastError();
 }
 

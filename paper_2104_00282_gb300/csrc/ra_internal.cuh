@@ -62,6 +62,8 @@ struct EvalOut {
     double q[RA_MAX_M];
     double r[RA_MAX_M];
     double r_lin[RA_MAX_M];  // part of r used by linear-utility jobs (kinds 2, 3; no-cap mode)
+    int32_t rec_buf;         // solver mode: record buffer this evaluation wrote (-1 = none)
+    int32_t pad_;
 };
 
 // Projected L-BFGS state of one solve, entirely in device memory.
@@ -198,6 +200,13 @@ struct ra_problem {
     cudaGraphExec_t loop_exec;
     uint64_t loop_wait_ns;
     void *host_state;    // pinned host copy of the solver's result fields
+    // the solve's lower-bound pass runs beside the price update on this
+    // stream (created on the first solve); its results alternate between two
+    // slots, so that the update reads the previous evaluation's bound while
+    // the pass writes this evaluation's
+    double *lb_slot;
+    cudaStream_t lb_side;
+    cudaEvent_t lb_fork, lb_join;
 };
 
 namespace ra {
@@ -281,6 +290,9 @@ void release_loop_graph(ra_problem *p);
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
                            double *g_out, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);
+// the solver's lower-bound pass over the records the last evaluation wrote
+// (into p->lb_slot[p->ev->rec_buf]); does nothing when *skip != 0
+cudaError_t launch_lagged_bound(const ra_problem *p, const int32_t *skip, cudaStream_t s);
 cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jstar, int32_t *j12,
                            float *x12, float *t, float *X, double *U, uint8_t *near_tie,
                            unsigned long long *n_ties, cudaStream_t s);

@@ -608,6 +608,9 @@ __device__ __forceinline__ void warp_rows_t32(float *warp_rows, int lane, int ro
     if (cP >= 0) warp_rows[cP * 32 + lane] = xP;
     if (cQ >= 0) warp_rows[cQ * 32 + lane] = xQ;
     __syncwarp();
+    // the lane mask rotated with the chunk order, so that chunk c's four
+    // bits sit at the constant positions 4c .. 4c + 3
+    const unsigned lmr = LIN ? __funnelshift_r(lm, lm, 4 * rot) : 0u;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int q = (c + rot) & 7;
@@ -617,11 +620,10 @@ __device__ __forceinline__ void warp_rows_t32(float *warp_rows, int lane, int ro
         cs[2] += v.z;
         cs[3] += v.w;
         if (LIN) {
-            const unsigned b = lm >> (4 * q);
-            cl[0] += (b & 1u) ? v.x : 0.f;
-            cl[1] += (b & 2u) ? v.y : 0.f;
-            cl[2] += (b & 4u) ? v.z : 0.f;
-            cl[3] += (b & 8u) ? v.w : 0.f;
+            if (lmr & (1u << (4 * c))) cl[0] += v.x;
+            if (lmr & (2u << (4 * c))) cl[1] += v.y;
+            if (lmr & (4u << (4 * c))) cl[2] += v.z;
+            if (lmr & (8u << (4 * c))) cl[3] += v.w;
         }
     }
     __syncwarp();

@@ -307,7 +307,7 @@ struct LpShared {
     double CU[kCand];                                  // candidate utility, staged
 };
 
-__device__ void master_body(SolverState *st, const EvalOut *ev)
+__device__ void master_body(SolverState *st, const EvalOut *ev, double ulb_prev)
 {
     extern __shared__ __align__(16) unsigned char lp_dyn[];
     LpShared &S = *reinterpret_cast<LpShared *>(lp_dyn);
@@ -339,7 +339,7 @@ __device__ void master_body(SolverState *st, const EvalOut *ev)
             head = (head + 1) % kCand;
             count = min(count + 1, kCand);
         }
-        if (st->have_lb_prev && isfinite(ev->Ulb_prev)) {
+        if (st->have_lb_prev && isfinite(ulb_prev)) {
             ss = head;
             head = (head + 1) % kCand;
             count = min(count + 1, kCand);
@@ -351,7 +351,7 @@ __device__ void master_body(SolverState *st, const EvalOut *ev)
             st->cand_scaled[su] = 0;
         }
         if (ss >= 0) {
-            st->cand_U[ss] = ev->Ulb_prev;
+            st->cand_U[ss] = ulb_prev;
             st->cand_scaled[ss] = 1;
         }
         s_slotU = su;
@@ -726,9 +726,9 @@ __device__ void lbfgs_update(SolverState *st, int j, int m, bool active, double 
 }
 
 // One update after the evaluation of st->lam_trial (results in *ev).
-__device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
-                            int32_t *rec_on, const int *kstatus, cudaGraphConditionalHandle cond,
-                            int use_cond, int32_t *done_host_flag)
+__device__ void update_body(SolverState *st, const EvalOut *ev, double ulb_prev, int32_t *pingpong,
+                            int32_t *lag_on, int32_t *rec_on, const int *kstatus,
+                            cudaGraphConditionalHandle cond, int use_cond, int32_t *done_host_flag)
 {
     const int j = threadIdx.x;
     st += blockIdx.x;  // block b: problem b of a batch (one block for a single solve)
@@ -755,8 +755,8 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, int32_t *pingpon
     // certificate of the best bound: one allocation with weight 1, or the
     // master LP's mixture (copied, since the candidate ring moves on)
     int cert = 0;     // 1 scaled previous, 2 raw current, 3 master mixture
-    if (st->have_lb_prev && ev->Ulb_prev > U_best) {
-        U_best = ev->Ulb_prev;
+    if (st->have_lb_prev && ulb_prev > U_best) {
+        U_best = ulb_prev;
         cert = 1;
     }
     const int feasible = wmin_i(active ? (q_t >= 0.0 ? 1 : 0) : 1);
@@ -997,8 +997,13 @@ template <bool STAGE>
 __global__ void __launch_bounds__(kLpThreads)
     step_kernel(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
                 int32_t *rec_on, const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
-                int32_t *done_host_flag)
+                int32_t *done_host_flag, const double *lb_slot)
 {
+    // the previous evaluation's column-scaled bound: from the evaluation
+    // itself (lagged pass) or, when the bound has its own pass, from the slot
+    // that pass wrote (the other slot is being written for this evaluation)
+    const double ulb_prev = lb_slot != nullptr ? lb_slot[pingpong[blockIdx.x] & 1]
+                                               : ev[blockIdx.x].Ulb_prev;
     extern __shared__ __align__(16) unsigned char lp_dyn[];
     SolverState *const glob = st;
     if (STAGE) {
@@ -1011,10 +1016,11 @@ __global__ void __launch_bounds__(kLpThreads)
     const int hist0 = S->hist_len;
     const unsigned long long t0 = device_ns();
     const bool live = !S->done;
-    master_body(st, ev);
+    master_body(st, ev, ulb_prev);
     __syncthreads();
     if (threadIdx.x < 32)
-        update_body(st, ev, pingpong, lag_on, rec_on, kstatus, cond, use_cond, done_host_flag);
+        update_body(st, ev, ulb_prev, pingpong, lag_on, rec_on, kstatus, cond, use_cond,
+                    done_host_flag);
     if (threadIdx.x == 0 && live) {
         const unsigned long long t1 = device_ns();
         if (t0 > S->t_last) S->eval_ns += static_cast<double>(t0 - S->t_last);
@@ -1305,8 +1311,13 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     dp.lam = st->lam_trial;
     dp.s_prev = st->s_lag;
     dp.s_lin_prev = st->s_lin_lag;
-    dp.lbt_prev = p->lbt[0];  // non-NULL selects the lagged instantiation
-    dp.lbj_prev = p->lbj[0];
+    // The evaluation writes its records; the column-scaled bound over them is
+    // a separate pass that runs beside the price update on a second stream
+    // (the update consumes the previous evaluation's bound, as a lagged
+    // bound would).  The pass reads 19 B per job instead of adding its work
+    // to the evaluation's instruction-bound loop.
+    dp.lbt_prev = nullptr;    // NULL selects the instantiation without the lagged bound
+    dp.lbj_prev = nullptr;
     dp.lbt_out = p->lbt[1];
     dp.lbj_out = p->lbj[1];
     dp.lbt_buf[0] = p->lbt[0];
@@ -1326,6 +1337,12 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     // {dual evaluation, solver step}.  It depends only on the problem's
     // buffers and the wait limit, so it is built once and kept with the
     // problem (a repair of the lower bound resumes it too).
+    if (!p->lb_side) {
+        e = cudaStreamCreateWithFlags(&p->lb_side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->lb_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->lb_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(RA_ECUDA, "lower-bound stream: %s", cudaGetErrorString(e));
+    }
     cudaGraphExec_t exec = nullptr;
     if (opts.use_graph) {
         const uint64_t wns = wait_limit_ns();
@@ -1348,10 +1365,16 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                 ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeThreadLocal) == cudaSuccess;
                 if (ok) {
+                    // {evaluation; then the bound pass (side stream) beside the step}
                     cudaError_t e1 = launch_dual(p, dp, s);
+                    if (e1 == cudaSuccess) e1 = cudaEventRecord(p->lb_fork, s);
+                    if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(p->lb_side, p->lb_fork, 0);
+                    if (e1 == cudaSuccess) e1 = launch_lagged_bound(p, nullptr, p->lb_side);
+                    if (e1 == cudaSuccess) e1 = cudaEventRecord(p->lb_join, p->lb_side);
                     step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(
-                        st, p->ev, pingpong, lag_on, rec_on, p->status, cond, 1, nullptr);
+                        st, p->ev, pingpong, lag_on, rec_on, p->status, cond, 1, nullptr, p->lb_slot);
                     cudaError_t e2 = cudaGetLastError();
+                    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, p->lb_join, 0);
                     cudaError_t e3 = cudaStreamEndCapture(s, &body);
                     ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
                 }
@@ -1384,10 +1407,11 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
             return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
         for (int it = 0; it < opts.max_evals && !done_h; it += 8) {
             for (int k = 0; k < 8; ++k) {
-                if ((e = launch_dual(p, dh, s)) != cudaSuccess)
+                if ((e = launch_dual(p, dh, s)) != cudaSuccess ||
+                    (e = launch_lagged_bound(p, done_flag, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
                 step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, 0, 0,
-                                                      done_flag);
+                                                      done_flag, p->lb_slot);
             }
             if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
                     cudaSuccess ||
@@ -1565,7 +1589,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
             if (e1 != cudaSuccess) return e1;
         }
         step_kernel<false><<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, nullptr, b->status, cond,
-                                              0, nullptr);
+                                              0, nullptr, nullptr);
         batch_any_active_kernel<<<1, 1024, 0, s>>>(b->st, P, cond, use_cond, b->active);
         return cudaGetLastError();
     };
@@ -1727,7 +1751,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
         if (rs != RA_OK) return rs;
         shard_combine_kernel<<<1, 32, 0, s>>>(recv, world, m, st->lam_trial, p->R, p->ev, p->status);
         step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(st, p->ev, pingpong, lag_on, nullptr, p->status, 0, 0,
-                                                          done_flag);
+                                                          done_flag, nullptr);
         if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return fail(RA_ECUDA, "sharded loop: %s", cudaGetErrorString(e));

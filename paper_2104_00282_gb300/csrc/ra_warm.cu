@@ -315,34 +315,50 @@ __global__ void __launch_bounds__(256)
 }
 
 // Inference on one problem's resources (few rows), the whole network in one
-// launch: CTA r computes row r, thread c hidden unit c of both layers with the
-// fused multiply-adds and order of rows_bias_gelu_kernel, then warp 0 the head
-// as head_kernel does -- the same bits as the three-kernel path.
-__global__ void __launch_bounds__(kHid) infer_rows_kernel(const float *X, const float *theta, float *y)
+// launch: CTA r computes row r.  Its latency is the chain of dependent L2
+// loads of W2 (256 per output unit), so each hidden unit of the second layer
+// is split over four threads (quarter g sums k in [64g, 64g + 64) in order)
+// and the quarters are added in order g = 0..3; layer 1 and the head as in
+// the training path.  The result differs from the training path's forward
+// only by that summation order (a few FP32 ulps).
+constexpr int kInferSplit = 4;
+__global__ void __launch_bounds__(kHid * kInferSplit) infer_rows_kernel(const float *X, const float *theta, float *y)
 {
     __shared__ float xr[kFeatIn];
     __shared__ float h1[kHid];
     __shared__ float h2[kHid];
-    const int r = blockIdx.x, c = threadIdx.x;
-    if (c < kFeatIn) xr[c] = X[static_cast<long long>(r) * kFeatIn + c];
+    __shared__ float part[kInferSplit][kHid];
+    const int r = blockIdx.x, t = threadIdx.x;
+    const int c = t % kHid, g = t / kHid;
+    if (t < kFeatIn) xr[t] = X[static_cast<long long>(r) * kFeatIn + t];
     __syncthreads();
+    if (g == 0) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kFeatIn; ++k) acc = fmaf(xr[k], theta[oW1 + k * kHid + c], acc);
+        h1[c] = gelu(acc + theta[ob1 + c]);
+    }
+    __syncthreads();
+    constexpr int KQ = kHid / kInferSplit;
     float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kFeatIn; ++k) acc = fmaf(xr[k], theta[oW1 + k * kHid + c], acc);
-    h1[c] = gelu(acc + theta[ob1 + c]);
-    __syncthreads();
-    acc = 0.0f;
 #pragma unroll 16
-    for (int k = 0; k < kHid; ++k) acc = fmaf(h1[k], theta[oW2 + k * kHid + c], acc);
-    h2[c] = gelu(acc + theta[ob2 + c]);
+    for (int k = g * KQ; k < (g + 1) * KQ; ++k) acc = fmaf(h1[k], theta[oW2 + k * kHid + c], acc);
+    part[g][c] = acc;
     __syncthreads();
-    if (c < 32) {
-        float s = 0.0f;
+    if (g == 0) {
+        float z = part[0][c];
 #pragma unroll
-        for (int k = 0; k < kHid / 32; ++k) s = fmaf(h2[c + 32 * k], theta[oW3 + c + 32 * k], s);
+        for (int q = 1; q < kInferSplit; ++q) z += part[q][c];
+        h2[c] = gelu(z + theta[ob2 + c]);
+    }
+    __syncthreads();
+    if (t < 32) {
+        float s2 = 0.0f;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (c == 0) y[r] = s + theta[ob3];
+        for (int k = 0; k < kHid / 32; ++k) s2 = fmaf(h2[t + 32 * k], theta[oW3 + t + 32 * k], s2);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+        if (t == 0) y[r] = s2 + theta[ob3];
     }
 }
 
@@ -515,7 +531,7 @@ cudaError_t mlp_forward(ra_mlp *net, const float *X, int rows, float *y_out, cud
     mlp_buffers(net, rows, &z1, &h1, &z2, &h2, &dz2, &dz1, &y, &dy);
     const float *th = net->theta;
     if (rows <= 64 && y_out) {   // inference on one problem's resources
-        infer_rows_kernel<<<rows, kHid, 0, s>>>(X, th, y_out);
+        infer_rows_kernel<<<rows, kHid * kInferSplit, 0, s>>>(X, th, y_out);
         return cudaGetLastError();
     }
     if (rows <= 64) {   // one problem's resources: one CTA per row
