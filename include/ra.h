@@ -135,7 +135,13 @@ typedef struct {
                              room for the FP32 rounding of its own estimate of the gap           */
     int32_t max_evals;    /* cap on dual evaluations (line-search trials included)             */
     int32_t lbfgs_mem;    /* L-BFGS memory, 1..16 (Section 6.1 uses 10)                         */
-    int32_t update;       /* 0 = projected L-BFGS, 1 = projected subgradient (Section 5)        */
+    int32_t update;       /* price update (Section 5):
+                             0 = projected L-BFGS, initial inverse Hessian chosen by the problem
+                                 (default): diagonal without the per-job cap, scalar with it;
+                             1 = projected subgradient;
+                             2 = projected L-BFGS, scalar initial matrix s^T y / y^T y;
+                             3 = projected L-BFGS, diagonal initial matrix diag(lambda_j / r_j)
+                                 scaled by s^T y / y^T D y                                    */
     int32_t use_graph;    /* 1 = run the loop as one CUDA graph with a device-side while node   */
     double lam_floor;     /* lower bound on prices; <0 selects 0 (cap) / 1e-12 max(lambda^1)    */
     int32_t master_lb;    /* 1 = also bound U* by the master LP over evaluated allocations      */

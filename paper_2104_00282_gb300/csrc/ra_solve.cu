@@ -257,7 +257,33 @@ __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
         }
     }
     float gamma;
-    if (cnt > 0) {
+    // update 0: diagonal without the per-job cap (g is smooth there except at
+    // linear jobs), scalar with it (g is piecewise smooth with kinks that pin
+    // the prices; the diagonal's long moves along flat directions land on
+    // other points of the optimal face); 3: diagonal, 2: scalar
+    const bool diag = st->update == 3 || (st->update == 0 && !st->cap);
+    if (diag) {
+        // Diagonal initial inverse Hessian D_j = lambda_j / r_j: the Newton
+        // scale of a market where every buyer's spending on j is fixed (log
+        // utilities: r_j = W_j / lambda_j, so dq_j / dlambda_j = r_j /
+        // lambda_j); with the newest pair it is scaled so that s^T y =
+        // y^T D y (the Barzilai-Borwein ratio in the D-metric), without one
+        // it is halved (a damped Newton step).  Prices at zero use 1e-3 of
+        // the largest price, usage below 1e-3 R_j counts as 1e-3 R_j.
+        const double lmax = wmax(l);
+        const double rj = active ? st->R[j] - q : 0.0;
+        const double Rj = active ? st->R[j] : 0.0;
+        const float dj = active ? static_cast<float>(fmax(l, 1e-3 * lmax) /
+                                                     fmax(rj, fmax(1e-3 * Rj, 1e-300)))
+                                : 0.0f;
+        float scale = 0.5f;
+        if (cnt > 0) {
+            const int idx = (head - 1 + mem) % mem;
+            const float sj = active ? st->S[idx][j] : 0.0f, yj = active ? st->Y[idx][j] : 0.0f;
+            scale = wsumf(sj * yj) / fmaxf(wsumf(yj * dj * yj), 1e-37f);
+        }
+        gamma = isfinite(dj * scale) ? dj * scale : 0.0f;
+    } else if (cnt > 0) {
         const int idx = (head - 1 + mem) % mem;
         const float sj = active ? st->S[idx][j] : 0.0f, yj = active ? st->Y[idx][j] : 0.0f;
         gamma = wsumf(sj * yj) / fmaxf(wsumf(yj * yj), 1e-37f);
@@ -1263,6 +1289,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if (o) opts = *o;
     if (opts.lbfgs_mem < 1 || opts.lbfgs_mem > kMaxLbfgsMem)
         return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
+    if (opts.update < 0 || opts.update > 3) return fail(RA_EINVAL, "update must be 0, 1, 2 or 3");
     if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
     if (!(opts.tol_rel >= 0.0)) return fail(RA_EINVAL, "tol_rel must be >= 0");
     if (!(opts.init_step > 0.0)) return fail(RA_EINVAL, "init_step must be > 0");
@@ -1526,6 +1553,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
     if (o) opts = *o;
     if (opts.lbfgs_mem < 1 || opts.lbfgs_mem > kMaxLbfgsMem)
         return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
+    if (opts.update < 0 || opts.update > 3) return fail(RA_EINVAL, "update must be 0, 1, 2 or 3");
     if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
     if (!(opts.tol_rel >= 0.0)) return fail(RA_EINVAL, "tol_rel must be >= 0");
     if (!(opts.init_step > 0.0)) return fail(RA_EINVAL, "init_step must be > 0");
@@ -1680,6 +1708,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
     if (n_total < p->n) return fail(RA_EINVAL, "n_total = %lld < shard size %lld", (long long)n_total, (long long)p->n);
     if (opts.lbfgs_mem < 1 || opts.lbfgs_mem > kMaxLbfgsMem)
         return fail(RA_EINVAL, "lbfgs_mem must be in [1, %d]", kMaxLbfgsMem);
+    if (opts.update < 0 || opts.update > 3) return fail(RA_EINVAL, "update must be 0, 1, 2 or 3");
     if (opts.max_evals < 1) return fail(RA_EINVAL, "max_evals must be >= 1");
     if (!(opts.tol_rel >= 0.0) || !(opts.init_step > 0.0)) return fail(RA_EINVAL, "bad tolerance or step");
     cudaStream_t s = p->stream;

@@ -501,7 +501,7 @@ class AllocationProblem:
         o.tol_rel = tol
         o.max_evals = max_evals
         o.lbfgs_mem = lbfgs_mem
-        o.update = 0 if update == "lbfgs" else 1
+        o.update = {"lbfgs": 0, "subgradient": 1, "lbfgs-scalar": 2, "lbfgs-diag": 3}[update]
         o.use_graph = 1 if use_graph else 0
         lam = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
         lam_lb = torch.empty(self.m, dtype=torch.float64, device=self.A.device)
