@@ -527,6 +527,11 @@ ra_status ra_batch_features(ra_batch *b, float *feats);
  * The statistics and the network run on a stream of the problem's own
  * (created on the first call) joined back to the problem's stream, beside
  * the cold start's pass; both g values come from one pass over the data.
+ * That pass is also a complete evaluation at lambda_w: when ra_solve is the
+ * next call on this problem and is given this lambda0 buffer (unchanged), a
+ * solve that starts from the network's prices uses it as its first
+ * evaluation instead of repeating it (any other call on the problem in
+ * between drops it).
  */
 ra_status ra_warmstart_prices(ra_problem *prob, ra_mlp *net, double *lambda0, int32_t *used_warm);
 /* The choice of the problem's last ra_warmstart_prices call: *used_warm (host)

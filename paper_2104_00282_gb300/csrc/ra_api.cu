@@ -242,6 +242,7 @@ static ra_status check_status_word(ra_problem *p)
 ra_status ra_eval_dual(ra_problem *p, const double *lambda, double *g, double *q, double *U_lb)
 {
     if (!p || !lambda) return fail(RA_EINVAL, "NULL problem or lambda");
+    p->pre_lam0 = nullptr;   // overwrites the evaluation a warm start left for ra_solve
     ra::DualParams dp{};
     dp.A = p->A;
     dp.kind = p->kind;
@@ -288,6 +289,7 @@ ra_status ra_eval_records(ra_problem *p, int32_t *j12, float *t12)
 ra_status ra_init_prices(ra_problem *p, double *lambda1)
 {
     if (!p || !lambda1) return fail(RA_EINVAL, "NULL problem or output");
+    p->pre_lam0 = nullptr;
     cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
     if (e == cudaSuccess) e = ra::launch_init(p, lambda1, p->stream);
     if (e != cudaSuccess) return fail(RA_ECUDA, "init launch: %s", cudaGetErrorString(e));
@@ -329,6 +331,7 @@ ra_status ra_recover_primal(ra_problem *p, const double *lambda, int32_t *jstar,
                             int64_t *n_near_ties)
 {
     if (!p || !lambda) return fail(RA_EINVAL, "NULL problem or lambda");
+    p->pre_lam0 = nullptr;
     unsigned long long *cnt = nullptr;
     cudaError_t e;
     if (n_near_ties) {
@@ -352,6 +355,7 @@ ra_status ra_recover_primal(ra_problem *p, const double *lambda, int32_t *jstar,
 ra_status ra_eval_partial(ra_problem *p, const double *lambda, double *part)
 {
     if (!p || !lambda || !part) return fail(RA_EINVAL, "NULL argument");
+    p->pre_lam0 = nullptr;
     return ra::eval_partial(p, lambda, part);
 }
 
@@ -369,6 +373,7 @@ ra_status ra_solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t
                            ra_solve_info *info)
 {
     if (!p) return fail(RA_EINVAL, "NULL problem");
+    p->pre_lam0 = nullptr;
     ra_status s = ra::solve_sharded(p, n_total, rank, world, send, recv, fn, ctx, opts, lambda0,
                                     lambda_out, info);
     if (s == RA_OK || s == RA_ENOTCONV) {
@@ -397,6 +402,7 @@ ra_status ra_recover_feasible(ra_problem *p, const double *lambda, const ra_repa
 {
     if (!p || !lambda || !info) return fail(RA_EINVAL, "NULL problem, lambda or info");
     if ((jk == nullptr) != (xk == nullptr)) return fail(RA_EINVAL, "jk and xk go together");
+    p->pre_lam0 = nullptr;
     ra_repair_opts o;
     ra_repair_opts_default(&o);
     if (opts) o = *opts;
@@ -779,6 +785,7 @@ ra_status ra_warmstart_prices(ra_problem *p, ra_mlp *net, double *lambda0, int32
 {
     if (!p || !net || !lambda0) return fail(RA_EINVAL, "NULL argument");
     if (p->flags & RA_FP64_JOBMATH) return fail(RA_EINVAL, "the warm start uses the FP32 job math");
+    p->pre_lam0 = nullptr;
     cudaStream_t s = p->stream;
     float *stats = reinterpret_cast<float *>(p->warm + kWsStats);
     float *feats = reinterpret_cast<float *>(p->warm + kWsFeats);
@@ -806,11 +813,15 @@ ra_status ra_warmstart_prices(ra_problem *p, ra_mlp *net, double *lambda0, int32
     if (e == cudaSuccess) e = ra::launch_init(p, lam_c, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join, 0);
     if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start launch: %s", cudaGetErrorString(e));
-    // g at both candidates in one pass over the data
+    // g at both candidates in one pass over the data, which is also the first
+    // evaluation of a solve from the network's prices: when they are chosen,
+    // ra_solve from lambda0 (called next on this problem) starts from it
     double *g2 = reinterpret_cast<double *>(p->warm + kWsG2);
-    if (e == cudaSuccess) e = ra::launch_dual_g2(p, lam_w, lam_c, g2, s);
+    if (e == cudaSuccess) e = ra::launch_dual_g2(p, lam_w, lam_c, g2, true, s);
     if (e == cudaSuccess) e = ra::launch_choose(p->m, lam_w, lam_c, g2, lambda0, used, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->graph_flag + 4, used, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(RA_ECUDA, "warm-start evaluation: %s", cudaGetErrorString(e));
+    p->pre_lam0 = lambda0;
     if (used_warm) {
         e = cudaMemcpyAsync(used_warm, used, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

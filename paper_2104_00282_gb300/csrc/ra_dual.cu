@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     __shared__ double lamd_s[RA_MAX_M], Rd_s[RA_MAX_M];
     __shared__ double lr_s;
 
-    if (P.skip != nullptr && *P.skip != 0) return;
+    if ((P.skip != nullptr && *P.skip != 0) || (P.skip2 != nullptr && *P.skip2 != 0)) return;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int m = P.m;
@@ -510,22 +510,27 @@ __global__ void __launch_bounds__(kTile, 2)
 
 // Dual values g(lambda_a) and g(lambda_b) in one pass over the data (the
 // two start points a warm start chooses between): each job is solved at both
-// price vectors from the same staged row; only the two sums of h are
-// reduced.  g_out[0], g_out[1] receive lambda^T R + sum_i h_i for each.
+// price vectors from the same staged row.  g_out[0], g_out[1] receive
+// lambda^T R + sum_i h_i for each.  With `out` set the pass is also the
+// solver's first evaluation at lambda_a: U(X), r and r_lin of a's
+// allocation are reduced as in dual_tma_kernel, the EvalOut is filled and
+// a's per-job records go to rec_t / rec_j (reported as buffer 1, the one a
+// solve's first evaluation writes).
 template <int MT, bool CAP>
 __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
     dual_g2_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
                    const double *R, long long n, int m, const double *lam_a, const double *lam_b,
                    int stages, long long num_full, double *partials, unsigned *ticket, int *status,
-                   uint64_t wait_ns, double *g_out)
+                   uint64_t wait_ns, double *g_out, float2 *rec_t, uchar2 *rec_j, EvalOut *out)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ __align__(16) float la_s[RA_MAX_M], ma_s[RA_MAX_M], lb_s[RA_MAX_M], mb_s[RA_MAX_M];
     __shared__ double lr_s[2];
     __shared__ double lad_s[RA_MAX_M], lbd_s[RA_MAX_M], Rd_s[RA_MAX_M];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool grouped = (m == MT);
+    const bool full = out != nullptr;   // the same for the whole grid
     constexpr int C = MT / 4;
     const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
     if (tid < RA_MAX_M) {
@@ -538,17 +543,30 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         mb_s[tid] = inv_price<float>(lb_s[tid]);
     }
     __syncthreads();
-    KahanF ha, hb;
+    KahanF ha, hb, ux, racc, rlin;
     auto job = [&](long long i, bool valid, const float *row, int kd, float wi, float pi,
                    float *warp_rows, const unsigned char *) {
-        (void)i;
-        (void)warp_rows;
-        if (!valid) return;
         JobSol<float> sa, sb;
-        solve_job_sm<MT, CAP>(row, ma_s, la_s, m, grouped, rot, kd, wi, pi, sa);
-        solve_job_sm<MT, CAP>(row, mb_s, lb_s, m, grouped, rot, kd, wi, pi, sb);
-        ha.add(sa.h);
-        hb.add(sb.h);
+        sa.cP = sa.cQ = -1;
+        sa.xP = sa.xQ = 0.f;
+        if (valid) {
+            solve_job_sm<MT, CAP>(row, ma_s, la_s, m, grouped, rot, kd, wi, pi, sa);
+            solve_job_sm<MT, CAP>(row, mb_s, lb_s, m, grouped, rot, kd, wi, pi, sb);
+            ha.add(sa.h);
+            hb.add(sb.h);
+            if (full) {
+                ux.add(sa.u);
+                rec_t[i] = make_float2(sa.tP, sa.tQ);
+                rec_j[i] = make_uchar2(sa.cP >= 0 ? sa.cP : 255, sa.cQ >= 0 ? sa.cQ : 255);
+            }
+        }
+        if (full) {   // every thread: warp collectives
+            if (!CAP)
+                warp_rsum_lin<MT, KahanF>(warp_rows, m, lane, grouped, rot, sa,
+                                          valid && kd >= RA_U_LINCAP, racc, rlin);
+            else
+                warp_rsum<MT, float, KahanF>(warp_rows, m, lane, grouped, rot, sa, racc);
+        }
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
@@ -560,11 +578,35 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                     });
     const FF z = red_zero<FF>();
     FF(*red)[kPartW] = ring_red(smem);
-    if (grid_reduce(ff_of(ha), ff_of(hb), z, z, z, 0, false, true, partials, ticket, red) &&
-        tid == 0) {
-        const bool bad = (ld_status(status) & kStatusTimeout) != 0;
-        g_out[0] = bad ? nan_d() : lr_s[0] + to_double(red[0][0]);
-        g_out[1] = bad ? nan_d() : lr_s[1] + to_double(red[0][1]);
+    if (!full) {
+        if (grid_reduce(ff_of(ha), ff_of(hb), z, z, z, 0, false, true, partials, ticket, red) &&
+            tid == 0) {
+            const bool bad = (ld_status(status) & kStatusTimeout) != 0;
+            g_out[0] = bad ? nan_d() : lr_s[0] + to_double(red[0][0]);
+            g_out[1] = bad ? nan_d() : lr_s[1] + to_double(red[0][1]);
+        }
+        return;
+    }
+    const bool lin = !CAP;
+    if (!grid_reduce(ff_of(ha), ff_of(ux), ff_of(hb), ff_of(racc), ff_of(rlin), m, lin,
+                     grouped ? (lane / MT == 0) : true, partials, ticket, red))
+        return;
+    const bool bad = (ld_status(status) & kStatusTimeout) != 0;
+    if (tid < m) {
+        const double r = bad ? nan_d() : to_double(red[0][4 + tid]);
+        out->r[tid] = r;
+        out->q[tid] = R[tid] - r;
+        out->r_lin[tid] = bad ? nan_d() : lin ? to_double(red[0][4 + m + tid]) : 0.0;
+    }
+    if (tid == 0) {
+        const double sumh = bad ? nan_d() : to_double(red[0][0]);
+        out->sumh = sumh;
+        out->g = lr_s[0] + sumh;
+        out->Ux = bad ? nan_d() : to_double(red[0][1]);
+        out->Ulb_prev = 0.0;
+        out->rec_buf = 1;
+        g_out[0] = out->g;
+        g_out[1] = bad ? nan_d() : lr_s[1] + to_double(red[0][2]);
     }
 }
 
@@ -945,7 +987,7 @@ __global__ void __launch_bounds__(kTile)
     __shared__ double lr_s;
     Real *rows = reinterpret_cast<Real *>(smem_simple);  // kTile x m
 
-    if (P.skip != nullptr && *P.skip != 0) return;
+    if ((P.skip != nullptr && *P.skip != 0) || (P.skip2 != nullptr && *P.skip2 != 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = P.m;
     // records in the per-job precision: FP64 job math keeps FP64 throughputs
@@ -1444,6 +1486,27 @@ cudaError_t configure_dual(ra_problem *p)
     if (per_sm < 1) per_sm = 1;
     p->grid_dual = p->num_sms * per_sm;
     p->grid_aux = p->num_sms * 4;
+    // the initial-price and ray-scaling passes hold more registers per thread
+    // (fewer CTAs fit an SM); their persistent grids must fit in one wave
+    const void *fi = nullptr, *fr = nullptr;
+    switch (p->mt) {
+    case 4: fi = reinterpret_cast<const void *>(init_tma_kernel<4>);
+            fr = reinterpret_cast<const void *>(ray_scale_kernel<4>); break;
+    case 8: fi = reinterpret_cast<const void *>(init_tma_kernel<8>);
+            fr = reinterpret_cast<const void *>(ray_scale_kernel<8>); break;
+    case 16: fi = reinterpret_cast<const void *>(init_tma_kernel<16>);
+             fr = reinterpret_cast<const void *>(ray_scale_kernel<16>); break;
+    default: fi = reinterpret_cast<const void *>(init_tma_kernel<32>);
+             fr = reinterpret_cast<const void *>(ray_scale_kernel<32>); break;
+    }
+    int per_i = 1, per_r = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_i, fi, kTile, p->smem_dual)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_r, fr, kTile, p->smem_dual)) != cudaSuccess)
+        return e;
+    p->grid_init = p->num_sms * (per_i < 1 ? 1 : per_i);
+    p->grid_ray = p->num_sms * (per_r < 1 ? 1 : per_r);
+    if (p->grid_init > p->grid_dual) p->grid_init = p->grid_dual;
+    if (p->grid_ray > p->grid_dual) p->grid_ray = p->grid_dual;
     return cudaSuccess;
 }
 
@@ -1532,8 +1595,11 @@ cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaSt
 }
 
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
-                           double *g_out, cudaStream_t s)
+                           double *g_out, bool first_eval, cudaStream_t s)
 {
+    float2 *rt = first_eval ? p->lbt[1] : nullptr;
+    uchar2 *rj = first_eval ? p->lbj[1] : nullptr;
+    EvalOut *ev = first_eval ? p->ev : nullptr;
     const long long num_full = p->n / kTile;
     int grid = p->grid_dual;
     if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
@@ -1542,11 +1608,11 @@ cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const doubl
     if (cap)                                                                                       \
         dual_g2_kernel<MT, true><<<grid, kTile, p->smem_dual, s>>>(                                \
             p->A, p->kind, p->w, p->param, p->R, p->n, p->m, lam_a, lam_b, p->stages, num_full,    \
-            p->partials, p->ticket + 3, p->status, wait_limit_ns(), g_out);                        \
+            p->partials, p->ticket + 3, p->status, wait_limit_ns(), g_out, rt, rj, ev);            \
     else                                                                                           \
         dual_g2_kernel<MT, false><<<grid, kTile, p->smem_dual, s>>>(                               \
             p->A, p->kind, p->w, p->param, p->R, p->n, p->m, lam_a, lam_b, p->stages, num_full,    \
-            p->partials, p->ticket + 3, p->status, wait_limit_ns(), g_out);
+            p->partials, p->ticket + 3, p->status, wait_limit_ns(), g_out, rt, rj, ev);
     switch (p->mt) {
     case 4: RA_G2(4) break;
     case 8: RA_G2(8) break;
@@ -1561,7 +1627,7 @@ cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long 
 {
     if (n_all <= 0) n_all = p->n;
     const long long num_full = p->n / kTile;
-    int grid = p->grid_dual;
+    int grid = p->grid_init;
     if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
     const int cap = !(p->flags & RA_NO_JOB_CAP);
 #define RA_INIT(MT)                                                                                \
@@ -1582,7 +1648,7 @@ cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long 
 cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s)
 {
     const long long num_full = p->n / kTile;
-    int grid = p->grid_dual;
+    int grid = p->grid_ray;
     if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
 #define RA_RAY(MT)                                                                                 \
     ray_scale_kernel<MT><<<grid, kTile, p->smem_dual, s>>>(p->A, p->kind, p->w, p->param, p->R,     \

@@ -178,6 +178,8 @@ struct ra_problem {
     int stages;
     int grid_dual;       // CTAs of the streaming dual kernel
     int grid_aux;        // CTAs of the lighter passes
+    int grid_init;       // CTAs of the initial-price and ray-scaling passes (their own
+    int grid_ray;        // occupancy: a grid above it would run in a second wave)
     size_t smem_dual;
     // workspace (library-owned)
     double *partials;    // max(grid) * kPartW
@@ -205,6 +207,9 @@ struct ra_problem {
     // slots, so that the update reads the previous evaluation's bound while
     // the pass writes this evaluation's
     double *lb_slot;
+    // the prices of the last ra_warmstart_prices call, whose pass was also
+    // the first evaluation of a solve from them (NULL once anything else ran)
+    const double *pre_lam0;
     cudaStream_t lb_side;
     cudaEvent_t lb_fork, lb_join;
 };
@@ -233,6 +238,7 @@ struct DualParams {
     int *status;
     EvalOut *out;
     const int32_t *skip;      // when non-NULL and *skip != 0 the launch does nothing
+    const int32_t *skip2;     // the same, a second flag (a solve's first evaluation made earlier)
     // solver mode: record buffers selected by a device-side parity word and
     // the lagged bound switched on by a device flag (NULL = fields above)
     float2 *lbt_buf[2];
@@ -287,8 +293,10 @@ cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long 
 cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s);
 cudaError_t launch_dual_exact(const ra_problem *p, const double *lam, EvalOut *out, cudaStream_t s);
 void release_loop_graph(ra_problem *p);
+// g at two price vectors in one pass; with first_eval also the solver's first
+// evaluation at lam_a (p->ev, records into buffer 1)
 cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const double *lam_b,
-                           double *g_out, cudaStream_t s);
+                           double *g_out, bool first_eval, cudaStream_t s);
 cudaError_t launch_records(const ra_problem *p, int32_t *j12, float *t12, cudaStream_t s);
 // the solver's lower-bound pass over the records the last evaluation wrote
 // (into p->lb_slot[p->ev->rec_buf]); does nothing when *skip != 0

@@ -1023,7 +1023,7 @@ template <bool STAGE>
 __global__ void __launch_bounds__(kLpThreads)
     step_kernel(SolverState *st, const EvalOut *ev, int32_t *pingpong, int32_t *lag_on,
                 int32_t *rec_on, const int *kstatus, cudaGraphConditionalHandle cond, int use_cond,
-                int32_t *done_host_flag, const double *lb_slot)
+                int32_t *done_host_flag, const double *lb_slot, int32_t *first_flag)
 {
     // the previous evaluation's column-scaled bound: from the evaluation
     // itself (lagged pass) or, when the bound has its own pass, from the slot
@@ -1060,6 +1060,8 @@ __global__ void __launch_bounds__(kLpThreads)
         for (int i = hist0 * kHistCols + threadIdx.x; i < h1 * kHistCols; i += blockDim.x)
             glob->hist[i / kHistCols][i % kHistCols] = S->hist[i / kHistCols][i % kHistCols];
     }
+    // a first evaluation made before the solve has been consumed
+    if (first_flag != nullptr && threadIdx.x == 0) *first_flag = 0;
 }
 
 // The relative gap the loop stops at.  With FP32 per-job arithmetic the
@@ -1301,12 +1303,19 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     int32_t *lag_on = p->graph_flag + 1;
     int32_t *done_flag = p->graph_flag + 2;
     int32_t *rec_on = p->graph_flag + 3;   // the evaluation in flight writes lower-bound records
+    // set by ra_warmstart_prices when its pass was this solve's first
+    // evaluation (at the network's prices, when they were chosen): the first
+    // evaluation launch then does nothing and the step reads that pass
+    int32_t *first_flag = p->graph_flag + 4;
+    const bool pre = lambda0 != nullptr && lambda0 == p->pre_lam0;
+    p->pre_lam0 = nullptr;
     const int cap = !(p->flags & RA_NO_JOB_CAP);
     // A cold start writes no records until the dual is in its local regime;
     // prices the caller supplies may already be near the optimum, so the
     // first evaluation at them writes its records.
     if ((e = cudaMemsetAsync(p->status, 0, sizeof(int), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(rec_on, lambda0 ? 1 : 0, sizeof(int32_t), s)) != cudaSuccess)
+        (e = cudaMemsetAsync(rec_on, lambda0 ? 1 : 0, sizeof(int32_t), s)) != cudaSuccess ||
+        (!pre && (e = cudaMemsetAsync(first_flag, 0, sizeof(int32_t), s)) != cudaSuccess))
         return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     if (!lambda0) {
         if ((e = launch_init(p, st->lam_trial, s)) != cudaSuccess)
@@ -1359,6 +1368,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     dp.status = p->status;
     dp.out = p->ev;
     dp.skip = nullptr;
+    dp.skip2 = first_flag;
 
     // the loop as one CUDA graph: a conditional while node whose body is
     // {dual evaluation, solver step}.  It depends only on the problem's
@@ -1399,7 +1409,8 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                     if (e1 == cudaSuccess) e1 = launch_lagged_bound(p, nullptr, p->lb_side);
                     if (e1 == cudaSuccess) e1 = cudaEventRecord(p->lb_join, p->lb_side);
                     step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(
-                        st, p->ev, pingpong, lag_on, rec_on, p->status, cond, 1, nullptr, p->lb_slot);
+                        st, p->ev, pingpong, lag_on, rec_on, p->status, cond, 1, nullptr, p->lb_slot,
+                        first_flag);
                     cudaError_t e2 = cudaGetLastError();
                     if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, p->lb_join, 0);
                     cudaError_t e3 = cudaStreamEndCapture(s, &body);
@@ -1438,7 +1449,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                     (e = launch_lagged_bound(p, done_flag, s)) != cudaSuccess)
                     return fail(RA_ECUDA, "dual launch: %s", cudaGetErrorString(e));
                 step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(st, p->ev, pingpong, lag_on, rec_on, p->status, 0, 0,
-                                                      done_flag, p->lb_slot);
+                                                      done_flag, p->lb_slot, first_flag);
             }
             if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
                     cudaSuccess ||
@@ -1617,7 +1628,7 @@ ra_status batch_solve(ra_batch *b, const ra_solve_opts *o, const double *lambda0
             if (e1 != cudaSuccess) return e1;
         }
         step_kernel<false><<<P, kLpThreads, sizeof(LpShared), s>>>(b->st, b->ev, b->pingpong, b->lag_on, nullptr, b->status, cond,
-                                              0, nullptr, nullptr);
+                                              0, nullptr, nullptr, nullptr);
         batch_any_active_kernel<<<1, 1024, 0, s>>>(b->st, P, cond, use_cond, b->active);
         return cudaGetLastError();
     };
@@ -1780,7 +1791,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
         if (rs != RA_OK) return rs;
         shard_combine_kernel<<<1, 32, 0, s>>>(recv, world, m, st->lam_trial, p->R, p->ev, p->status);
         step_kernel<true><<<1, kLpThreads, kStepSmemStaged, s>>>(st, p->ev, pingpong, lag_on, nullptr, p->status, 0, 0,
-                                                          done_flag, nullptr);
+                                                          done_flag, nullptr, nullptr);
         if ((e = cudaMemcpyAsync(&done_h, done_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return fail(RA_ECUDA, "sharded loop: %s", cudaGetErrorString(e));

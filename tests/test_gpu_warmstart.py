@@ -237,3 +237,30 @@ def test_start_price_choice_follows_oracle(ra, WS, oracle, cap):
         np.testing.assert_allclose(got, lam_w if used else lam_c, rtol=2e-5)
     P.close()
     assert False in seen                            # the fallback was exercised
+
+
+def test_solve_reuses_the_warm_start_pass(ra):
+    """ra_warmstart_prices' pass is also the first evaluation of a solve from
+    the prices it returns: a solve called next with that buffer starts from
+    it, and its result equals a solve from a copy of the same prices (which
+    evaluates them itself) field by field."""
+    from paper_2104_00282_gb300 import warmstart as WSG
+    A, kind, w, param, R = W.hetero_device(120_000, 16, 7, 3, "cuda")
+    P = ra.AllocationProblem(A, kind, w, param, R, job_cap=False)
+    net = WSG.load()
+    timing = ("eval_ms", "step_ms")
+    lam0, used = P.warm_prices(net)
+    assert used
+    reused = {k: v for k, v in P.solve(tol=1e-6, lam0=lam0).items() if k not in timing}
+    lam_r = P.prices.cpu().numpy().copy()
+    plain = {k: v for k, v in P.solve(tol=1e-6, lam0=lam0.clone()).items() if k not in timing}
+    lam_p = P.prices.cpu().numpy().copy()
+    # anything run in between drops the reuse: the solve evaluates again
+    lam0b, _ = P.warm_prices(net)
+    P.eval_dual(lam0b)
+    again = {k: v for k, v in P.solve(tol=1e-6, lam0=lam0b).items() if k not in timing}
+    net.close()
+    P.close()
+    assert reused["status"] == ra.RA_OK
+    assert reused == plain == again
+    assert np.array_equal(lam_r, lam_p)
