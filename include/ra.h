@@ -541,6 +541,28 @@ ra_status ra_warmstart_prices(ra_problem *prob, ra_mlp *net, double *lambda0, in
 ra_status ra_warmstart_used(ra_problem *prob, int32_t *used_warm);
 
 /*
+ * ra_scale_by_demand -- per-job demands (Section 7.1, "Extensions and
+ * variations"): a job may hold several units of a resource while it runs, so
+ * the resource constraint becomes sum_i d_i o x_i <= R, with d_i a positive
+ * scalar per job or a positive m-vector per job (o the elementwise product).
+ * Without the per-job cap this is the plain problem in resource units
+ * y_ij = d_ij x_ij with efficiencies a_ij / d_ij: a_i^T x_i = sum_j
+ * (a_ij / d_ij) y_ij and sum_i y_i <= R.  This call writes
+ *     A_out[i, j] = A[i, j] / d[i]          (per_resource = 0: d has n entries)
+ *     A_out[i, j] = A[i, j] / d[i * m + j]  (per_resource = 1: d is n x m)
+ * (IEEE FP32 division).  Create the problem on A_out with RA_NO_JOB_CAP; its
+ * solution y gives x_ij = y_ij / d_ij and the same prices, dual value and
+ * utility.  (With the per-job cap the cap would become sum_j y_ij / d_ij <= 1,
+ * which this transformation does not express.)
+ *   A, d, A_out  device arrays (A_out may equal A); 16-byte aligned
+ * Enqueued on `stream`.  RA_EINVAL on bad sizes or NULL pointers; a demand
+ * that is not positive gives an infinite or NaN efficiency, which
+ * ra_problem_create with RA_VALIDATE rejects.
+ */
+ra_status ra_scale_by_demand(int64_t n, int32_t m, const float *A, const float *d,
+                             int32_t per_resource, float *A_out, void *stream);
+
+/*
  * ra_set_wait_timeout -- bound of every device-side wait of the library's
  * kernels (a CTA waiting for its bulk copies), in seconds of device time; 2
  * by default, process-wide, read when work is enqueued (or captured).  A

@@ -75,6 +75,18 @@ static ra_status validate(const ra_problem *p)
 
 using ra::fail;
 
+namespace {
+// A_out = A / d row by row (one demand per job) or entry by entry.
+__global__ void scale_by_demand_kernel(long long n, int m, const float *A, const float *d,
+                                       int per_resource, float *A_out)
+{
+    const long long total = n * m;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        A_out[e] = A[e] / (per_resource ? d[e] : d[e / m]);
+}
+}  // namespace
+
 extern "C" {
 
 const char *ra_status_string(ra_status s)
@@ -94,6 +106,21 @@ const char *ra_status_string(ra_status s)
 const char *ra_last_error(void) { return ra::g_err; }
 
 const char *ra_version(void) { return "libra 0.2 sm_103a"; }
+
+
+ra_status ra_scale_by_demand(int64_t n, int32_t m, const float *A, const float *d,
+                             int32_t per_resource, float *A_out, void *stream)
+{
+    if (n < 1 || m < 1 || m > RA_MAX_M) return fail(RA_EINVAL, "n = %lld, m = %d", (long long)n, m);
+    if (!A || !d || !A_out) return fail(RA_EINVAL, "NULL argument");
+    long long blocks = (n * m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    scale_by_demand_kernel<<<static_cast<int>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, m, A, d, per_resource ? 1 : 0, A_out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RA_ECUDA, "demand scaling launch: %s", cudaGetErrorString(e));
+    return RA_OK;
+}
 
 ra_status ra_set_wait_timeout(double seconds)
 {

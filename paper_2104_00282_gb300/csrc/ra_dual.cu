@@ -887,8 +887,12 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
     }
 }
 
-// Batched Eq. e-initialization (once per batch solve): direct loads, one
-// FP64 partial per chunk, per-problem ticket and fixed-order final sum.
+// Batched Eq. e-initialization (once per batch solve): each tile's rows are
+// copied into shared memory with coalesced 16-byte loads (a thread's own row
+// read from global memory would touch a different 128-byte line per lane),
+// then read back per thread in rotated 16-byte chunks as in the streaming
+// kernels; one FP64 partial per chunk, per-problem ticket and fixed-order
+// final sum.
 template <int MT>
 __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, double *lam1,
                                                            const long long *lam_off)
@@ -896,7 +900,7 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
     __shared__ float x0_s[RA_MAX_M];
     __shared__ FF red[kWarps][kPartW];
     __shared__ int is_last;
-    __shared__ float rows[kTile * MT];
+    __shared__ __align__(16) float rows[kTile * MT];   // 16-byte chunks are read and written
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (long long c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
         const int p = B.chunk_prob[c];
@@ -912,16 +916,34 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
         }
         __syncthreads();
         KahanF racc;
+        const bool grouped = (m == MT);
+        constexpr int C = MT / 4;
+        const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
         for (int k = 0; k < B.chunk_ntiles[c]; ++k) {
-            const long long i = static_cast<long long>(B.chunk_tile0[c] + k) * kTile + tid;
+            const long long i0 = static_cast<long long>(B.chunk_tile0[c] + k) * kTile;
+            const long long i = i0 + tid;
             const bool valid = i < P.n;
+            const long long left = P.n - i0;
+            const int cnt = static_cast<int>((left < kTile ? left : kTile) * m);
+            const float *src = P.A + i0 * m;   // 16-byte aligned: i0 is a multiple of 256
+            __syncthreads();   // the previous tile's rows are consumed
+            if ((cnt & 3) == 0) {
+                for (int e = tid; e < (cnt >> 2); e += kTile)
+                    reinterpret_cast<float4 *>(rows)[e] = __ldg(reinterpret_cast<const float4 *>(src) + e);
+            } else {
+                for (int e = tid; e < cnt; e += kTile) rows[e] = __ldg(src + e);
+            }
+            __syncthreads();
+            // slot k of a holds column colof(k, rot) (rotated 16-byte chunks)
             float a[MT];
+            load_row<MT>(a, rows + tid * m, nullptr, i, valid, m, grouped, rot);
+            if (!valid) {
+#pragma unroll
+                for (int k = 0; k < MT; ++k) a[k] = 0.0f;
+            }
             float tc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                a[j] = (valid && j < m) ? __ldg(&P.A[i * m + j]) : 0.0f;
-                tc[j & 3] = fmaf(a[j], x0_s[j], tc[j & 3]);
-            }
+            for (int k = 0; k < MT; ++k) tc[k & 3] = fmaf(a[k], x0_s[colof<MT>(k, rot)], tc[k & 3]);
             const float t = (tc[0] + tc[1]) + (tc[2] + tc[3]);
             float d = 0.0f;
             if (valid) {
@@ -932,9 +954,16 @@ __global__ void __launch_bounds__(kTile) batch_init_kernel(BatchDualArgs B, doub
                 else d = t < pi ? wi : 0.0f;
             }
             float *own = rows + tid * m;
+            if (grouped) {
 #pragma unroll
-            for (int j = 0; j < MT; ++j)
-                if (j < m) own[j] = d * a[j];
+                for (int cc = 0; cc < C; ++cc)
+                    reinterpret_cast<float4 *>(own)[(cc + rot) & (C - 1)] =
+                        make_float4(d * a[4 * cc], d * a[4 * cc + 1], d * a[4 * cc + 2], d * a[4 * cc + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < MT; ++j)
+                    if (j < m) own[j] = d * a[j];
+            }
             __syncwarp();
             warp_colsum<MT, float, KahanF>(rows + warp * 32 * m, m, lane, false, racc);
         }

@@ -117,6 +117,8 @@ def lib():
         L.ra_recover_feasible.restype = i32
         L.ra_eval_dual_static.argtypes = [i64, i32, P, P, P, P, P, P, u32, P, P, P]
         L.ra_eval_dual_static.restype = i32
+        L.ra_scale_by_demand.argtypes = [i64, i32, P, P, i32, P, P]
+        L.ra_scale_by_demand.restype = i32
         L.ra_batch_create.argtypes = [i32, P, P, P, P, P, P, P, u32, P, ctypes.POINTER(P)]
         L.ra_batch_create.restype = i32
         L.ra_batch_create_shaped.argtypes = [i32, P, P, P, P, P, P, P, u32,
@@ -314,6 +316,17 @@ def ra_recover_feasible(h, lam, jk=None, xk=None, X=None, tie_rel=None, max_flex
                                      _ptr(jk, torch.int32), _ptr(xk, torch.float32),
                                      _ptr(X, torch.float32), ctypes.byref(info)))
     return info.as_dict()
+
+
+def ra_scale_by_demand(A, d, A_out=None, stream=None):
+    """A_out = A / d for per-job demands (include/ra.h): d of n entries (one
+    demand per job) or n x m (per resource).  Returns A_out."""
+    n, m = A.shape
+    per_res = 1 if d.dim() == 2 else 0
+    out = torch.empty_like(A) if A_out is None else A_out
+    _check(lib().ra_scale_by_demand(n, m, _ptr(A, torch.float32), _ptr(d, torch.float32, n * m if per_res else n),
+                                    per_res, _ptr(out, torch.float32), _stream(stream)))
+    return out
 
 
 def ra_eval_dual_static(A, kind, w, param, R, lam, g, q, flags=0, stream=None):

@@ -711,3 +711,66 @@ def test_paper_medium_target_priority_statistics(oracle):
     assert (~reach[low]).mean() == pytest.approx(0.10, abs=0.04)
     assert (~reach[~low]).mean() <= 0.01
     assert 0.17 <= st["two_resources"] <= 0.67 + 0.03
+
+
+@pytest.mark.parametrize("per_resource", [False, True], ids=["scalar-demand", "vector-demand"])
+def test_demands_reduce_to_scaled_efficiencies(oracle, per_resource):
+    """Per-job demands (Section 7.1): without the per-job cap, max sum_i
+    u_i(a_i^T x_i) over X >= 0 with sum_i d_i o x_i <= R -- solved directly
+    over X by SLSQP -- equals the plain problem with efficiencies a_ij / d_ij
+    (resource units y = d o x) that the oracle solves, and the oracle's prices
+    satisfy the demand problem's KKT conditions: every used resource of job i
+    is priced at u_i'(t_i) a_ij / d_ij."""
+    rng = np.random.default_rng(31 + int(per_resource))
+    n, m = 12, 3
+    A = rng.uniform(0.3, 1.0, (n, m)).astype(np.float32)
+    kind = (np.arange(n) % 2).astype(np.uint8)
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    par = np.where(kind == 1, rng.uniform(0.3, 0.7, n), 0.0).astype(np.float32)
+    D = (rng.uniform(0.5, 3.0, (n, m)) if per_resource else
+         np.repeat(rng.uniform(0.5, 3.0, (n, 1)), m, axis=1)).astype(np.float32)
+    R = rng.uniform(0.8, 1.6, m)
+    As = (A / D).astype(np.float32)                 # the scaled problem's efficiencies
+    p = W.Problem(As, kind, w, par, R)
+    Af, Df = A.astype(float), D.astype(float)
+
+    def negU(x):
+        X = x.reshape(n, m)
+        return -sum(_u(int(kind[i]), float(w[i]), float(par[i]), float(Af[i] @ X[i])) for i in range(n))
+
+    cons = [{"type": "ineq", "fun": lambda x, j=j: R[j] - (Df[:, j] * x.reshape(n, m)[:, j]).sum()}
+            for j in range(m)]
+    best = -np.inf
+    for _ in range(12):
+        res = minimize(negU, rng.uniform(0.05, 0.3, n * m), method="SLSQP",
+                       bounds=[(1e-9, None)] * (n * m), constraints=cons,
+                       options=dict(ftol=1e-15, maxiter=5000))
+        if np.isfinite(res.fun) and min(c["fun"](res.x) for c in cons) > -1e-9:
+            best = max(best, -res.fun)
+    assert np.isfinite(best)
+    sol = oracle.solve(p, cap=False, tol=1e-9, max_evals=2000)
+    scale = max(1.0, abs(best))
+    # the scaled problem's g bounds the demand problem's optimum from above
+    # (weak duality), its feasible allocation from below ...
+    assert sol.g >= best - 1e-9 * scale
+    assert sol.U_lb <= best + 1e-6 * scale     # SLSQP's own accuracy
+    # ... and min g, refined by a derivative-free search (g has kinks where
+    # jobs tie between resources), equals the demand problem's optimum
+    gfun = lambda lam: oracle.dual(p, np.abs(lam), cap=False)[0]
+    x, g_min = sol.lam, sol.g
+    for _ in range(4):
+        res = minimize(gfun, x, method="Nelder-Mead",
+                       options=dict(xatol=1e-12, fatol=1e-14, maxiter=20000, maxfev=20000))
+        if res.fun < g_min:
+            g_min, x = res.fun, np.abs(res.x)
+    assert abs(g_min - best) <= 2e-6 * scale, (g_min, best)
+    # KKT in the demand problem's units: at the oracle's allocation y (x = y / d)
+    # a used resource j of job i has lam_j d_ij = u_i'(t_i) a_ij
+    Y, _ = oracle.allocation(p, sol.lam, cap=False)
+    X = Y / Df
+    for i in range(n):
+        t = float(Af[i] @ X[i])
+        du = float(w[i]) / t if kind[i] == 0 else float(w[i]) * float(par[i]) * t ** (float(par[i]) - 1)
+        for j in range(m):
+            if X[i, j] > 1e-9:
+                assert sol.lam[j] * Df[i, j] == pytest.approx(du * Af[i, j], rel=1e-5)
