@@ -833,9 +833,7 @@ ra_status ra_warmstart_prices(ra_problem *p, ra_mlp *net, double *lambda0, int32
     e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaEventRecord(p->fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
-    if (e == cudaSuccess) e = ra::launch_features(nullptr, feat_of(p), 1, p->m, stats, feats, p->side);
-    if (e == cudaSuccess) e = ra::mlp_forward(net, feats, p->m, y, p->side);
-    if (e == cudaSuccess) e = ra::launch_exp_prices(p->m, y, lam_w, p->side);
+    if (e == cudaSuccess) e = ra::launch_warm_network(feat_of(p), p->m, stats, net, feats, y, lam_w, p->side);
     if (e == cudaSuccess) e = cudaEventRecord(p->join, p->side);
     if (e == cudaSuccess) e = ra::launch_init(p, lam_c, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join, 0);

@@ -331,6 +331,9 @@ cudaError_t mlp_forward(ra_mlp *net, const float *X, int rows, float *y_out, cud
 cudaError_t mlp_train_step(ra_mlp *net, const float *X, const float *target, int rows, float lr,
                            float *loss, cudaStream_t s);
 cudaError_t launch_exp_prices(int m, const float *y, double *lam, cudaStream_t s);
+// one problem's statistics, network input, network and start prices (two launches)
+cudaError_t launch_warm_network(const FeatProblem &one, int m, float *stats, const ra_mlp *net,
+                                float *feats, float *y, double *lam, cudaStream_t s);
 cudaError_t launch_choose(int m, const double *lam_w, const double *lam_c, const double *g2,
                           double *lam0, int32_t *used, cudaStream_t s);
 

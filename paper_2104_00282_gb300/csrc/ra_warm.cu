@@ -49,15 +49,18 @@ __device__ __forceinline__ float fkey_inv(unsigned k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Statistics of resource blockIdx.x < m of problem blockIdx.y: the 8 quantiles of
-// A[:, j] over the sample (order statistics of rank floor((2l+1) S / 16),
-// selected exactly by a radix select over the float's order-preserving key,
-// 8 bits a pass, all 8 ranks at once: integer bin counts, so the selection
-// does not depend on thread timing) and log(R_j / n); CTA m of the problem
-// adds the fractions of log, power and linear utilities and the mean of log w
-// over the sample to every resource's row.
+// Statistics of problem blockIdx.y: the 8 quantiles of A[:, j] over the
+// sample (order statistics of rank floor((2l+1) S / 16), selected exactly by
+// a radix select over the float's order-preserving key, 8 bits a pass:
+// integer bin counts, so the selection does not depend on thread timing) and
+// log(R_j / n) of every resource j, and the fractions of log, power and linear
+// utilities and the mean of log w over the sample (every resource's row).
+// Work split: with nq = kQuant a CTA selects all 8 quantiles of resource
+// blockIdx.x (CTA m: the shared statistics); with nq = 1 (a single problem,
+// whose 8 selections would otherwise run on m SMs only) CTA 8 j + l selects
+// quantile l of resource j and CTA 8 m the shared statistics.
 __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, FeatProblem one,
-                                                     float *stats)
+                                                     float *stats, int nq)
 {
     extern __shared__ unsigned key[];   // kSampleMax keys
     __shared__ double red[32][3];
@@ -65,8 +68,10 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
     __shared__ unsigned pref[kQuant];   // key bits fixed so far
     __shared__ unsigned rank[kQuant];   // rank within the keys matching pref
     const FeatProblem P = probs ? probs[blockIdx.y] : one;
-    const int j = blockIdx.x;
-    if (j > P.m) return;
+    const int per = kQuant / nq;        // CTAs per resource
+    const int j = blockIdx.x / per;
+    const int l0 = (blockIdx.x % per) * nq;   // first quantile of this CTA
+    if (j > P.m || (j == P.m && l0 != 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = P.n;
     const int S = n < kSampleMax ? static_cast<int>(n) : kSampleMax;
@@ -129,9 +134,9 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
         }
         for (; k < S; k += blockDim.x) key[k] = fkey(P.A[sample_row(k, n, S) * P.m + j]);
     }
-    if (tid < kQuant) {
+    if (tid < nq) {
         pref[tid] = 0u;
-        rank[tid] = static_cast<unsigned>(((2 * tid + 1) * S) / 16);
+        rank[tid] = static_cast<unsigned>(((2 * (l0 + tid) + 1) * S) / 16);
     }
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
@@ -149,13 +154,12 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
                 const unsigned grp = __match_any_sync(0xffffffffu, in ? bin : 0xffffffffu);
                 if (in && (__ffs(grp) - 1) == lane) atomicAdd(&hist[0][bin], __popc(grp));
             } else {   // few keys still match a rank's prefix: plain atomics
-#pragma unroll
-                for (int l = 0; l < kQuant; ++l)
+                for (int l = 0; l < nq; ++l)
                     if (in && ((kv ^ pref[l]) >> (shift + 8)) == 0u) atomicAdd(&hist[l][bin], 1u);
             }
         }
         __syncthreads();
-        if (warp < kQuant) {   // warp l finds the bin holding its rank
+        if (warp < nq) {   // warp l finds the bin holding its rank
             const unsigned *h = hist[pass == 0 ? 0 : warp];
             unsigned c[8], tot = 0u;
 #pragma unroll
@@ -185,8 +189,9 @@ __global__ void __launch_bounds__(1024) stats_kernel(const FeatProblem *probs, F
         __syncthreads();
     }
     float *out = stats + (P.row0 + j) * kFeatRes;
-    if (tid < kQuant) out[tid] = logf(fmaxf(fkey_inv(pref[tid]), 1e-30f));
-    if (tid == kQuant) out[8] = static_cast<float>(log(fmax(P.R[j] / static_cast<double>(n), 1e-30)));
+    if (tid < nq) out[l0 + tid] = logf(fmaxf(fkey_inv(pref[tid]), 1e-30f));
+    if (tid == kQuant && l0 == 0)
+        out[8] = static_cast<float>(log(fmax(P.R[j] / static_cast<double>(n), 1e-30)));
 }
 
 // Network input of every resource of problem blockIdx.x: its statistics,
@@ -322,16 +327,14 @@ __global__ void __launch_bounds__(256)
 // the training path.  The result differs from the training path's forward
 // only by that summation order (a few FP32 ulps).
 constexpr int kInferSplit = 4;
-__global__ void __launch_bounds__(kHid * kInferSplit) infer_rows_kernel(const float *X, const float *theta, float *y)
+
+// The network on one input row xr (shared memory, kFeatIn floats), all
+// kHid * kInferSplit threads of the CTA taking part; thread 0 gets y.
+__device__ __forceinline__ float mlp_row(const float *xr, const float *theta, float *h1, float *h2,
+                                         float (*part)[kHid])
 {
-    __shared__ float xr[kFeatIn];
-    __shared__ float h1[kHid];
-    __shared__ float h2[kHid];
-    __shared__ float part[kInferSplit][kHid];
-    const int r = blockIdx.x, t = threadIdx.x;
+    const int t = threadIdx.x;
     const int c = t % kHid, g = t / kHid;
-    if (t < kFeatIn) xr[t] = X[static_cast<long long>(r) * kFeatIn + t];
-    __syncthreads();
     if (g == 0) {
         float acc = 0.0f;
 #pragma unroll
@@ -352,13 +355,56 @@ __global__ void __launch_bounds__(kHid * kInferSplit) infer_rows_kernel(const fl
         h2[c] = gelu(z + theta[ob2 + c]);
     }
     __syncthreads();
+    float s2 = 0.0f;
     if (t < 32) {
-        float s2 = 0.0f;
 #pragma unroll
         for (int k = 0; k < kHid / 32; ++k) s2 = fmaf(h2[t + 32 * k], theta[oW3 + t + 32 * k], s2);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-        if (t == 0) y[r] = s2 + theta[ob3];
+    }
+    return s2 + theta[ob3];
+}
+
+__global__ void __launch_bounds__(kHid * kInferSplit) infer_rows_kernel(const float *X, const float *theta, float *y)
+{
+    __shared__ float xr[kFeatIn];
+    __shared__ float h1[kHid];
+    __shared__ float h2[kHid];
+    __shared__ float part[kInferSplit][kHid];
+    const int r = blockIdx.x, t = threadIdx.x;
+    if (t < kFeatIn) xr[t] = X[static_cast<long long>(r) * kFeatIn + t];
+    __syncthreads();
+    const float v = mlp_row(xr, theta, h1, h2, part);
+    if (t == 0) y[r] = v;
+}
+
+// The warm start's whole network step for one problem's m resources, CTA r
+// for resource r: its input row (its 13 statistics, then their mean over the
+// resources, summed in FP64 in resource order as features_kernel does), the
+// network, and the start price max(exp(y) - RA_MLP_PRICE_OFFSET, 0) -- the
+// work of features_kernel, infer_rows_kernel and exp_prices_kernel in one
+// launch.
+__global__ void __launch_bounds__(kHid * kInferSplit)
+    warm_infer_kernel(const float *stats, int m, const float *theta, float *feats, float *y,
+                      double *lam)
+{
+    __shared__ float xr[kFeatIn];
+    __shared__ float h1[kHid];
+    __shared__ float h2[kHid];
+    __shared__ float part[kInferSplit][kHid];
+    const int r = blockIdx.x, t = threadIdx.x;
+    if (t < kFeatRes) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += stats[j * kFeatRes + t];
+        xr[kFeatRes + t] = static_cast<float>(s / m);
+        xr[t] = stats[r * kFeatRes + t];
+    }
+    __syncthreads();
+    if (t < kFeatIn) feats[r * kFeatIn + t] = xr[t];
+    const float v = mlp_row(xr, theta, h1, h2, part);
+    if (t == 0) {
+        y[r] = v;
+        lam[r] = fmax(exp(static_cast<double>(v)) - RA_MLP_PRICE_OFFSET, 0.0);
     }
 }
 
@@ -489,7 +535,9 @@ cudaError_t launch_features(const FeatProblem *probs, const FeatProblem &one, in
     cudaError_t e = cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSampleMax * 4);
     if (e != cudaSuccess) return e;
-    stats_kernel<<<dim3(m_max + 1, P), 1024, kSampleMax * 4, s>>>(probs, one, stats);
+    // one problem: a CTA per resource and quantile (8 m + 1 CTAs instead of m + 1)
+    const int nq = P == 1 ? 1 : kQuant;
+    stats_kernel<<<dim3((m_max + 1) * (kQuant / nq), P), 1024, kSampleMax * 4, s>>>(probs, one, stats, nq);
     features_kernel<<<P, 256, 0, s>>>(probs, one, stats, feats);
     return cudaGetLastError();
 }
@@ -580,6 +628,18 @@ cudaError_t mlp_train_step(ra_mlp *net, const float *X, const float *target, int
     adam_kernel<<<(RA_MLP_PARAMS + 255) / 256, 256, 0, s>>>(RA_MLP_PARAMS, net->theta, g, net->m1,
                                                             net->m2, lr, static_cast<float>(c1),
                                                             static_cast<float>(c2));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_network(const FeatProblem &one, int m, float *stats, const ra_mlp *net,
+                                float *feats, float *y, double *lam, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSampleMax * 4);
+    if (e != cudaSuccess) return e;
+    stats_kernel<<<dim3((m + 1) * kQuant, 1), 1024, kSampleMax * 4, s>>>(nullptr, one, stats, 1);
+    warm_infer_kernel<<<m, kHid * kInferSplit, 0, s>>>(stats + static_cast<long long>(one.row0) * kFeatRes,
+                                                       m, net->theta, feats, y, lam);
     return cudaGetLastError();
 }
 
