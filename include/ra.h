@@ -148,7 +148,9 @@ typedef struct {
     int32_t repair_window;/* > 0: when the gap has not halved in this many evaluations, leave the
                              device loop, re-mix the jobs at ties at the best prices (as
                              ra_recover_feasible) and resume; also tried once at max_evals.
-                             0 = off.  Default 16                                               */
+                             0 = off.  -1 (default) = automatic: 4 when the problem has fewer
+                             than 4096 jobs per resource (ties stall its column-scaled bound
+                             early), else 16                                                    */
     double init_step;     /* length of the first price step (and of a restarted gradient step)
                              as a fraction of |lambda|; default 0.05, smaller from a close start */
     int32_t init_scale;   /* without the per-job cap and lambda0: 1 (default) scales the prices

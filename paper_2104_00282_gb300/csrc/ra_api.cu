@@ -140,7 +140,7 @@ void ra_solve_opts_default(ra_solve_opts *o)
     o->use_graph = 1;
     o->lam_floor = -1.0;
     o->master_lb = 1;
-    o->repair_window = 16;
+    o->repair_window = -1;
     o->init_scale = 1;
     o->pad_ = 0;
     o->init_step = 0.05;

@@ -1239,7 +1239,8 @@ void release_loop_graph(ra_problem *p)
 
 namespace {
 
-constexpr int kMaxRepairs = 5;   // lower-bound repairs per solve (the last at max_evals)
+constexpr int kMaxRepairs = 12;  // lower-bound repairs per solve (the last at max_evals)
+constexpr int kMaxRepairWindow = 64;
 
 double stop_tolerance(double tol, uint32_t flags)
 {
@@ -1296,6 +1297,13 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     if (!(opts.tol_rel >= 0.0)) return fail(RA_EINVAL, "tol_rel must be >= 0");
     if (!(opts.init_step > 0.0)) return fail(RA_EINVAL, "init_step must be > 0");
     if (!lambda_out) return fail(RA_EINVAL, "lambda_out is NULL");
+    if (opts.repair_window < -1) return fail(RA_EINVAL, "repair_window must be >= -1");
+    // automatic window: few jobs per resource leave the column-scaled bound
+    // stalled at ties early, so repair after 4 evaluations without the gap
+    // halving; otherwise after 16
+    const int repair_window = opts.repair_window >= 0
+                                  ? opts.repair_window
+                                  : (p->n < 4096LL * p->m ? 4 : 16);
     cudaStream_t s = p->stream;
     cudaError_t e;
     SolverState *st = p->st;
@@ -1327,7 +1335,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                                          stop_tolerance(opts.tol_rel, p->flags), opts.max_evals,
                                          opts.lbfgs_mem, opts.update, opts.lam_floor, cap,
                                          opts.master_lb, opts.init_step, pingpong, lag_on,
-                                         opts.repair_window);
+                                         repair_window);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
@@ -1503,7 +1511,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         copied = true;
         // the lower bound stalled (or the evaluations ran out): re-mix the jobs
         // at ties at the best prices (ra_repair.cu), then stop or resume
-        const bool want = opts.repair_window > 0 && repairs < kMaxRepairs &&
+        const bool want = repair_window > 0 && repairs < kMaxRepairs &&
                           (h.status == kStatusStalled || h.status == RA_ENOTCONV);
         if (!want) break;
         ra_repair_opts ro;
@@ -1515,7 +1523,11 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         n_flex = ri.n_flex;
         // while the prices are still moving a repair may fall short: exit again
         // after twice as many evaluations without the gap halving
-        const int next = repairs + 1 < kMaxRepairs ? opts.repair_window << repairs : 0;
+        int next = 0;
+        if (repairs + 1 < kMaxRepairs) {
+            next = repair_window << (repairs < 5 ? repairs : 5);
+            if (next > kMaxRepairWindow) next = kMaxRepairWindow;
+        }
         if ((e = launch_dual_exact(p, st->lam_best, p->ev + 1, s)) != cudaSuccess)
             return fail(RA_ECUDA, "exact evaluation: %s", cudaGetErrorString(e));
         repair_accept_kernel<<<1, 32, 0, s>>>(st, ri.U, p->ev + 1, opts.tol_rel, lag_on, rec_on, next);
