@@ -511,7 +511,9 @@ ra_status ra_batch_create_shaped(int32_t P, const int64_t *n, const int32_t *m, 
         if (!ra::aligned16(A[p]) || !ra::aligned16(kind[p]) || !ra::aligned16(w[p]) ||
             !ra::aligned16(param[p]))
             return fail(RA_EINVAL, "problem %d: A, kind, w and param must be 16-byte aligned", p);
-        total += n[p];
+        // each problem's slice of the record pools starts at a multiple of 8
+        // jobs, so its records can be bulk-copied (16-byte aligned) with its tiles
+        total += (n[p] + 7) & ~7LL;
         m_total += m[p];
     }
     ra_batch *b = new (std::nothrow) ra_batch();
@@ -610,7 +612,7 @@ ra_status ra_batch_create_shaped(int32_t P, const int64_t *n, const int32_t *m, 
             probs[p].lbt[k] = b->lbt_pool[k] + job_off;
             probs[p].lbj[k] = b->lbj_pool[k] + job_off;
         }
-        job_off += n[p];
+        job_off += (n[p] + 7) & ~7LL;   // as in `total`
     }
     for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
         if (!b->nchunks[c]) continue;

@@ -74,6 +74,9 @@ struct StageLayout {
 constexpr size_t kRecBytes = kTile * (sizeof(float2) + sizeof(uchar2));
 constexpr int kRingSmemMax = 112 * 1024;  // dynamic allowance of the single-problem streaming kernels
 __host__ __device__ inline size_t ring_stage_bytes(int m) { return StageLayout<4>::bytes(m) + kRecBytes; }
+// A stage of the batched pass: a tile of the width class (rows of mt columns)
+// and room for its records.
+__host__ __device__ inline size_t batch_stage_bytes(int mt) { return StageLayout<4>::bytes(mt) + kRecBytes; }
 
 // The block stage's rows of the single-problem streaming kernels live in the
 // tile ring, idle by then (one row of kPartW per warp).
@@ -704,13 +707,23 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
         const size_t a_bytes = static_cast<size_t>(kTile) * m * 4;
         const size_t st_bytes = a_bytes + kTile * 9;
         const int st = static_cast<int>(issued % stages);
-        unsigned char *base = smem + st * StageLayout<MT>::bytes(MT);
-        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes));
+        unsigned char *base = smem + st * batch_stage_bytes(MT);
+        // the previous evaluation's records of the tile come with it when the
+        // problem's lagged bound is on (the same flag the consumers read)
+        const int pq = B.chunk_prob[prod.c];
+        const bool recs = B.lag_on[pq] != 0;
+        const int ppq = B.pingpong[pq] & 1;
+        mbar_arrive_expect_tx(&bars[st], static_cast<uint32_t>(st_bytes + (recs ? kRecBytes : 0)));
         const uint64_t pol = policy_evict_first();
         bulk_load_stream(base, P.A + j0 * m, static_cast<uint32_t>(a_bytes), &bars[st], pol);
         bulk_load_stream(base + a_bytes, P.w + j0, kTile * 4, &bars[st], pol);
         bulk_load_stream(base + a_bytes + kTile * 4, P.param + j0, kTile * 4, &bars[st], pol);
         bulk_load_stream(base + a_bytes + kTile * 8, P.kind + j0, kTile, &bars[st], pol);
+        if (recs) {
+            unsigned char *rb = base + StageLayout<MT>::bytes(MT);
+            bulk_load(rb, P.lbt[ppq] + j0, kTile * sizeof(float2), &bars[st]);
+            bulk_load(rb + kTile * sizeof(float2), P.lbj[ppq] + j0, kTile * sizeof(uchar2), &bars[st]);
+        }
         ++issued;
         cursor_next(B, prod);
     };
@@ -754,6 +767,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
         int kind = RA_U_LINCAP;
         float w = 1.0f, pr = 0.0f;
         int st = 0;
+        const unsigned char *rec_s = nullptr;   // the tile's staged records (full tiles, lag on)
         if (full) {
             st = static_cast<int>(consumed % stages);
             const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>((consumed / stages) & 1),
@@ -770,7 +784,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
                 __syncthreads();
                 return;
             }
-            unsigned char *base = smem + st * StageLayout<MT>::bytes(MT);
+            unsigned char *base = smem + st * batch_stage_bytes(MT);
             const size_t a_bytes = static_cast<size_t>(kTile) * m * 4;
             float *a_s = reinterpret_cast<float *>(base);
             row = a_s + tid * m;
@@ -778,6 +792,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
             kind = base[a_bytes + kTile * 8 + tid];
             w = reinterpret_cast<const float *>(base + a_bytes)[tid];
             pr = reinterpret_cast<const float *>(base + a_bytes + kTile * 4)[tid];
+            if (lag) rec_s = base + StageLayout<MT>::bytes(MT);
         } else {
             // ragged last tile of a problem: direct loads (every stage of the
             // ring may hold a copy in flight, so no shared scratch is used)
@@ -791,8 +806,13 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3) batch_dual_kernel(BatchDua
         float2 tp = make_float2(0.f, 0.f);
         uchar2 jp = make_uchar2(255, 255);
         if (lag && valid) {
-            tp = lbt_prev[i];
-            jp = lbj_prev[i];
+            if (rec_s != nullptr) {
+                tp = reinterpret_cast<const float2 *>(rec_s)[tid];
+                jp = reinterpret_cast<const uchar2 *>(rec_s + kTile * sizeof(float2))[tid];
+            } else {
+                tp = lbt_prev[i];
+                jp = lbj_prev[i];
+            }
         }
         JobSol<float> sol;
         sol.cP = sol.cQ = -1;
@@ -1366,15 +1386,6 @@ __global__ void records_kernel(const Rec *lbt, const uchar2 *lbj, long long n, i
 
 // Ring stages for a shared-memory budget per CTA: 106 KB lets two CTAs share
 // an SM (the capped kernels, 128 registers), 70 KB three (the uncapped ones).
-template <int MT>
-int mt_stages(int m, size_t budget = 106 * 1024)
-{
-    const size_t sb = StageLayout<MT>::bytes(m);
-    int s = static_cast<int>(budget / sb);
-    if (s > kMaxStages) s = kMaxStages;
-    if (s < 2) s = 2;
-    return s;
-}
 
 template <int MT, bool CAP, bool LAG, bool REC>
 cudaError_t launch_tma(const ra_problem *p, const DualParams &dp_in, cudaStream_t s)
@@ -1733,15 +1744,13 @@ cudaError_t launch_recover(const ra_problem *p, const double *lam, int32_t *jsta
 int batch_stages(int mt, int cap)
 {
     const size_t budget = cap ? 106 * 1024 : 70 * 1024;   // two / three CTAs per SM
-    switch (mt) {
-    case 4: return mt_stages<4>(4, budget);
-    case 8: return mt_stages<8>(8, budget);
-    case 16: return mt_stages<16>(16, budget);
-    default: return mt_stages<32>(32, budget);
-    }
+    int s = static_cast<int>(budget / batch_stage_bytes(mt));
+    if (s > kMaxStages) s = kMaxStages;
+    if (s < 2) s = 2;
+    return s;
 }
 
-size_t batch_smem(int mt, int cap) { return batch_stages(mt, cap) * StageLayout<4>::bytes(mt) + 128; }
+size_t batch_smem(int mt, int cap) { return batch_stages(mt, cap) * batch_stage_bytes(mt) + 128; }
 
 cudaError_t batch_configure(int mt, int cap, int *blocks_per_sm)
 {
