@@ -144,8 +144,10 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
     """Cold and warm ra_solve of P held-out problems; per problem the device
     time (CUDA events on the solve's stream, the warm one including the
     statistics, the network and both start-point evaluations) and the
-    evaluation count.  The order of the two solves alternates, so neither
-    always finds the problem's data in L2."""
+    evaluation count.  The cold start is the paper's Eq. e-initialization;
+    the library's default (those prices scaled by the minimiser of g along
+    their ray) is solved too, for comparison.  The order of the cold and warm
+    solves alternates, so neither always finds the problem's data in L2."""
     torch = _torch()
     from . import ra
     from . import workloads as W
@@ -169,6 +171,9 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
         def cold():   # the paper's Eq. e-initialization, unscaled
             return prob.solve(tol=tol, max_evals=max_evals, init_scale=False)
 
+        def cold_scaled():   # the library's default cold start: Eq. e-initialization
+            return prob.solve(tol=tol, max_evals=max_evals)   # scaled along its ray
+
         def warm():   # nothing waits for the start-price choice
             lam0, _ = prob.warm_prices(net, sync=False)
             return prob.solve(tol=tol, max_evals=max_evals, lam0=lam0, init_step=WARM_INIT_STEP)
@@ -180,10 +185,12 @@ def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500
             wi, wt = timed(warm)
             ci, ct = timed(cold)
         used = prob.warm_used()
+        si, sct = timed(cold_scaled)
         rec.append({"n": int(sizes[i]), "cold_ms": ct, "warm_ms": wt, "cold_evals": ci["evals"],
                     "warm_evals": wi["evals"], "cold_status": ci["status"],
                     "warm_status": wi["status"], "cold_gap": ci["rel_gap"], "warm_gap": wi["rel_gap"],
-                    "used_warm": bool(used)})
+                    "used_warm": bool(used), "cold_scaled_ms": sct, "cold_scaled_evals": si["evals"],
+                    "cold_scaled_status": si["status"]})
         prob.close()
         if log and (i + 1) % 100 == 0:
             log(f"evaluated {i + 1}/{P}")
@@ -203,6 +210,13 @@ def summarize(rec):
     }
     out["speedup_median_time"] = out["cold"]["median_ms"] / out["warm"]["median_ms"]
     out["speedup_median_evals"] = out["cold"]["median_evals"] / out["warm"]["median_evals"]
+    if rec and "cold_scaled_ms" in rec[0]:
+        # the library's default cold start (Eq. e-initialization scaled by the
+        # minimiser of g along its ray, one more pass) for comparison
+        out["cold_scaled"] = {"median_ms": med("cold_scaled_ms", rec),
+                              "median_evals": med("cold_scaled_evals", rec),
+                              "converged": sum(r["cold_scaled_status"] == 0 for r in rec)}
+        out["speedup_vs_scaled_cold_time"] = out["cold_scaled"]["median_ms"] / out["warm"]["median_ms"]
     if both:
         out["both_converged"] = {
             "problems": len(both),
