@@ -228,6 +228,45 @@ def lower_bound(prob, lam, cap=True, method="hull", nthreads=0, r=None, r_lin=No
     return scaled_utility(prob, lam, s, cap, method, nthreads, s_lin=s_lin), (s, s_lin)
 
 
+def own_lower_bound(prob, lam, nthreads=0):
+    """Lower bound on the column-scaled utility U(X~) at lam without the
+    per-job cap (``lower_bound`` with cap=False), formed from the evaluation's
+    sums alone.  Without the cap job i uses one resource j, and at its
+    subproblem optimum t_i u_i'(t_i) = (lam_j / A_ij) t_i = lam_j x_ij
+    (Section 4.1).  Scaling t_i by s (ln s = l):
+
+    * log:            w ln(s t) = w ln t + l (t u'(t))                 (exact)
+    * power, p > 0:   s^p u(t) >= (1 + p l) u(t) = u(t) + l (t u'(t))   (e^y >= 1 + y, u >= 0)
+    * power, p < 0:   s^p u(t) >= u(t) + l (t u'(t)) - (p l)^2 / 2 e^(|p l|) |u(t)|
+                      (Taylor remainder of e^(p l); u < 0, |p| <= 64)
+    * linear kinds:   kept whole or scaled up, which lowers no u.
+
+    Summed over column j the first-order terms give lam_j (r_j - r_lin_j) l_j,
+    so the bound is U(X) + sum_j lam_j (r_j - r_lin_j) ln s_j - L^2/2 e^(64 L)
+    sum_{p_i<0} p_i^2 |u_i(t_i)|, L = max_j |ln s_j| over the scaled columns.
+    A column that scales its linear-utility jobs down (s_lin < 1) admits no
+    such bound: -inf.  Returns (bound, (s, s_lin))."""
+    _, kind, w, par, R = _arrays(prob)
+    lam = np.asarray(lam, np.float64)
+    _, r, U, r_lin = dual(prob, lam, cap=False, nthreads=nthreads, split=True)
+    s, s_lin = column_scales(R, r, r_lin, cap=False)
+    if np.any((s_lin < 1.0) & (r_lin > 0.0)):
+        return -np.inf, (s, s_lin)
+    r_oth = r - r_lin
+    scaled = (r_oth > 0.0) & (s != 1.0)
+    ls = np.where(scaled, np.log(np.where(scaled, s, 1.0)), 0.0)
+    L = float(np.max(np.abs(ls))) if prob.m else 0.0
+    bound = U + float(np.sum(lam * r_oth * ls))
+    neg = (kind == 1) & (par < 0)
+    if np.any(neg):
+        t = jobs(prob, lam, idx=np.flatnonzero(neg), cap=False, nthreads=nthreads)[:, 0]
+        wn, pn = w[neg].astype(np.float64), par[neg].astype(np.float64)
+        s2 = float(np.sum(pn * pn * np.abs(-wn * np.power(t, pn))))
+        if s2 > 0.0:
+            bound -= 0.5 * L * L * np.exp(64.0 * L) * s2
+    return bound, (s, s_lin)
+
+
 def init_prices(prob, cap=True, nthreads=0):
     """lam^1 of Eq. e-initialization."""
     A, kind, w, par, R = _arrays(prob)

@@ -461,6 +461,75 @@ def test_uncapped_scaling_spares_saturated_linear_jobs(oracle):
     assert (g - lb) < 0.5 * (g - uniform)                       # tighter near the optimum
 
 
+def _prices_around(oracle, p, spread, k, seed):
+    lam0 = oracle.init_prices(p, cap=False)
+    rng = np.random.default_rng(seed)
+    return [lam0 * np.exp(spread * rng.standard_normal(p.m)) for _ in range(k)]
+
+
+def test_own_bound_is_exact_for_log_utilities(oracle):
+    # w log(s t) = w log t + w log s and w = t u'(t) = lambda_j x_ij at the
+    # subproblem optimum: for log utilities the bound formed from the sums
+    # (U(X), r, r_lin) equals the column-scaled utility itself
+    p = W.random_small(3000, 5, seed=4, kinds=(0,))
+    for lam in _prices_around(oracle, p, 0.3, 4, 5):
+        exact, _ = oracle.lower_bound(p, lam, cap=False)
+        own, _ = oracle.own_lower_bound(p, lam)
+        assert own == pytest.approx(exact, rel=1e-11, abs=1e-9)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.random_small(4000, 6, seed=3, kinds=(0, 1, 2, 3)),
+    lambda: W.alpha_fair(n=4000, m=6, seed=2),
+    lambda: W.config_large(n=20_000, m=8, seed=1),
+], ids=["mixed", "alpha-fair", "large"])
+def test_own_bound_never_exceeds_scaled_utility(oracle, make):
+    # a valid lower bound on the utility of the same column-scaled allocation
+    # (and so on U*), far from and near the optimum
+    p = make()
+    lams = _prices_around(oracle, p, 0.3, 3, 5) + _prices_around(oracle, p, 0.02, 3, 6)
+    sol = oracle.solve(p, cap=False, tol=1e-9, max_evals=3000)
+    lams.append(sol.lam)
+    for lam in lams:
+        exact, _ = oracle.lower_bound(p, lam, cap=False)
+        own, _ = oracle.own_lower_bound(p, lam)
+        assert own <= exact + 1e-10 * abs(exact)
+    # near the optimum it closes the gap as the exact bound does (its extra
+    # slack is second order in ln s, like the gap itself)
+    g, _, _ = oracle.dual(p, sol.lam, cap=False)
+    exact, _ = oracle.lower_bound(p, sol.lam, cap=False)
+    own, _ = oracle.own_lower_bound(p, sol.lam)
+    assert oracle.rel_gap(g, own) <= max(10 * oracle.rel_gap(g, exact), 1e-7)
+
+
+def test_own_bound_needs_the_remainder_for_negative_powers(oracle):
+    # for -w t^p, p < 0, s^p u(t) lies below the first-order term (e^y >= 1 + y
+    # with u < 0): without the Taylor remainder the bound would exceed the
+    # utility of the allocation it describes
+    p = W.alpha_fair(n=4000, m=6, seed=2)
+    over = 0
+    for lam in _prices_around(oracle, p, 0.3, 4, 5):
+        _, r, U, r_lin = oracle.dual(p, lam, cap=False, split=True)
+        exact, (s, _) = oracle.lower_bound(p, lam, cap=False)
+        ro = r - r_lin
+        ls = np.where((ro > 0) & (s != 1), np.log(np.where(s > 0, s, 1.0)), 0.0)
+        over += U + np.sum(lam * ro * ls) > exact
+        own, _ = oracle.own_lower_bound(p, lam)
+        assert own <= exact
+    assert over > 0
+
+
+def test_own_bound_rejects_linear_jobs_scaled_down(oracle):
+    # a column whose linear-utility jobs alone exceed R_j scales them down,
+    # which the sums cannot bound: -inf
+    p = W.random_small(2000, 3, seed=7, kinds=(2,), r_scale=0.1)
+    lam = np.full(p.m, 1e-6)          # every linear job takes its target
+    _, r, _, r_lin = oracle.dual(p, lam, cap=False, split=True)
+    assert np.all(r_lin > p.R)
+    own, (s, s_lin) = oracle.own_lower_bound(p, lam)
+    assert own == -np.inf and np.all(s_lin < 1)
+
+
 def test_subgradient_matches_finite_differences(oracle):
     p = W.random_small(4000, 4, seed=9, kinds=(0, 1))
     lam = np.array([0.7, 1.1, 0.9, 1.6])
