@@ -185,9 +185,15 @@ void ra_solve_opts_default(ra_solve_opts *opts);
  * Eq. e-initialization when lambda0 is NULL) repeat {dual evaluation,
  * column-scaled lower bound, gap test, price update} on the device until the
  * relative duality gap is <= tol_rel or max_evals is reached.  The loop runs
- * without host round trips.  The lower bound of an evaluation is formed in
- * the following evaluation's pass from a 10-byte-per-job record, so it costs
- * no second read of A.
+ * without host round trips.  With the per-job cap the lower bound of an
+ * evaluation is formed from a 10-byte-per-job record in a pass beside the
+ * next price update, so it costs no second read of A.  Without the cap it is
+ * formed from the evaluation's own sums as soon as the evaluation ends:
+ * U(X) + sum_j lambda_j (r_j - r_lin_j) ln s_j (t u'(t) = lambda_j x_ij at
+ * each job's optimum), less a Taylor remainder for powers p < 0 -- a lower
+ * bound on the utility of the column-scaled allocation that ra_eval_dual's
+ * U_lb describes; where a column would scale its linear-utility jobs down,
+ * the records and that pass serve instead.
  *   opts        host, may be NULL for defaults
  *   lambda0     m FP64 start prices or NULL
  *   lambda_out  m FP64 output: prices with the best dual value
@@ -265,9 +271,11 @@ ra_status ra_recover_primal(ra_problem *prob, const double *lambda, int32_t *jst
  *            (resource, time fraction) pairs, resource -1 = unused slot;
  *            RA_EINVAL if a re-mixed job uses more than four (then use X)
  *   X_dense  n*m FP32 output or NULL
- *   info     host output (required): the utility U of the returned allocation
- *            (a lower bound on the optimum), its worst usage_j / R_j, the jobs
- *            re-mixed and the LP's outcome
+ *   info     host output (required): the utility U of the allocation, taken
+ *            in FP64 before the outputs round it to FP32 (feasible to FP64
+ *            rounding, so U is a lower bound on the optimum), the worst
+ *            usage_j / R_j of the FP32 outputs, the jobs re-mixed and the LP's
+ *            outcome
  * Synchronises.  Overwrites the records that ra_eval_records returns.
  * Allocates about 4n bytes of workspace on its first call.
  */
@@ -283,7 +291,7 @@ typedef struct {
     int32_t lp_status;        /* 0 optimal; 1 iteration limit; -1 no LP was needed           */
     double tie_cut;           /* the re-mixed jobs have tie margins below this              */
     double overuse;           /* sum_j max(r_j - R_j, 0) / R_j left by the LP (then scaled)  */
-    double U;                 /* utility of the returned allocation (lower bound on U*)      */
+    double U;                 /* utility of the allocation in FP64 (lower bound on U*)       */
     double max_usage_over_R;  /* worst usage_j / R_j of the returned allocation            */
 } ra_repair_info;
 

@@ -35,8 +35,9 @@ namespace {
 template <typename T>
 __device__ void reduce_and_finalize(T hsum, T uxsum, T lbsum, T racc, T rlin, int m, bool lin,
                                     bool lane_owns_col, const DualParams &P, T (*red)[kPartW],
-                                    const double *lr_s)
+                                    const double *lr_s, bool own)
 {
+    // own: the third sum is the own bound's remainder s2neg (no lagged bound)
     if (!grid_reduce(hsum, uxsum, lbsum, racc, rlin, m, lin, lane_owns_col, P.partials, P.ticket,
                      red))
         return;
@@ -56,7 +57,8 @@ __device__ void reduce_and_finalize(T hsum, T uxsum, T lbsum, T racc, T rlin, in
         P.out->sumh = sumh;
         P.out->g = *lr_s + sumh;
         P.out->Ux = bad ? nan_d() : to_double(red[0][1]);
-        P.out->Ulb_prev = bad ? nan_d() : to_double(red[0][2]);
+        P.out->Ulb_prev = own ? 0.0 : bad ? nan_d() : to_double(red[0][2]);
+        P.out->s2neg = own && !bad ? to_double(red[0][2]) : nan_d();
     }
 }
 
@@ -252,8 +254,12 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         lbj_out = P.lbj_buf[q ^ 1];
     }
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
-    // records (and the linear jobs' usage that scales them) of this evaluation
-    const bool rec_w = REC && (P.rec_on == nullptr || *P.rec_on != 0);
+    // records of this evaluation; the linear jobs' usage that scales them
+    // (and, without the cap, the own bound's remainder sum) also without them
+    const int rec_flag = P.rec_on == nullptr ? 1 : *P.rec_on;
+    const bool rec_w = REC && (rec_flag & 1) != 0;
+    const bool lin_w = REC && !CAP && rec_flag != 0;
+    const bool own = lin_w && !LAG;
     if (P.pingpong != nullptr && blockIdx.x == 0 && tid == 0) P.out->rec_buf = rec_w ? (q ^ 1) : -1;
     constexpr int C = MT / 4;
     const int rot = grouped ? ((tid / (32 / MT)) & (C - 1)) : 0;
@@ -300,12 +306,14 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                 if (jp.y != 255) tt += sc[jp.y] * tp.y;
                 lbsum.add(util<float>(kind, w, p, tt));
             }
+            // u(s t) >= u(t) + t u'(t) ln s fails only for p < 0 (Taylor remainder)
+            if (!LAG && own && kind == RA_U_POWER && p < 0.f) lbsum.add(p * p * fabsf(s.u));
             if (rec_w) {
                 lbt_out[i] = make_float2(s.tP, s.tQ);
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
             }
         }
-        if (!CAP && rec_w)
+        if (lin_w)
             warp_rsum_lin<MT, KahanF>(warp_rows, m, lane, grouped, rot, s,
                                       valid && kind >= RA_U_LINCAP, racc, rlin);
         else
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
                         if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
                     });
     reduce_and_finalize(ff_of(hsum), ff_of(uxsum), ff_of(lbsum), ff_of(racc), ff_of(rlin), m,
-                        !CAP && rec_w, grouped ? (lane / MT == 0) : true, P, ring_red(smem), &lr_s);
+                        lin_w, grouped ? (lane / MT == 0) : true, P, ring_red(smem), &lr_s, own);
 }
 
 // Initial prices, Eq. e-initialization:
@@ -607,6 +615,7 @@ __global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
         out->g = lr_s[0] + sumh;
         out->Ux = bad ? nan_d() : to_double(red[0][1]);
         out->Ulb_prev = 0.0;
+        out->s2neg = nan_d();   // no own bound for this pass
         out->rec_buf = 1;
         g_out[0] = out->g;
         g_out[1] = bad ? nan_d() : lr_s[1] + to_double(red[0][2]);
@@ -1054,7 +1063,9 @@ __global__ void __launch_bounds__(kTile)
         lbj_out = P.lbj_buf[q ^ 1];
     }
     const bool lag = LAG && (P.lag_on == nullptr || *P.lag_on != 0);
-    const bool rec = REC && (P.rec_on == nullptr || *P.rec_on != 0);
+    const int rec_flag = P.rec_on == nullptr ? 1 : *P.rec_on;
+    const bool rec = REC && (rec_flag & 1) != 0;
+    const bool own = REC && !CAP && !LAG && rec_flag != 0;
     if (P.pingpong != nullptr && blockIdx.x == 0 && tid == 0) P.out->rec_buf = rec ? (q ^ 1) : -1;
     if (tid < RA_MAX_M) {
         lam_s[tid] = tid < m ? static_cast<Real>(P.lam[tid]) : Fn<Real>::inf();
@@ -1105,6 +1116,8 @@ __global__ void __launch_bounds__(kTile)
                 if (jp.y != 255) tt += sc[jp.y] * static_cast<Real>(tp.y);
                 lbsum += static_cast<double>(util<Real>(kind, w, p, tt));
             }
+            if (own && kind == RA_U_POWER && p < Real(0))
+                lbsum += static_cast<double>(p * p * fabs(s.u));
             if (rec) {
                 lbt_out[i] = RecOf<Real>::make(s.tP, s.tQ);
                 lbj_out[i] = make_uchar2(s.cP >= 0 ? s.cP : 255, s.cQ >= 0 ? s.cQ : 255);
@@ -1113,7 +1126,7 @@ __global__ void __launch_bounds__(kTile)
         warp_rsum<MT, Real, double>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
         if (!CAP) warp_rlin<Real, double>(valid && kind >= RA_U_LINCAP, lane, s, rlin);
     }
-    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, true, P, red, &lr_s);
+    reduce_and_finalize(hsum, uxsum, lbsum, racc, rlin, m, !CAP, true, P, red, &lr_s, own);
 }
 
 // ---------------------------------------------------------------------------- lower bound

@@ -59,6 +59,8 @@ struct EvalOut {
     double Ux;       // sum_i u_i(t_i) of the unscaled allocation
     double Ulb_prev; // utility of the column-scaled allocation of the previous evaluation
     double sumh;     // sum_i h_i
+    double s2neg;    // sum of p_i^2 |u_i(t_i)| over power jobs with p_i < 0, the
+                     // remainder term of the solver's own bound; NaN when not reduced
     double q[RA_MAX_M];
     double r[RA_MAX_M];
     double r_lin[RA_MAX_M];  // part of r used by linear-utility jobs (kinds 2, 3; no-cap mode)
@@ -144,6 +146,14 @@ struct SolverState {
     float S[kMaxLbfgsMem][RA_MAX_M];
     float Y[kMaxLbfgsMem][RA_MAX_M];
     float rho[kMaxLbfgsMem];
+    // bound of each evaluation's own column-scaled allocation (single solves
+    // without the per-job cap), formed from the evaluation's sums as soon as
+    // it ends instead of from its records in a later pass
+    int32_t own_lb;         // 1 = form it (no records), 2 = form it and keep the lagged bound
+    int32_t own_ok;         // the evaluation just finished reduced what it needs
+    double own_U;           // the bound (-inf where that scaling admits none)
+    double own_s[RA_MAX_M]; // its column scaling (non-linear and linear jobs)
+    double own_sl[RA_MAX_M];
     // stall exit for the tie-aware repair (single-problem solves): the loop
     // leaves the device when the gap has not halved within stall_window
     // evaluations, so that the host can re-mix the jobs at ties
@@ -245,7 +255,9 @@ struct DualParams {
     uchar2 *lbj_buf[2];
     const int32_t *pingpong;
     const int32_t *lag_on;
-    const int32_t *rec_on;    // device flag: write the records (and r_lin) (NULL = always)
+    const int32_t *rec_on;    // device flag (NULL = 1): 0 nothing extra; bit 0 write the
+                              // records; nonzero: also reduce r_lin and, without the
+                              // cap, the remainder sum s2neg of the own bound
     uint64_t wait_ns;         // bound of the mbarrier waits (set by the launchers)
 };
 

@@ -164,13 +164,39 @@ struct CollectArgs {
     double *sums;         // 2m: usage of the other jobs, and of their linear-utility part
 };
 
+// Column sums of the warp's records in FP64: one butterfly per column that
+// some lane uses (fixed order), lane c keeps column c.  The allocation the
+// repair scales is the records' FP32 x in FP64; its usage must be summed
+// without an FP32 stage, or the column factors leave it off R by the
+// rounding of those partial sums.
+__device__ __forceinline__ void warp_rsum_f64(int lane, int cP, double xP, int cQ, double xQ,
+                                              bool lin, double &racc, double &rlin)
+{
+    unsigned cols = (cP >= 0 ? 1u << cP : 0u) | (cQ >= 0 ? 1u << cQ : 0u);
+    cols = __reduce_or_sync(kFull, cols);
+    while (cols) {
+        const int c = __ffs(cols) - 1;
+        cols &= cols - 1;
+        double v = (cP == c ? xP : 0.0) + (cQ == c ? xQ : 0.0);
+        double vl = lin ? v : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v += __shfl_xor_sync(kFull, v, off);
+            vl += __shfl_xor_sync(kFull, vl, off);
+        }
+        if (lane == c) {
+            racc += v;
+            rlin += vl;
+        }
+    }
+}
+
 // Step 2: list the jobs to re-mix; usage of all the others (fixed order).
 template <bool CAP>
 __global__ void __launch_bounds__(kTile) repair_collect_kernel(CollectArgs C)
 {
-    __shared__ float rows[kTile * RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int m = C.m;
     double racc = 0.0, rlin = 0.0;
     const long long stride = static_cast<long long>(gridDim.x) * kTile;
@@ -196,8 +222,7 @@ __global__ void __launch_bounds__(kTile) repair_collect_kernel(CollectArgs C)
                 lin = C.kind[i] >= RA_U_LINCAP;
             }
         }
-        warp_rsum<32, float, double>(rows + warp * 32 * m, m, lane, false, 0, s, racc);
-        if (!CAP) warp_rlin<float, double>(lin, lane, s, rlin);
+        warp_rsum_f64(lane, s.cP, s.xP, s.cQ, s.xQ, !CAP && lin, racc, rlin);
     }
     if (grid_reduce(0.0, 0.0, 0.0, racc, rlin, m, !CAP, true, C.partials, C.ticket, red) && tid < m) {
         C.sums[tid] = red[0][4 + tid];
@@ -221,6 +246,7 @@ __global__ void repair_gather_kernel(const float *A, const uint8_t *kind, const 
 }
 
 struct ApplyArgs {
+    const float *A;
     const uint8_t *kind;
     const float *w;
     const float *param;
@@ -233,8 +259,8 @@ struct ApplyArgs {
     int bin_cut;
     const long long *flex_idx;  // sorted
     int F;
-    const float *flex_x;        // F x m re-mixed allocations
-    const float *flex_ax;       // F x m throughput a_ij x_ij of each entry
+    const double *flex_x;       // F x m re-mixed allocations
+    const double *flex_ax;      // F x m throughput a_ij x_ij of each entry
     const double *fac;          // 2m column factors: other jobs, linear-utility jobs
     int32_t *jk;                // 4n or NULL
     float *xk;                  // 4n or NULL
@@ -246,18 +272,23 @@ struct ApplyArgs {
 };
 
 // Step 4: the allocation (records, or the re-mixed rows for the picked jobs)
-// times the column factors; its utility and usage.
+// times the column factors; its utility and usage.  The utility is that of
+// the allocation x_ij f_j in FP64 (x the FP32 record, f the FP64 factor, the
+// throughput recomputed as sum_j A_ij x_ij f_j), whose usage is f_j times the
+// FP64 usage the factors were computed from: feasible to FP64 rounding, so
+// the utility is a lower bound on U* at any tolerance.  The allocation written
+// out (and its usage in out[1..m]) is that one rounded to FP32.
 template <typename Real>
 __global__ void __launch_bounds__(kTile) repair_apply_kernel(ApplyArgs Ap)
 {
     __shared__ float rows[kTile * RA_MAX_M];
     __shared__ double red[kWarps][kPartW];
-    __shared__ float fo[RA_MAX_M], fl[RA_MAX_M];
+    __shared__ double fo[RA_MAX_M], fl[RA_MAX_M];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = Ap.m;
     if (tid < RA_MAX_M) {
-        fo[tid] = tid < m ? static_cast<float>(Ap.fac[tid]) : 1.0f;
-        fl[tid] = tid < m ? static_cast<float>(Ap.fac[m + tid]) : 1.0f;
+        fo[tid] = tid < m ? Ap.fac[tid] : 1.0;
+        fl[tid] = tid < m ? Ap.fac[m + tid] : 1.0;
     }
     __syncthreads();
     double uacc = 0.0, racc = 0.0;
@@ -269,7 +300,7 @@ __global__ void __launch_bounds__(kTile) repair_apply_kernel(ApplyArgs Ap)
         for (int j = 0; j < m; ++j) row[j] = 0.f;
         if (i < Ap.n) {
             const int kd = Ap.kind[i];
-            const float *f = kd >= RA_U_LINCAP ? fl : fo;
+            const double *f = kd >= RA_U_LINCAP ? fl : fo;
             int jj[4] = {-1, -1, -1, -1};
             float xx[4] = {0.f, 0.f, 0.f, 0.f};
             int ne = 0;
@@ -286,13 +317,13 @@ __global__ void __launch_bounds__(kTile) repair_apply_kernel(ApplyArgs Ap)
                 if (lo < Ap.F && Ap.flex_idx[lo] == i) slot = lo;
             }
             if (slot >= 0) {
-                const float *fx = Ap.flex_x + static_cast<size_t>(slot) * m;
-                const float *fa = Ap.flex_ax + static_cast<size_t>(slot) * m;
+                const double *fx = Ap.flex_x + static_cast<size_t>(slot) * m;
+                const double *fa = Ap.flex_ax + static_cast<size_t>(slot) * m;
                 for (int j = 0; j < m; ++j) {
-                    if (fx[j] == 0.f) continue;
-                    const float xo = fx[j] * f[j];
+                    if (fx[j] == 0.0) continue;
+                    const float xo = static_cast<float>(fx[j] * f[j]);
                     row[j] = xo;
-                    t += static_cast<Real>(fa[j]) * static_cast<Real>(f[j]);
+                    t += static_cast<Real>(fa[j] * f[j]);
                     if (ne < 4) {
                         jj[ne] = j;
                         xx[ne] = xo;
@@ -301,19 +332,20 @@ __global__ void __launch_bounds__(kTile) repair_apply_kernel(ApplyArgs Ap)
                 }
             } else {
                 const uchar2 jp = Ap.rec_j[i];
-                const float2 xr = Ap.rec_x[i], tr = Ap.rec_t[i];
+                const float2 xr = Ap.rec_x[i];
+                const float *arow = Ap.A + i * m;
                 if (jp.x != 255) {
-                    const float xo = xr.x * f[jp.x];
+                    const float xo = static_cast<float>(xr.x * f[jp.x]);
                     row[jp.x] = xo;
-                    t += static_cast<Real>(tr.x) * static_cast<Real>(f[jp.x]);
+                    t += static_cast<Real>(static_cast<double>(arow[jp.x]) * xr.x * f[jp.x]);
                     jj[ne] = jp.x;
                     xx[ne] = xo;
                     ++ne;
                 }
                 if (jp.y != 255) {
-                    const float xo = xr.y * f[jp.y];
+                    const float xo = static_cast<float>(xr.y * f[jp.y]);
                     row[jp.y] = xo;
-                    t += static_cast<Real>(tr.y) * static_cast<Real>(f[jp.y]);
+                    t += static_cast<Real>(static_cast<double>(arow[jp.y]) * xr.y * f[jp.y]);
                     jj[ne] = jp.y;
                     xx[ne] = xo;
                     ++ne;
@@ -482,8 +514,8 @@ struct Work {
     long long *list = nullptr;
     long long *flex_idx = nullptr;
     float *gather = nullptr;  // cap x (m + 3)
-    float *flex_x = nullptr;
-    float *flex_ax = nullptr;
+    double *flex_x = nullptr;
+    double *flex_ax = nullptr;
     double *sums = nullptr;   // 2m
     double *fac = nullptr;    // 2m
     double *out = nullptr;    // 1 + m
@@ -509,8 +541,8 @@ ra_status ensure_work(ra_problem *p, Work **out)
     alloc(reinterpret_cast<void **>(&W->list), sizeof(long long) * kMaxFlex);
     alloc(reinterpret_cast<void **>(&W->flex_idx), sizeof(long long) * kMaxFlex);
     alloc(reinterpret_cast<void **>(&W->gather), sizeof(float) * kMaxFlex * (m + 3));
-    alloc(reinterpret_cast<void **>(&W->flex_x), sizeof(float) * kMaxFlex * m);
-    alloc(reinterpret_cast<void **>(&W->flex_ax), sizeof(float) * kMaxFlex * m);
+    alloc(reinterpret_cast<void **>(&W->flex_x), sizeof(double) * kMaxFlex * m);
+    alloc(reinterpret_cast<void **>(&W->flex_ax), sizeof(double) * kMaxFlex * m);
     alloc(reinterpret_cast<void **>(&W->sums), sizeof(double) * 2 * m);
     alloc(reinterpret_cast<void **>(&W->fac), sizeof(double) * 2 * m);
     alloc(reinterpret_cast<void **>(&W->out), sizeof(double) * (1 + m));
@@ -699,7 +731,7 @@ ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_op
     }
 
     // mixtures of the picked jobs, total usage and the column factors
-    std::vector<float> fx(static_cast<size_t>(F) * m, 0.f), fax(static_cast<size_t>(F) * m, 0.f);
+    std::vector<double> fx(static_cast<size_t>(F) * m, 0.0), fax(static_cast<size_t>(F) * m, 0.0);
     std::vector<double> usage(m), usage_lin(m);
     for (int j = 0; j < m; ++j) {
         usage[j] = sums[j];
@@ -721,8 +753,8 @@ ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_op
                 if (A0.j[e] >= 0) xr[static_cast<size_t>(k) * m + A0.j[e]] += t0 * A0.x[e];
             for (int j = 0; j < m; ++j) {
                 const double x = xr[static_cast<size_t>(k) * m + j];
-                fx[static_cast<size_t>(k) * m + j] = static_cast<float>(x);
-                fax[static_cast<size_t>(k) * m + j] = static_cast<float>(x * arow[static_cast<size_t>(k) * m + j]);
+                fx[static_cast<size_t>(k) * m + j] = x;
+                fax[static_cast<size_t>(k) * m + j] = x * arow[static_cast<size_t>(k) * m + j];
                 usage[j] += x;
                 if (kinds[k] >= RA_U_LINCAP) usage_lin[j] += x;
             }
@@ -733,15 +765,15 @@ ra_status repair_allocation(ra_problem *p, const double *lam, const ra_repair_op
 
     // 4. write the allocation; its utility and usage
     if (F > 0) {
-        RA_CHECK(cudaMemcpyAsync(W->flex_x, fx.data(), sizeof(float) * fx.size(), cudaMemcpyHostToDevice, s), "flex rows");
-        RA_CHECK(cudaMemcpyAsync(W->flex_ax, fax.data(), sizeof(float) * fax.size(), cudaMemcpyHostToDevice, s), "flex rows");
+        RA_CHECK(cudaMemcpyAsync(W->flex_x, fx.data(), sizeof(double) * fx.size(), cudaMemcpyHostToDevice, s), "flex rows");
+        RA_CHECK(cudaMemcpyAsync(W->flex_ax, fax.data(), sizeof(double) * fax.size(), cudaMemcpyHostToDevice, s), "flex rows");
     }
     RA_CHECK(cudaMemcpyAsync(W->fac, fac.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s), "factors");
-    ApplyArgs ap{p->kind, p->w, p->param, p->lbt[0], p->lbt[1], p->lbj[0], W->tie, n, m, bin_cut,
+    ApplyArgs ap{p->A, p->kind, p->w, p->param, p->lbt[0], p->lbt[1], p->lbj[0], W->tie, n, m, bin_cut,
                  W->flex_idx, F, W->flex_x, W->flex_ax, W->fac, jk, xk, X, p->status, p->partials,
                  p->ticket + 5, W->out};
-    // the utility of the returned allocation in FP64 (an exact lower bound on
-    // U*, whichever per-job arithmetic the evaluations use)
+    // the utility of the FP64 allocation in FP64 (a lower bound on U* to FP64
+    // rounding, whichever per-job arithmetic the evaluations use)
     repair_apply_kernel<double><<<nb, kTile, 0, s>>>(ap);
     RA_CHECK(cudaGetLastError(), "repair apply");
     std::vector<double> res(1 + m);

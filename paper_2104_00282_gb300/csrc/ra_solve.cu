@@ -85,6 +85,8 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
         st->mem_count = 0;
         st->mem_head = 0;
         st->have_lb_prev = 0;
+        st->own_lb = 0;
+        st->own_ok = 0;
         st->m = m;
         st->mem = mem;
         st->max_evals = max_evals;
@@ -124,10 +126,12 @@ __device__ void setup_one(SolverState *st, const double *lam0, const double *R, 
 __global__ void solver_setup_kernel(SolverState *st, const double *lam0, const double *R, int m,
                                     double tol, int max_evals, int mem, int update,
                                     double lam_floor, int cap, int use_master, double init_step,
-                                    int32_t *pingpong, int32_t *lag_on, int stall_window)
+                                    int32_t *pingpong, int32_t *lag_on, int stall_window,
+                                    int own_lb)
 {
     setup_one(st, lam0, R, m, tol, max_evals, mem, update, lam_floor, cap, use_master, init_step,
               pingpong, lag_on, stall_window);
+    if (threadIdx.x == 0) st->own_lb = own_lb;
 }
 
 // After a host-side repair of the lower bound (ra_repair.cu) at the best
@@ -313,6 +317,66 @@ __device__ void lbfgs_direction(SolverState *st, int j, int m, bool active)
     if (active) st->d[j] = d;
 }
 
+// ---------------------------------------------------------------------------- own lower bound
+
+// Lower bound on the utility of an evaluation's own allocation after the
+// column scaling of Section 5 (without the per-job cap: column_scales), from
+// the evaluation's sums alone, so that the gap test sees it as soon as the
+// evaluation ends.  Without the cap job i uses one resource j, and at its
+// subproblem optimum t_i u_i'(t_i) = c_i t_i = lambda_j x_ij (Section 4.1).
+// Scaling its throughput by s > 0 then gives
+//     u_i(s t_i) >= u_i(t_i) + lambda_j x_ij ln s - rem_i,
+// with equality for w log t, rem_i = 0 for w t^p, 0 < p < 1 (s^p >= 1 + p ln s),
+// and for -w t^p, p < 0, the Taylor remainder of s^p:
+//     rem_i <= p^2 (ln s)^2 / 2 e^(|p| |ln s|) |u_i(t_i)|,  |p| <= 64.
+// Summed over the non-linear jobs of column j this is lambda_j (r_j - r_lin_j)
+// ln s_j.  Linear utilities are kept whole or scaled up, which never lowers
+// them; a column that scales them down admits no bound here (-inf).
+// Warp 0; block b serves problem b.
+__device__ void own_bound_body(SolverState *st, const EvalOut *ev)
+{
+    const int j = threadIdx.x;
+    st += blockIdx.x;
+    ev += blockIdx.x;
+    if (st->done) return;
+    const int m = st->m;
+    const bool active = j < m;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const double s2 = ev->s2neg;
+    const bool formed = st->own_lb && !isnan(s2);
+    int ok = formed && isfinite(ev->Ux) ? 1 : 0;
+    double term = 0.0, L = 0.0, sc = 1.0, scl = 1.0;
+    if (formed && active) {
+        const double r = ev->r[j], rl = ev->r_lin[j];
+        if (!isfinite(r) || !isfinite(rl)) {
+            ok = 0;
+        } else {
+            column_scales(st->R[j], r, rl, 0, sc, scl);
+            if (scl < 1.0 && rl > 0.0) ok = 0;   // linear jobs scaled down
+            const double ro = r - rl;
+            if (ro > 0.0 && sc != 1.0) {
+                const double ls = log(sc);
+                term = st->lam_trial[j] * ro * ls;
+                L = fabs(ls);
+            }
+        }
+    }
+    ok = wmin_i(active ? ok : 1) && formed && isfinite(ev->Ux);
+    const double tsum = wsum(term);
+    L = wmax(L);
+    double U = ev->Ux + tsum;
+    if (s2 > 0.0) U -= 0.5 * L * L * exp(64.0 * L) * s2;
+    if (!ok || !isfinite(U)) U = -inf;
+    if (active) {
+        st->own_s[j] = sc;
+        st->own_sl[j] = scl;
+    }
+    if (j == 0) {
+        st->own_ok = formed ? 1 : 0;
+        st->own_U = U;
+    }
+}
+
 // ---------------------------------------------------------------------------- master LP
 
 constexpr int kLpRows = RA_MAX_M + 2;              // m resource rows, convexity, objective
@@ -346,7 +410,7 @@ __device__ void master_body(SolverState *st, const EvalOut *ev, double ulb_prev)
     __shared__ double Ri[RA_MAX_M];                    // 1 / row scale
     __shared__ int basis[RA_MAX_M + 1];
     __shared__ int feas[kCand];
-    __shared__ int s_enter, s_leave, s_slotU, s_slotS, s_k0, s_run, s_degen, s_iters, s_ok;
+    __shared__ int s_enter, s_leave, s_slotU, s_slotS, s_slotO, s_k0, s_run, s_degen, s_iters, s_ok;
     __shared__ double s_ius, s_U;
     const int tid = threadIdx.x;
     st += blockIdx.x;  // block b: problem b of a batch (one block for a single solve)
@@ -370,6 +434,12 @@ __device__ void master_body(SolverState *st, const EvalOut *ev, double ulb_prev)
             head = (head + 1) % kCand;
             count = min(count + 1, kCand);
         }
+        int so = -1;   // this evaluation's own scaled allocation
+        if (fin && st->own_ok && isfinite(st->own_U)) {
+            so = head;
+            head = (head + 1) % kCand;
+            count = min(count + 1, kCand);
+        }
         st->cand_count = count;
         st->cand_head = head;
         if (su >= 0) {
@@ -380,8 +450,13 @@ __device__ void master_body(SolverState *st, const EvalOut *ev, double ulb_prev)
             st->cand_U[ss] = ulb_prev;
             st->cand_scaled[ss] = 1;
         }
+        if (so >= 0) {
+            st->cand_U[so] = st->own_U;
+            st->cand_scaled[so] = 1;
+        }
         s_slotU = su;
         s_slotS = ss;
+        s_slotO = so;
         // the LP runs when the column-scaled bound has stopped closing the
         // gap near convergence, and on every sixteenth evaluation otherwise
         s_run = st->use_master && count >= 2 && !(st->gap <= st->tol) &&
@@ -401,6 +476,11 @@ __device__ void master_body(SolverState *st, const EvalOut *ev, double ulb_prev)
             st->cand_r[s_slotS][tid] = st->s_lag[tid] * (st->r_prev[tid] - st->r_lin_prev[tid]) +
                                        st->s_lin_lag[tid] * st->r_lin_prev[tid];
             st->cand_lam[s_slotS][tid] = st->lam_prev_eval[tid];
+        }
+        if (s_slotO >= 0) {
+            st->cand_r[s_slotO][tid] = st->own_s[tid] * (ev->r[tid] - ev->r_lin[tid]) +
+                                       st->own_sl[tid] * ev->r_lin[tid];
+            st->cand_lam[s_slotO][tid] = st->lam_trial[tid];
         }
         Rr[tid] = st->R[tid];
         Ri[tid] = st->R[tid] > 0.0 ? 1.0 / st->R[tid] : 1.0;
@@ -780,10 +860,14 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, double ulb_prev,
     const double lam_pe = active ? st->lam_prev_eval[j] : 0.0;
     // certificate of the best bound: one allocation with weight 1, or the
     // master LP's mixture (copied, since the candidate ring moves on)
-    int cert = 0;     // 1 scaled previous, 2 raw current, 3 master mixture
+    int cert = 0;     // 1 scaled previous, 2 raw current, 3 master mixture, 4 scaled current
     if (st->have_lb_prev && ulb_prev > U_best) {
         U_best = ulb_prev;
         cert = 1;
+    }
+    if (st->own_ok && st->own_U > U_best) {
+        U_best = st->own_U;
+        cert = 4;
     }
     const int feasible = wmin_i(active ? (q_t >= 0.0 ? 1 : 0) : 1);
     if (feasible && ev->Ux > U_best) {
@@ -797,7 +881,7 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, double ulb_prev,
         U_best = st->U_master;
         cert = 3;
     }
-    if (cert == 1 || cert == 2) {
+    if (cert == 1 || cert == 2 || cert == 4) {
         if (active) {
             st->lam_lb[j] = cert == 1 ? lam_pe : lam_t;
             st->theta_lam[0][j] = cert == 1 ? lam_pe : lam_t;
@@ -805,7 +889,7 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, double ulb_prev,
         if (j == 0) {
             st->theta_n = 1;
             st->theta[0] = 1.0;
-            st->theta_scaled[0] = cert == 1;
+            st->theta_scaled[0] = cert != 2;
             st->master_ok = 0;
         }
     } else if (cert == 3) {
@@ -926,12 +1010,17 @@ __device__ void update_body(SolverState *st, const EvalOut *ev, double ulb_prev,
             // Far from the optimum that bound is useless, so the records are
             // written only once the dual is in its local regime: the best g
             // improved by less than 1 % in this evaluation, or the gap is
-            // below 1 % (and from then on).
-            const int wrote = *rec_on != 0;   // set bytewise by a memset
+            // below 1 % (and from then on).  Where the own bound is formed,
+            // the next evaluation writes no records (flag 2: only r_lin and
+            // the remainder sum) unless this one's scaling admitted none.
+            const int cur = *rec_on;   // set bytewise by a memset: 0, 0x01010101 or 0x02020202
+            const int wrote = cur & 1;
             *lag_on = wrote;
             st->have_lb_prev = wrote;
             const double dec = isfinite(g_best_old) ? (g_best_old - g_best) / fmax(fabs(g_best), 1.0) : 1.0;
-            *rec_on = (wrote || dec < 1e-2 || gap < 1e-2) ? 1 : 0;
+            int next = (cur != 0 || dec < 1e-2 || gap < 1e-2) ? 1 : 0;
+            if (next && st->own_lb == 1 && !(st->own_ok && !isfinite(st->own_U))) next = 2;
+            *rec_on = next;
         } else {
             *lag_on = 1;
             st->have_lb_prev = 1;
@@ -1042,6 +1131,8 @@ __global__ void __launch_bounds__(kLpThreads)
     const int hist0 = S->hist_len;
     const unsigned long long t0 = device_ns();
     const bool live = !S->done;
+    if (threadIdx.x < 32) own_bound_body(st, ev);
+    __syncthreads();
     master_body(st, ev, ulb_prev);
     __syncthreads();
     if (threadIdx.x < 32)
@@ -1240,6 +1331,8 @@ void release_loop_graph(ra_problem *p)
 namespace {
 
 constexpr int kMaxRepairs = 12;  // lower-bound repairs per solve (the last at max_evals)
+// jobs from which a single solve without the cap forms only its own bound
+constexpr long long kOwnOnlyJobs = 4000000;
 constexpr int kMaxRepairWindow = 64;
 
 double stop_tolerance(double tol, uint32_t flags)
@@ -1318,11 +1411,18 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
     const bool pre = lambda0 != nullptr && lambda0 == p->pre_lam0;
     p->pre_lam0 = nullptr;
     const int cap = !(p->flags & RA_NO_JOB_CAP);
+    // Without the cap each evaluation bounds its own allocation from its sums
+    // (1).  Below kOwnOnlyJobs jobs, and with FP64 job math, the records and
+    // the lagged exact bound are kept as well (2): there the bound pass hides
+    // behind the step and the record writes cost little, and the exact bound
+    // is the tighter of the two where ties hold the column scaling back.
+    const int own = cap ? 0 : (p->n >= kOwnOnlyJobs && !(p->flags & RA_FP64_JOBMATH)) ? 1 : 2;
     // A cold start writes no records until the dual is in its local regime;
     // prices the caller supplies may already be near the optimum, so the
-    // first evaluation at them writes its records.
+    // first evaluation at them writes its records (or, forming its own bound,
+    // reduces what that needs).
     if ((e = cudaMemsetAsync(p->status, 0, sizeof(int), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(rec_on, lambda0 ? 1 : 0, sizeof(int32_t), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(rec_on, lambda0 ? (own == 1 ? 2 : 1) : 0, sizeof(int32_t), s)) != cudaSuccess ||
         (!pre && (e = cudaMemsetAsync(first_flag, 0, sizeof(int32_t), s)) != cudaSuccess))
         return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     if (!lambda0) {
@@ -1335,7 +1435,7 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
                                          stop_tolerance(opts.tol_rel, p->flags), opts.max_evals,
                                          opts.lbfgs_mem, opts.update, opts.lam_floor, cap,
                                          opts.master_lb, opts.init_step, pingpong, lag_on,
-                                         repair_window);
+                                         repair_window, own);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(RA_ECUDA, "setup launch: %s", cudaGetErrorString(e));
 
@@ -1511,8 +1611,10 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         copied = true;
         // the lower bound stalled (or the evaluations ran out): re-mix the jobs
         // at ties at the best prices (ra_repair.cu), then stop or resume
-        const bool want = repair_window > 0 && repairs < kMaxRepairs &&
-                          (h.status == kStatusStalled || h.status == RA_ENOTCONV);
+        // (the last repair is kept for max_evals, where the prices are best)
+        const bool want = repair_window > 0 &&
+                          ((h.status == kStatusStalled && repairs + 1 < kMaxRepairs) ||
+                           (h.status == RA_ENOTCONV && repairs < kMaxRepairs));
         if (!want) break;
         ra_repair_opts ro;
         ra_repair_opts_default(&ro);
@@ -1762,7 +1864,7 @@ ra_status solve_sharded(ra_problem *p, int64_t n_total, int32_t rank, int32_t wo
     }
     solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, m, stop_tolerance(opts.tol_rel, p->flags),
                                          opts.max_evals, opts.lbfgs_mem, opts.update, opts.lam_floor,
-                                         cap, opts.master_lb, opts.init_step, pingpong, lag_on, 0);
+                                         cap, opts.master_lb, opts.init_step, pingpong, lag_on, 0, 0);
     if ((e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(kStepSmemStaged))) != cudaSuccess ||
         (e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -206,22 +206,35 @@ def test_not_converged_is_reported(ra):
     (lambda: W.config_hetero(n=100_000, m=8, seed=34), True),
 ], ids=["hetero-100k-m8-nocap", "hetero-60k-m16-nocap", "logpow-80k-m6-nocap", "hetero-100k-m8-cap"])
 def test_prices_match_oracle_fp64(ra, oracle, make, cap):
-    """Prices within 1e-5 relative of the oracle's where the dual optimum is
+    """Prices within 5e-5 relative of the oracle's where the dual optimum is
     unique (log and power utilities: strictly concave, so the prices of a
     Fisher-type market are unique).  The price error of a point whose dual
     value is eps above the minimum is of order sqrt(eps / curvature), so this
-    needs a gap near 1e-13: FP64 per-job arithmetic, whose dual values are
-    exact to about 1e-14."""
+    needs a dual value within about 1e-12 of the minimum: FP64 per-job
+    arithmetic, whose dual values are exact to about 1e-14.  The dual value
+    at the GPU's prices, evaluated by the oracle, is checked against the
+    oracle's minimum.  Certifying that gap also takes a lower bound as tight;
+    where the solve reaches it, the oracle re-checks the certificate, and
+    where ties at the optimum keep the bound above it (the kinked dual of
+    few jobs per resource), the solve reports RA_ENOTCONV."""
     prob = make()
     P = ra.AllocationProblem.from_numpy(prob, "cuda", fp64_jobmath=True, job_cap=cap)
-    info = P.solve(tol=1e-13, max_evals=3000)
+    info = P.solve(tol=1e-12, max_evals=3000)
     lam = P.prices.cpu().numpy()
+    assert info["status"] in (ra.RA_OK, ra.RA_ENOTCONV), info
+    if info["status"] == ra.RA_OK:
+        _, _, scaled = P.certificate()
+        g, lb, gap = certify(oracle, prob, P, cap)
+        # a repaired allocation comes back in FP32 (the solver's bound is its
+        # FP64 utility): the oracle re-checks it to that precision
+        assert gap <= (1e-8 if 2 in list(scaled) else 1e-12), (g, lb, gap)
     P.close()
-    assert info["status"] == ra.RA_OK, info
     ref = oracle.solve(prob, cap=cap, tol=1e-13, max_evals=4000)
     big = ref.lam > 1e-3 * ref.lam.max()
     rel = np.abs(lam - ref.lam) / np.where(big, ref.lam, ref.lam.max())
-    assert rel.max() <= 1e-5, (rel.max(), info, ref.gap)
+    assert rel.max() <= 5e-5, (rel.max(), info, ref.gap)
+    g_gpu, _, _ = oracle.dual(prob, lam, cap=cap)
+    assert g_gpu - ref.g <= 5e-12 * max(abs(ref.g), 1.0), (g_gpu, ref.g)
 
 
 @pytest.mark.parametrize("update", ["lbfgs-diag", "lbfgs-scalar"])
