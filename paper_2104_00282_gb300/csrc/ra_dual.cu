@@ -108,8 +108,11 @@ template <int MT, class Job, class Pre = NoPrologue>
 __device__ bool stream_jobs(const float *A, const float *W, const float *Par, const uint8_t *Kind,
                             const float2 *rec_t, const uchar2 *rec_j, long long n, int m,
                             int stages, long long num_full, unsigned char *smem, uint64_t *bars,
-                            int *status, uint64_t wait_ns, Job &&job, Pre &&pre = Pre{})
+                            int *status, uint64_t wait_ns, Job &&job, Pre &&pre = Pre{},
+                            long long tstride = 1)
 {
+    // tstride > 1: only full tiles 0, tstride, 2 tstride, ... (a strided
+    // sample of the jobs; no ragged tail)
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t a_bytes = StageLayout<MT>::a_bytes(m);
     const size_t core_bytes = StageLayout<MT>::bytes(m);
@@ -121,10 +124,11 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
     }
     __syncthreads();
     const long long G = gridDim.x;
-    const long long n_my = (num_full > blockIdx.x) ? (num_full - blockIdx.x + G - 1) / G : 0;
+    const long long n_tiles = (num_full + tstride - 1) / tstride;
+    const long long n_my = (n_tiles > blockIdx.x) ? (n_tiles - blockIdx.x + G - 1) / G : 0;
     auto issue = [&](long long it) {
         if (it >= n_my) return;
-        const long long tile = blockIdx.x + it * G;
+        const long long tile = (blockIdx.x + it * G) * tstride;
         const int st = static_cast<int>(it % stages);
         unsigned char *base = smem + st * st_bytes;
         const long long j0 = tile * kTile;
@@ -164,7 +168,7 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
         const float *w_s = reinterpret_cast<const float *>(base + a_bytes);
         const float *p_s = reinterpret_cast<const float *>(base + a_bytes + kTile * 4);
         const uint8_t *k_s = base + a_bytes + kTile * 8;
-        const long long i = (blockIdx.x + it * G) * kTile + tid;
+        const long long i = (blockIdx.x + it * G) * tstride * kTile + tid;
         job(i, true, a_s + tid * m, static_cast<int>(k_s[tid]), w_s[tid], p_s[tid],
             a_s + warp * 32 * m, recs ? base + core_bytes : nullptr);
         __syncthreads();  // stage fully consumed
@@ -175,7 +179,7 @@ __device__ bool stream_jobs(const float *A, const float *W, const float *Par, co
     }
     // ragged tail: jobs [num_full * 256, n), one CTA, direct loads
     const long long tail0 = num_full * kTile;
-    if (tail0 < n && blockIdx.x == static_cast<unsigned>(num_full % G)) {
+    if (tstride == 1 && tail0 < n && blockIdx.x == static_cast<unsigned>(num_full % G)) {
         const long long i = tail0 + tid;
         const bool valid = i < n;
         float *scratch = reinterpret_cast<float *>(smem);  // stage 0 is idle now
@@ -338,10 +342,11 @@ __global__ void __launch_bounds__(kTile, 2)
     init_tma_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
                     const double *R, long long n, int m, int cap, int stages, long long num_full,
                     double *partials, unsigned *ticket, int *status, uint64_t wait_ns,
-                    long long n_all, double *lam1)
+                    long long n_all, double *lam1, long long tstride)
 {
     // n_all: jobs of the whole problem when these n are one shard of it (the
-    // per-job budget R / n_all and the mean's divisor); n otherwise
+    // per-job budget R / n_all and the mean's divisor); n otherwise.
+    // tstride > 1: the mean over every tstride-th full tile only
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ float x0_s[RA_MAX_M];
@@ -392,14 +397,16 @@ __global__ void __launch_bounds__(kTile, 2)
     };
     unsigned char *smem = align128<MT>(smem_dyn);
     stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
-                    wait_ns, job);
+                    wait_ns, job, NoPrologue{}, tstride);
     const FF z = red_zero<FF>();
     FF(*red)[kPartW] = ring_red(smem);
     if (grid_reduce(z, z, z, ff_of(racc), z, m, false, grouped ? (lane / MT == 0) : true, partials,
                     ticket, red)) {
         // a CTA whose wait gave up left its share out of the sums: no prices
         const bool bad = (ld_status(status) & kStatusTimeout) != 0;
-        if (tid < m) lam1[tid] = bad ? nan_d() : to_double(red[0][4 + tid]) / static_cast<double>(n_all);
+        const double div = tstride > 1 ? static_cast<double>((num_full + tstride - 1) / tstride * kTile)
+                                       : static_cast<double>(n_all);
+        if (tid < m) lam1[tid] = bad ? nan_d() : to_double(red[0][4 + tid]) / div;
     }
 }
 
@@ -421,8 +428,10 @@ __global__ void __launch_bounds__(kTile, 2)
     ray_scale_kernel(const float *A, const uint8_t *kind, const float *w, const float *param,
                      const double *R, long long n, int m, double *lam, int stages,
                      long long num_full, double *partials, unsigned *ticket, int *status,
-                     uint64_t wait_ns)
+                     uint64_t wait_ns, long long tstride)
 {
+    // tstride > 1: the spending of every tstride-th full tile, set against
+    // the same share of lambda^T R
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ __align__(16) float mu_s[RA_MAX_M];
@@ -488,7 +497,7 @@ __global__ void __launch_bounds__(kTile, 2)
     stream_jobs<MT>(A, w, param, kind, nullptr, nullptr, n, m, stages, num_full, smem, bars, status,
                     wait_ns, job, [&] {
                         if (tid == 32) lr_s = lam_dot_R(lamd_s, Rd_s, m);
-                    });
+                    }, tstride);
     // lane k of every warp takes the warp's total of S_k
     FF mine = red_zero<FF>();
 #pragma unroll
@@ -500,7 +509,10 @@ __global__ void __launch_bounds__(kTile, 2)
     FF(*red)[kPartW] = ring_red(smem);
     if (grid_reduce(z, z, z, mine, z, kRayK, false, true, partials, ticket, red) && tid == 0) {
         if (ld_status(status) & kStatusTimeout) return;   // incomplete sums: keep the prices
-        const double T = lr_s;
+        const double T = tstride > 1
+                             ? lr_s * static_cast<double>((num_full + tstride - 1) / tstride * kTile) /
+                                   static_cast<double>(n)
+                             : lr_s;
         double x = kRayK - 1;   // log2(s) + 8 of the crossing
         if (!(to_double(red[0][4]) > T)) {
             x = 0.0;
@@ -1676,18 +1688,21 @@ cudaError_t launch_dual_g2(const ra_problem *p, const double *lam_a, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all)
+cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all,
+                        long long tstride)
 {
     if (n_all <= 0) n_all = p->n;
     const long long num_full = p->n / kTile;
+    if (tstride < 1 || num_full < tstride) tstride = 1;
     int grid = p->grid_init;
-    if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
+    const long long tiles = (num_full + tstride - 1) / tstride;
+    if (tiles < grid) grid = static_cast<int>(tiles > 0 ? tiles : 1);
     const int cap = !(p->flags & RA_NO_JOB_CAP);
 #define RA_INIT(MT)                                                                                \
     init_tma_kernel<MT><<<grid, kTile, p->smem_dual, s>>>(p->A, p->kind, p->w, p->param, p->R,      \
                                                           p->n, p->m, cap, p->stages, num_full,    \
                                                           p->partials, p->ticket + 2, p->status,   \
-                                                          wait_limit_ns(), n_all, lam1)
+                                                          wait_limit_ns(), n_all, lam1, tstride)
     switch (p->mt) {
     case 4: RA_INIT(4); break;
     case 8: RA_INIT(8); break;
@@ -1698,16 +1713,18 @@ cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s)
+cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s, long long tstride)
 {
     const long long num_full = p->n / kTile;
+    if (tstride < 1 || num_full < tstride) tstride = 1;
     int grid = p->grid_ray;
-    if (num_full < grid) grid = static_cast<int>(num_full > 0 ? num_full : 1);
+    const long long tiles = (num_full + tstride - 1) / tstride;
+    if (tiles < grid) grid = static_cast<int>(tiles > 0 ? tiles : 1);
 #define RA_RAY(MT)                                                                                 \
     ray_scale_kernel<MT><<<grid, kTile, p->smem_dual, s>>>(p->A, p->kind, p->w, p->param, p->R,     \
                                                            p->n, p->m, lam, p->stages, num_full,   \
                                                            p->partials, p->ticket + 6, p->status,  \
-                                                           wait_limit_ns())
+                                                           wait_limit_ns(), tstride)
     switch (p->mt) {
     case 4: RA_RAY(4); break;
     case 8: RA_RAY(8); break;

@@ -301,8 +301,10 @@ struct BatchDualArgs {
 cudaError_t launch_dual(const ra_problem *p, const DualParams &dp, cudaStream_t s);
 cudaError_t launch_lower_bound(const ra_problem *p, const float2 *lbt, const uchar2 *lbj,
                                const EvalOut *src, double *U_lb, cudaStream_t s);
-cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all = 0);
-cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s);
+// tstride > 1: from every tstride-th full tile only (a strided sample)
+cudaError_t launch_init(const ra_problem *p, double *lam1, cudaStream_t s, long long n_all = 0,
+                        long long tstride = 1);
+cudaError_t launch_ray_scale(const ra_problem *p, double *lam, cudaStream_t s, long long tstride = 1);
 cudaError_t launch_dual_exact(const ra_problem *p, const double *lam, EvalOut *out, cudaStream_t s);
 void release_loop_graph(ra_problem *p);
 // g at two price vectors in one pass; with first_eval also the solver's first

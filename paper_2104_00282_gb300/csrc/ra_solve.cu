@@ -1426,9 +1426,21 @@ ra_status solve(ra_problem *p, const ra_solve_opts *o, const double *lambda0, do
         (!pre && (e = cudaMemsetAsync(first_flag, 0, sizeof(int32_t), s)) != cudaSuccess))
         return fail(RA_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     if (!lambda0) {
-        if ((e = launch_init(p, st->lam_trial, s)) != cudaSuccess)
+        // With the ray scaling, Eq. e-initialization only gives the start's
+        // direction and the scale is the minimiser of g along it: on large
+        // problems both passes read every ts-th tile only (at least eight
+        // tiles per CTA, ts <= 16), about 0.5 ms less at n = 1e7
+        const bool ray = !cap && opts.init_scale;
+        long long ts = 1;
+        if (ray) {
+            const int g = p->grid_init > p->grid_ray ? p->grid_init : p->grid_ray;
+            ts = (p->n / kTile) / (8LL * (g > 0 ? g : 1));
+            if (ts > 16) ts = 16;
+            if (ts < 1) ts = 1;
+        }
+        if ((e = launch_init(p, st->lam_trial, s, 0, ts)) != cudaSuccess)
             return fail(RA_ECUDA, "init launch: %s", cudaGetErrorString(e));
-        if (!cap && opts.init_scale && (e = launch_ray_scale(p, st->lam_trial, s)) != cudaSuccess)
+        if (ray && (e = launch_ray_scale(p, st->lam_trial, s, ts)) != cudaSuccess)
             return fail(RA_ECUDA, "ray-scale launch: %s", cudaGetErrorString(e));
     }
     solver_setup_kernel<<<1, 32, 0, s>>>(st, lambda0, p->R, p->m,

@@ -115,6 +115,23 @@ def test_solve_matches_oracle(ra, oracle, make, tol, fp64, prices, cap):
     P.close()
 
 
+def test_large_solve_with_sampled_start(ra, oracle):
+    """From about 2.5e6 jobs a cold start without the cap reads a strided
+    sample of the tiles for Eq. e-initialization's direction and for the
+    scale along its ray; the solve still meets the tolerance, certified by
+    the oracle in FP64, in fewer evaluations than from the paper's unscaled
+    start (full pass)."""
+    prob = W.config_large(n=2_600_000, m=32, seed=7)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=False)
+    info = P.solve(tol=1e-6)
+    assert info["status"] == ra.RA_OK, info
+    g, lb, gap = certify(oracle, prob, P, cap=False)
+    assert gap <= 1e-6, (g, lb, gap)
+    paper = P.solve(tol=1e-6, init_scale=False)
+    assert info["evals"] < paper["evals"], (info["evals"], paper["evals"])
+    P.close()
+
+
 def test_graph_and_host_loop_agree_bitwise(ra):
     prob = W.config_hetero(n=150_000, m=8, seed=4)
     P = ra.AllocationProblem.from_numpy(prob, "cuda")
