@@ -73,10 +73,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # the timed region is tens of ms: start it once samples flow
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -389,9 +393,10 @@ def run_gpu(args):
                "converged": r["converged"], "gap": r["gap"], "sample": _sample_text(r)}
     evals = [i["evals"] for i in infos]
     # per solve: initialisation (+ the ray scaling without the cap) and setup,
-    # then per evaluation: dual pass, solver step; per repair of the lower
-    # bound: scan, collect, gather, apply, FP64 evaluation, accept
-    launches = sum((2 if cap else 3) + 2 * i["evals"] + 6 * i["repairs"] for i in infos)
+    # then per evaluation: dual pass, lower-bound pass (it returns at once
+    # when the evaluation wrote no records), solver step; per repair of the
+    # lower bound: scan, collect, gather, apply, FP64 evaluation, accept
+    launches = sum((2 if cap else 3) + 3 * i["evals"] + 6 * i["repairs"] for i in infos)
     # the in-solve evaluation kernel: device time between price updates (the
     # solver's own global-timer accounting), against the bytes of A, w,
     # param and kind alone (the lower-bound records, 10 B/job written and 10
@@ -400,7 +405,9 @@ def run_gpu(args):
     st_ms = statistics.median(i["step_ms"] / max(i["evals"], 1) for i in infos)
     in_solve = {"achieved": alg_bytes / (ev_ms * 1e-3) / 1e9, "frac": alg_bytes / (ev_ms * 1e-3) / 1e9 / peak,
                 "launch_ms": ev_ms, "step_ms": st_ms,
-                "kernel": f"dual_tma_kernel in the solve ({'with' if cap else 'no'} cap; lagged bound, records)",
+                "kernel": (f"dual_tma_kernel in the solve ({'with cap; records for the lagged bound' if cap else 'no cap; own bound from its sums, no records'})"
+                           if n >= 4_000_000 or cap else
+                           "dual_tma_kernel in the solve (no cap; own bound and records for the lagged one)"),
                 "timing": "device global timer between solver steps (graph launch gaps included)"}
     other_mode = {"achieved": alg_bytes / (o_eval_ms * 1e-3) / 1e9,
                   "frac": alg_bytes / (o_eval_ms * 1e-3) / 1e9 / peak, "launch_ms": o_eval_ms,
