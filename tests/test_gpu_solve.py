@@ -115,6 +115,27 @@ def test_solve_matches_oracle(ra, oracle, make, tol, fp64, prices, cap):
     P.close()
 
 
+def test_own_bound_matches_oracle(ra, oracle):
+    """From 4e6 jobs without the cap the solver's lower bound is each
+    evaluation's own bound, formed from its sums (r, r_lin, U(X)).  At the
+    prices the certificate names, the oracle's FP64 form of that bound
+    (own_lower_bound) and the exact utility of the same column-scaled
+    allocation (lower_bound) bracket the GPU's U_lb, which sits on the
+    former to FP32 rounding."""
+    prob = W.config_large(n=4_200_000, m=32, seed=11)
+    P = ra.AllocationProblem.from_numpy(prob, "cuda", job_cap=False)
+    info = P.solve(tol=1e-6, master_lb=False)
+    assert info["status"] == ra.RA_OK, info
+    theta, lams, scaled = P.certificate()
+    P.close()
+    assert len(theta) == 1 and scaled[0] == 1, (theta, scaled)
+    own, _ = oracle.own_lower_bound(prob, lams[0])
+    exact, _ = oracle.lower_bound(prob, lams[0], cap=False)
+    scale = max(abs(info["g"]), 1.0)
+    assert own - 1e-6 * scale <= info["U_lb"] <= exact + 1e-6 * scale, (own, info["U_lb"], exact)
+    assert abs(info["U_lb"] - own) <= 1e-6 * scale, (own, info["U_lb"])
+
+
 def test_large_solve_with_sampled_start(ra, oracle):
     """From about 2.5e6 jobs a cold start without the cap reads a strided
     sample of the tiles for Eq. e-initialization's direction and for the
