@@ -704,10 +704,12 @@ def run_warm(args):
     if not os.path.exists(WS.WEIGHTS):
         return {"unavailable": "no trained network in the package"}
     net = WS.load()
-    rec = WS.evaluate(net, P=args.warm, log=None)
+    max_evals = 3000
+    rec = WS.evaluate(net, P=args.warm, log=None, max_evals=max_evals)
     net.close()
     out = WS.summarize(rec)
     out["held_out_seed"] = WS.EVAL_SEED
+    out["max_evals"] = max_evals
     out["note"] = ("medians over all held-out problems; a solve that stops at the evaluation "
                    "limit counts with its time")
     return out

@@ -146,7 +146,14 @@ __global__ void repair_accept_kernel(SolverState *st, double U_rep, const EvalOu
 {
     const int j = threadIdx.x;
     const int m = st->m;
-    const bool better = U_rep > st->U_best;
+    // the repaired utility is exact (FP64), and so is g at lam_best from the
+    // FP64 pass: their gap needs no allowance for FP32 rounding.  When it
+    // meets the request the pair certifies the solve even if a bound formed
+    // with FP32 per-job arithmetic was nominally higher.
+    const double g64 = exact->g;
+    const double den64 = fmax(fmax(fabs(U_rep), fabs(g64)), 1.0);
+    const bool exact_ok = isfinite(g64) && isfinite(U_rep) && (g64 - U_rep) / den64 <= tol_exact;
+    const bool better = U_rep > st->U_best || exact_ok;
     if (better && j < m) {
         st->lam_lb[j] = st->lam_best[j];
         st->theta_lam[0][j] = st->lam_best[j];
@@ -162,11 +169,6 @@ __global__ void repair_accept_kernel(SolverState *st, double U_rep, const EvalOu
         }
         const double den = fmax(fmax(fabs(st->U_best), fabs(st->g_best)), 1.0);
         double gap = (st->g_best - st->U_best) / den;
-        // the repaired utility is exact (FP64), and so is g at lam_best from
-        // the FP64 pass: their gap needs no allowance for FP32 rounding
-        const double g64 = exact->g;
-        const double den64 = fmax(fmax(fabs(U_rep), fabs(g64)), 1.0);
-        const bool exact_ok = better && isfinite(g64) && (g64 - U_rep) / den64 <= tol_exact;
         if (exact_ok) {
             st->g_best = g64;
             gap = (g64 - U_rep) / den64;

@@ -139,7 +139,7 @@ def train(X, Y, epochs=60, rows_per_step=4096, lr=2e-3, seed=0, holdout=0.05, lo
     return net, hist
 
 
-def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=500, job_cap=False,
+def evaluate(net, P=1000, seed=EVAL_SEED, device="cuda", tol=1e-6, max_evals=3000, job_cap=False,
              log=print):
     """Cold and warm ra_solve of P held-out problems; per problem the device
     time (CUDA events on the solve's stream, the warm one including the
@@ -260,7 +260,7 @@ def main(argv=None):
     else:
         net = load(args.weights)
         rec = evaluate(net, P=args.problems or 1000, job_cap=args.job_cap,
-                       max_evals=args.max_evals or 500)
+                       max_evals=args.max_evals or 3000)
         report = summarize(rec)
         report["per_problem"] = rec
     print(json.dumps({k: v for k, v in report.items() if k not in ("per_problem", "history")}),
