@@ -229,7 +229,7 @@ __device__ __forceinline__ unsigned char *align128(unsigned char *p)
 
 // Main streaming kernel, FP32 per-job arithmetic (Sections 3 and 4).
 template <int MT, bool CAP, bool LAG, bool REC>
-__global__ void __launch_bounds__(kTile, CAP ? 2 : 3)
+__global__ void __launch_bounds__(kTile, (CAP && MT >= 16) ? 2 : 3)
     dual_tma_kernel(DualParams P, int stages, long long num_full)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -1484,8 +1484,10 @@ cudaError_t configure_dual(ra_problem *p)
     const int m = p->m;
     p->mt = m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
     const bool cap = !(p->flags & RA_NO_JOB_CAP);
-    // two / three CTAs per SM; a stage also holds the tile's 2.5 KB of records
-    const size_t budget = cap ? 111 * 1024 : 70 * 1024;
+    // three CTAs per SM (two for the capped walk from 16 columns, whose
+    // registers would spill at three); a stage also holds the tile's 2.5 KB
+    // of records
+    const size_t budget = (cap && p->mt >= 16) ? 111 * 1024 : 70 * 1024;
     const size_t sb = ring_stage_bytes(m);  // layout does not depend on MT
     int stages = static_cast<int>(budget / sb);
     if (stages > kMaxStages) stages = kMaxStages;
