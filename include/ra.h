@@ -210,8 +210,9 @@ ra_status ra_solve(ra_problem *prob, const ra_solve_opts *opts, const double *la
  * ra_solve_certificate -- the allocation behind the lower bound U_lb of the
  * last ra_solve, as a convex combination of subproblem allocations: entry k
  * has weight theta[k] (summing to 1), prices lam[k*m .. k*m+m) and scaled[k]
- * = 1 when that allocation was column-scaled to X diag(min(1, R/r)) (Section
- * 5) before mixing.  The mixture meets sum_i x_i <= R, and since every u_i is
+ * = 1 when that allocation was column-scaled (Section 5) before mixing: to
+ * X diag(min(1, R/r)) with the per-job cap, as ra_eval_dual's U_lb describes
+ * without it.  The mixture meets sum_i x_i <= R, and since every u_i is
  * concave its utility is at least U_lb.  A single entry with scaled[0] = 2
  * means the bound came from a repair (see repair_window): the allocation is
  * the one ra_recover_feasible returns at lam[0] with default options.  theta, scaled: host arrays of
