@@ -9,6 +9,8 @@ this module adds the price-discovery loop of Section 5 (Algorithm 2):
 
 * dual value and subgradient  g(lam), q = R - r          (Section 3)
 * feasible lower bound by column scaling  U(X~)            (Section 5)
+* a bound on U(X~) from the evaluation's sums alone (no per-job cap;
+  t u'(t) = lambda_j x_ij at each job's optimum, Section 4.1)
 * initial prices                                             (Eq. e-initialization)
 * L-BFGS price updates with bounds lam >= 0 -- scipy's L-BFGS-B
   (memory 10) serves as the quasi-Newton step (Section 5, "More efficient
